@@ -1,0 +1,210 @@
+"""FP64 CPU oracle for the mu-mode product, the Tucker operator and what they drive.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
+with the CUDA library and never imports it.
+
+Tensors are numpy arrays of any memory order; they are handed to the C code
+column-major (Fortran order), the layout of the vec operator of Appendix A.
+A matrix ``L`` of shape ``(n, m)`` acts on fibres of length ``m``.
+
+The C source is ``kron_oracle.c`` next to this file; it is compiled on first
+use (gcc, -O2, OpenMP, no fast-math, no FP contraction) into
+``libkron_oracle.so``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kron_oracle.c")
+_LIB = os.path.join(_HERE, "libkron_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle into a shared library next to the source."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp.%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+               "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = ctypes.CDLL(_LIB)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        dp = ctypes.c_void_p
+        _lib.oracle_mump.argtypes = [ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int64, dp, dp,
+                                     ctypes.c_int64, ctypes.c_int, dp]
+        _lib.oracle_tucker.argtypes = [ctypes.c_int, i64p, i64p, dp, dp, i64p, ctypes.c_int, dp]
+        _lib.oracle_tucker_nested.argtypes = [ctypes.c_int, i64p, i64p, dp, dp, i64p, ctypes.c_int, dp]
+        _lib.oracle_kron.argtypes = [ctypes.c_int64, ctypes.c_int64, dp, ctypes.c_int64,
+                                     ctypes.c_int64, dp, dp]
+        _lib.oracle_matvec.argtypes = [ctypes.c_int64, ctypes.c_int64, dp, dp, dp]
+        _lib.oracle_tucker_adjoint.argtypes = [ctypes.c_int, i64p, i64p, dp, dp, i64p, dp, dp, dp]
+        _lib.oracle_expm_tridiag_toeplitz.argtypes = [ctypes.c_int64, ctypes.c_double,
+                                                      ctypes.c_double, ctypes.c_double,
+                                                      ctypes.c_double, dp]
+        _lib.oracle_expm_taylor.argtypes = [ctypes.c_int64, dp, ctypes.c_double, dp]
+        _lib.oracle_expkronsum_steps.argtypes = [ctypes.c_int, i64p, dp, ctypes.c_int, dp]
+        _lib.oracle_kronsumv.argtypes = [ctypes.c_int, i64p, dp, dp, i64p, dp]
+        _lib.oracle_num_threads.restype = ctypes.c_int
+    return _lib
+
+
+def num_threads() -> int:
+    """OpenMP threads the oracle uses (the host cores it runs on)."""
+    return int(_load().oracle_num_threads())
+
+
+def _f64(a) -> np.ndarray:
+    return np.asfortranarray(np.asarray(a, dtype=np.float64))
+
+
+def _i64(vals) -> ctypes.Array:
+    arr = (ctypes.c_int64 * len(vals))(*[int(v) for v in vals])
+    return arr
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+def mump(T, L, mu: int, transL: bool = False) -> np.ndarray:
+    """``T x_mu op(L)`` (Eq. (mmp)); ``mu`` is 0-based.  op(L) = L, or L^T if transL."""
+    T = _f64(T)
+    L = _f64(L)
+    m = list(T.shape)
+    d = len(m)
+    n = L.shape[1] if transL else L.shape[0]
+    out = list(m)
+    out[mu] = n
+    S = np.zeros(out, dtype=np.float64, order="F")
+    ld = max(L.shape[0], 1)
+    _check(_load().oracle_mump(d, _i64(m), mu, n, _ptr(T), _ptr(L), ld, int(transL), _ptr(S)), "mump")
+    return S
+
+
+def _mat_table(Ls):
+    Ls = [_f64(L) for L in Ls]
+    ptrs = (ctypes.c_void_p * len(Ls))(*[_ptr(L) for L in Ls])
+    lds = _i64([max(L.shape[0], 1) for L in Ls])
+    return Ls, ptrs, lds
+
+
+def tucker(T, Ls, transL: bool = False) -> np.ndarray:
+    """Tucker operator ``T x_1 op(L_1) ... x_d op(L_d)`` (Eq. (tuckerop)), modes in order 1..d."""
+    T = _f64(T)
+    m = list(T.shape)
+    d = len(m)
+    Ls, ptrs, lds = _mat_table(Ls)
+    n = [(L.shape[1] if transL else L.shape[0]) for L in Ls]
+    S = np.zeros(n, dtype=np.float64, order="F")
+    _check(_load().oracle_tucker(d, _i64(m), _i64(n), _ptr(T), ptrs, lds, int(transL), _ptr(S)),
+           "tucker")
+    return S
+
+
+def tucker_nested(T, Ls, transL: bool = False) -> np.ndarray:
+    """Brute-force element-wise sum of Eq. (nestedmumode); tiny inputs only."""
+    T = _f64(T)
+    m = list(T.shape)
+    d = len(m)
+    Ls, ptrs, lds = _mat_table(Ls)
+    n = [(L.shape[1] if transL else L.shape[0]) for L in Ls]
+    S = np.zeros(n, dtype=np.float64, order="F")
+    _check(_load().oracle_tucker_nested(d, _i64(m), _i64(n), _ptr(T), ptrs, lds, int(transL),
+                                        _ptr(S)), "tucker_nested")
+    return S
+
+
+def kron(A, B) -> np.ndarray:
+    """Kronecker product ``A (x) B`` as defined in Appendix A."""
+    A = _f64(np.atleast_2d(A))
+    B = _f64(np.atleast_2d(B))
+    C = np.zeros((A.shape[0] * B.shape[0], A.shape[1] * B.shape[1]), order="F")
+    _check(_load().oracle_kron(A.shape[0], A.shape[1], _ptr(A), B.shape[0], B.shape[1], _ptr(B),
+                               _ptr(C)), "kron")
+    return C
+
+
+def matvec(A, x) -> np.ndarray:
+    A = _f64(A)
+    x = _f64(np.ravel(x, order="F"))
+    y = np.zeros(A.shape[0])
+    _check(_load().oracle_matvec(A.shape[0], A.shape[1], _ptr(A), _ptr(x), _ptr(y)), "matvec")
+    return y
+
+
+def vec(T) -> np.ndarray:
+    """vec operator of Appendix A: first index fastest."""
+    return np.ravel(np.asarray(T), order="F")
+
+
+def tucker_adjoint(T, Ls, dS, want_dT: bool = True, want_dL: bool = True):
+    """Gradients of <S, dS> with S = tucker(T, Ls): returns (dT, [dL_mu])."""
+    T = _f64(T)
+    dS = _f64(dS)
+    m = list(T.shape)
+    d = len(m)
+    Ls, ptrs, lds = _mat_table(Ls)
+    n = [L.shape[0] for L in Ls]
+    dT = np.zeros(m, order="F") if want_dT else None
+    dL = [np.zeros((n[k], m[k]), order="F") for k in range(d)] if want_dL else None
+    dLp = (ctypes.c_void_p * d)(*[_ptr(x) for x in dL]) if want_dL else None
+    _check(_load().oracle_tucker_adjoint(d, _i64(m), _i64(n), _ptr(T), ptrs, lds, _ptr(dS),
+                                         _ptr(dT) if want_dT else None, dLp), "tucker_adjoint")
+    return dT, dL
+
+
+def expm_tridiag_toeplitz(n: int, a: float, b: float, c: float, t: float) -> np.ndarray:
+    """Closed-form exp(t A) for A = tridiag(a, b, c) (sub, diag, super), long double inside."""
+    E = np.zeros((n, n), order="F")
+    _check(_load().oracle_expm_tridiag_toeplitz(n, a, b, c, t, _ptr(E)), "expm_tridiag_toeplitz")
+    return E
+
+
+def expm_taylor(A, t: float = 1.0) -> np.ndarray:
+    """exp(t A) by long-double Taylor series with scaling and squaring (small A only)."""
+    A = _f64(A)
+    n = A.shape[0]
+    E = np.zeros((n, n), order="F")
+    _check(_load().oracle_expm_taylor(n, _ptr(A), t, _ptr(E)), "expm_taylor")
+    return E
+
+
+def expkronsum_steps(U0, Es, nsteps: int) -> np.ndarray:
+    """nsteps steps U <- U x_1 E_1 ... x_d E_d (Eq. (exptucker)); returns a new array."""
+    U = np.array(_f64(U0), order="F", copy=True)
+    n = list(U.shape)
+    d = len(n)
+    Es = [_f64(E) for E in Es]
+    ptrs = (ctypes.c_void_p * d)(*[_ptr(E) for E in Es])
+    _check(_load().oracle_expkronsum_steps(d, _i64(n), ptrs, nsteps, _ptr(U)), "expkronsum_steps")
+    return U
+
+
+def kronsumv(V, Ls) -> np.ndarray:
+    """Action of the Kronecker sum, Eq. (actkron): sum_mu V x_mu L_mu."""
+    V = _f64(V)
+    n = list(V.shape)
+    d = len(n)
+    Ls, ptrs, lds = _mat_table(Ls)
+    S = np.zeros(n, order="F")
+    _check(_load().oracle_kronsumv(d, _i64(n), _ptr(V), ptrs, lds, _ptr(S)), "kronsumv")
+    return S

@@ -1,0 +1,320 @@
+"""Pins of the FP64 oracle against what the paper and plain mathematics fix.
+
+None of these compares the oracle with itself: every expected value comes
+from a different route (brute-force sums, the Kronecker form, a library
+routine, a closed form, or a value printed in the paper).
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle
+import workloads as W
+
+RNG = np.random.default_rng(12345)
+
+
+def rand(*shape):
+    return np.asfortranarray(RNG.standard_normal(shape))
+
+
+# ---------------------------------------------------------------- Tucker ---
+
+@pytest.mark.parametrize("m,n", [
+    ((1,), (3,)), ((3,), (1,)), ((2, 3), (4, 1)), ((3, 2, 4), (2, 4, 3)),
+    ((1, 4, 1), (3, 1, 2)), ((2, 3, 2, 2), (3, 2, 1, 4)), ((4, 4, 4), (4, 4, 4)),
+])
+def test_tucker_equals_nested_sum(m, n):
+    """Eq. (nestedmumode): brute-force sum over all input multi-indices."""
+    T = rand(*m)
+    Ls = [rand(n[k], m[k]) for k in range(len(m))]
+    S = oracle.tucker(T, Ls)
+    S2 = oracle.tucker_nested(T, Ls)
+    assert S.shape == tuple(n)
+    np.testing.assert_allclose(S, S2, rtol=1e-13, atol=1e-13 * np.abs(S2).max())
+
+
+@pytest.mark.parametrize("m,n", [((3, 4, 5), (5, 2, 3)), ((4, 4, 4, 4), (4, 3, 2, 4)),
+                                 ((7,), (5,)), ((6, 9), (8, 4))])
+def test_tucker_equals_kronecker_form(m, n):
+    """Lemma (krontomu): vec(S) = (L_d (x) ... (x) L_1) vec(T), the Kronecker
+    product built with numpy.kron (a library routine, Appendix A definition)."""
+    T = rand(*m)
+    Ls = [rand(n[k], m[k]) for k in range(len(m))]
+    K = Ls[0]
+    for L in Ls[1:]:
+        K = np.kron(L, K)
+    ref = K @ oracle.vec(T)
+    S = oracle.tucker(T, Ls)
+    np.testing.assert_allclose(oracle.vec(S), ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_kron_matches_numpy():
+    A, B = rand(3, 2), rand(4, 5)
+    np.testing.assert_array_equal(oracle.kron(A, B), np.kron(A, B))
+
+
+def test_identity_is_neutral():
+    """The identity is the neutral element of the mu-mode product (Section 2)."""
+    T = rand(5, 3, 4)
+    S = oracle.tucker(T, [np.eye(5), np.eye(3), np.eye(4)])
+    np.testing.assert_array_equal(S, T)
+
+
+def test_products_in_distinct_modes_commute():
+    """Order invariance of the Tucker operator (Section 2, after Eq. (nestedmumode))."""
+    T = rand(4, 5, 6)
+    A, B = rand(3, 4), rand(7, 6)
+    S1 = oracle.mump(oracle.mump(T, A, 0), B, 2)
+    S2 = oracle.mump(oracle.mump(T, B, 2), A, 0)
+    np.testing.assert_allclose(S1, S2, rtol=1e-13, atol=1e-13)
+
+
+def test_two_dimensional_case_is_matrix_product():
+    """Eq. (gen2dmatmat): for d = 2, S = L_1 T L_2^T."""
+    T = rand(6, 9)
+    L1, L2 = rand(5, 6), rand(4, 9)
+    np.testing.assert_allclose(oracle.tucker(T, [L1, L2]), L1 @ T @ L2.T, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("mu", [0, 1, 2, 3])
+def test_mump_matches_tensordot(mu):
+    """Definition (mmp): L applied to every mu-fibre, via numpy.tensordot."""
+    T = rand(3, 4, 5, 2)
+    L = rand(6, T.shape[mu])
+    ref = np.moveaxis(np.tensordot(L, T, axes=([1], [mu])), 0, mu)
+    np.testing.assert_allclose(oracle.mump(T, L, mu), ref, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(oracle.mump(T, np.asfortranarray(L.T), mu, transL=True), ref,
+                               rtol=1e-13, atol=1e-13)
+
+
+def test_rank_one_tensor():
+    """T = a o b o c gives S = (L_1 a) o (L_2 b) o (L_3 c) (Eq. (nestedmumode) factorises)."""
+    a, b, c = rand(7), rand(5), rand(6)
+    T = np.asfortranarray(np.multiply.outer(np.multiply.outer(a, b), c))
+    Ls = [rand(4, 7), rand(8, 5), rand(3, 6)]
+    ref = np.multiply.outer(np.multiply.outer(Ls[0] @ a, Ls[1] @ b), Ls[2] @ c)
+    np.testing.assert_allclose(oracle.tucker(T, Ls), ref, rtol=1e-13, atol=1e-13)
+
+
+def test_kronsumv_matches_kronecker_sum():
+    """Eq. (actkron) against the assembled Kronecker sum (Appendix A definition)."""
+    n = (3, 4, 2)
+    V = rand(*n)
+    Ls = [rand(k, k) for k in n]
+    K = np.zeros((int(np.prod(n)),) * 2)
+    for mu in range(3):
+        term = np.eye(1)
+        for k in range(3):
+            term = np.kron(Ls[k] if k == mu else np.eye(n[k]), term)
+        K += term
+    np.testing.assert_allclose(oracle.vec(oracle.kronsumv(V, Ls)), K @ oracle.vec(V),
+                               rtol=1e-13, atol=1e-13)
+
+
+# --------------------------------------------------------------- adjoint ---
+
+def test_adjoint_dot_product():
+    """<tucker(T), W> = <T, W x_mu L_mu^T> (Appendix A, property 5)."""
+    m, n = (4, 5, 3), (6, 2, 4)
+    T, Wt = rand(*m), rand(*n)
+    Ls = [rand(n[k], m[k]) for k in range(3)]
+    dT, _ = oracle.tucker_adjoint(T, Ls, Wt, want_dL=False)
+    lhs = np.sum(oracle.tucker(T, Ls) * Wt)
+    rhs = np.sum(T * dT)
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
+
+
+def _loss(T, Ls, target):
+    r = oracle.tucker(T, Ls) - target
+    return 0.5 * float(np.sum(r * r))
+
+
+def test_adjoint_central_differences():
+    """Gradient of 0.5 ||tucker(T, L) - target||^2 against central differences.
+    The loss is quadratic along a single-argument direction, so central
+    differences carry no truncation error."""
+    m, n = (3, 4, 2, 3), (2, 3, 4, 3)
+    T, target = rand(*m), rand(*n)
+    Ls = [rand(n[k], m[k]) for k in range(4)]
+    dS = oracle.tucker(T, Ls) - target
+    dT, dL = oracle.tucker_adjoint(T, Ls, dS)
+    h = 1e-3
+    for _ in range(4):
+        V = rand(*m)
+        fd = (_loss(T + h * V, Ls, target) - _loss(T - h * V, Ls, target)) / (2 * h)
+        assert abs(fd - np.sum(dT * V)) <= 1e-9 * max(1.0, abs(fd))
+    for mu in range(4):
+        V = rand(n[mu], m[mu])
+        Lp = list(Ls); Lm = list(Ls)
+        Lp[mu] = Ls[mu] + h * V
+        Lm[mu] = Ls[mu] - h * V
+        fd = (_loss(T, Lp, target) - _loss(T, Lm, target)) / (2 * h)
+        assert abs(fd - np.sum(dL[mu] * V)) <= 1e-9 * max(1.0, abs(fd))
+
+
+def test_adjoint_full_coordinate_fd_tiny():
+    m, n = (2, 3, 2), (3, 2, 2)
+    T, target = rand(*m), rand(*n)
+    Ls = [rand(n[k], m[k]) for k in range(3)]
+    dT, dL = oracle.tucker_adjoint(T, Ls, oracle.tucker(T, Ls) - target)
+    h = 1e-4
+    for idx in np.ndindex(*m):
+        E = np.zeros(m, order="F"); E[idx] = 1
+        fd = (_loss(T + h * E, Ls, target) - _loss(T - h * E, Ls, target)) / (2 * h)
+        assert abs(fd - dT[idx]) <= 1e-8 * max(1.0, abs(fd))
+    for mu in range(3):
+        for idx in np.ndindex(n[mu], m[mu]):
+            E = np.zeros((n[mu], m[mu])); E[idx] = 1
+            Lp = list(Ls); Lm = list(Ls)
+            Lp[mu] = Ls[mu] + h * E
+            Lm[mu] = Ls[mu] - h * E
+            fd = (_loss(T, Lp, target) - _loss(T, Lm, target)) / (2 * h)
+            assert abs(fd - dL[mu][idx]) <= 1e-8 * max(1.0, abs(fd))
+
+
+# ----------------------------------------------------------- exponential ---
+
+@pytest.mark.parametrize("n", [1, 2, 5, 12])
+def test_expm_closed_form_matches_scipy_and_taylor(n):
+    sub, diag, sup = W.fd_advection_diffusion(n)
+    t = 1e-4
+    A = W.tridiag_dense(n, sub, diag, sup)
+    E1 = oracle.expm_tridiag_toeplitz(n, sub, diag, sup, t)
+    E2 = oracle.expm_taylor(A, t)
+    E3 = scipy.linalg.expm(t * A)
+    scale = np.abs(E3).max()
+    np.testing.assert_allclose(E1, E3, rtol=0, atol=1e-13 * scale)
+    np.testing.assert_allclose(E2, E3, rtol=0, atol=1e-13 * scale)
+
+
+def test_expm_symmetric_matches_eigendecomposition():
+    """a = c: textbook symmetric eigen-decomposition (numpy.linalg.eigh)."""
+    n, a, b = 9, 1.3, -2.1
+    A = W.tridiag_dense(n, a, b, a)
+    lam, V = np.linalg.eigh(A)
+    ref = (V * np.exp(0.7 * lam)) @ V.T
+    np.testing.assert_allclose(oracle.expm_tridiag_toeplitz(n, a, b, a, 0.7), ref,
+                               rtol=0, atol=1e-13)
+
+
+def test_expm_taylor_nonnormal_small():
+    A = rand(6, 6)
+    np.testing.assert_allclose(oracle.expm_taylor(A, 0.9), scipy.linalg.expm(0.9 * A),
+                               rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("n", [4, 5, 6])
+def test_stepper_matches_full_kronecker_sum_expm(n):
+    """Eq. (expmat) with the assembled Kronecker sum (exponentiated by the
+    long-double Taylor routine) against one step of Eq. (exptucker)."""
+    sub, diag, sup = W.fd_advection_diffusion(n)
+    tau = 3e-3
+    A = W.tridiag_dense(n, sub, diag, sup)
+    I = np.eye(n)
+    K = np.kron(I, np.kron(I, A)) + np.kron(I, np.kron(A, I)) + np.kron(A, np.kron(I, I))
+    U0 = rand(n, n, n)
+    ref = oracle.expm_taylor(K, tau) @ oracle.vec(U0)
+    E = oracle.expm_tridiag_toeplitz(n, sub, diag, sup, tau)
+    U1 = oracle.expkronsum_steps(U0, [E, E, E], 1)
+    np.testing.assert_allclose(oracle.vec(U1), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_stepper_semigroup():
+    """k steps with exp(tau A) equal one step with exp(k tau A)."""
+    n, k, tau = 7, 5, 2e-3
+    sub, diag, sup = W.fd_advection_diffusion(n)
+    U0 = rand(n, n, n)
+    E1 = oracle.expm_tridiag_toeplitz(n, sub, diag, sup, tau)
+    Ek = oracle.expm_tridiag_toeplitz(n, sub, diag, sup, k * tau)
+    Uk = oracle.expkronsum_steps(U0, [E1] * 3, k)
+    U1 = oracle.expkronsum_steps(U0, [Ek] * 3, 1)
+    np.testing.assert_allclose(Uk, U1, rtol=0, atol=1e-12 * np.abs(U1).max())
+
+
+def test_stepper_pure_diffusion_eigenmode():
+    """No advection, a sine eigenmode: pure decay by exp(t sum_mu lambda_mu)."""
+    n, tau, steps = 16, 1e-3, 3
+    sub, diag, sup = W.fd_advection_diffusion(n, advection=0.0)
+    h = 1.0 / (n + 1)
+    x = np.arange(1, n + 1) * h
+    ks = (1, 2, 3)
+    vecs = [np.sin(k * np.pi * x) for k in ks]
+    lam = [diag + 2 * sub * np.cos(k * np.pi / (n + 1)) for k in ks]
+    U0 = np.asfortranarray(np.multiply.outer(np.multiply.outer(vecs[0], vecs[1]), vecs[2]))
+    E = oracle.expm_tridiag_toeplitz(n, sub, diag, sup, tau)
+    U = oracle.expkronsum_steps(U0, [E] * 3, steps)
+    ref = U0 * np.exp(steps * tau * sum(lam))
+    np.testing.assert_allclose(U, ref, rtol=0, atol=1e-13 * np.abs(U0).max())
+
+
+# --------------------------------------------------- workload matrices ---
+
+def test_chebyshev_vandermonde_discrete_orthogonality():
+    n = 20
+    L = W.chebyshev_vandermonde(n, n)
+    G = L.T @ L
+    ref = np.diag([n] + [n / 2] * (n - 1))
+    np.testing.assert_allclose(G, ref, rtol=0, atol=1e-12)
+    T = rand(n, n, n)
+    Dinv = np.diag(1.0 / np.diag(ref))
+    back = oracle.mump(oracle.mump(T, L, 1), Dinv @ L.T, 1)
+    np.testing.assert_allclose(back, T, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("m,n", [(8, 12), (11, 17), (15, 23), (64, 96)])
+def test_barycentric_partition_of_unity_and_polynomials(m, n):
+    x = W.uniform_points(n)
+    L = W.barycentric_matrix(m, x)
+    np.testing.assert_allclose(L.sum(axis=1), 1.0, rtol=0, atol=1e-12)
+    xi = W.chebyshev_points(m)
+    # a separable polynomial of degree < m per direction is reproduced exactly
+    c = rand(m)
+    p = lambda t: np.polynomial.chebyshev.chebval(t, c)
+    F = np.asfortranarray(np.multiply.outer(p(xi), p(xi)))
+    P = oracle.tucker(F, [L, L])
+    ref = np.multiply.outer(p(x), p(x))
+    np.testing.assert_allclose(P, ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+
+
+def _runge_error(m, n=35):
+    xi = W.chebyshev_points(m)
+    x = W.uniform_points(n)
+    F = W.runge([xi] * 5)
+    L = W.barycentric_matrix(m, x)
+    P = oracle.tucker(F, [L] * 5)
+    return W.rel_err_max(P, W.runge([x] * 5))
+
+
+def _golden_fig3():
+    path = os.path.join(os.path.dirname(__file__), "golden", "fig3_runge_errors.txt")
+    rows = []
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if line:
+            m, e = line.split()
+            rows.append((int(m), e))
+    return rows
+
+
+@pytest.mark.parametrize("m,printed", [r for r in _golden_fig3() if r[0] <= 25])
+def test_runge_interpolation_errors_match_paper(m, printed):
+    """Section 4.3, Figure 3: the printed max-norm relative errors, to the
+    printed digits."""
+    err = _runge_error(m)
+    digits = len(printed.split("e")[0].replace(".", "").lstrip("0"))
+    ref = float(printed)
+    ulp = 10.0 ** (np.floor(np.log10(ref)) - (digits - 1))
+    assert abs(err - ref) <= 0.5 * ulp, (m, err, printed)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("m,printed", [r for r in _golden_fig3() if r[0] == 35])
+def test_runge_interpolation_errors_match_paper_m35(m, printed):
+    err = _runge_error(m)
+    digits = len(printed.split("e")[0].replace(".", "").lstrip("0"))
+    ref = float(printed)
+    ulp = 10.0 ** (np.floor(np.log10(ref)) - (digits - 1))
+    assert abs(err - ref) <= 0.5 * ulp, (m, err, printed)
