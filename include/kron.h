@@ -1,0 +1,233 @@
+/*
+ * kron.h -- C ABI of libkron, a GB300 (sm_103a) library for mu-mode products
+ * and Tucker operators (Caliari, Cassini, Zivcovich, "A mu-mode BLAS approach
+ * for multidimensional tensor-structured problems", arXiv 2112.11238).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  * Tensors are dense and column-major: T in R^{m_1 x ... x m_d} stores
+ *    T(j_1, ..., j_d) (0-based) at j_1 + m_1 (j_2 + m_2 (j_3 + ...)), the vec
+ *    ordering of the paper's Appendix A.  d is 1..KRON_MAX_D.
+ *  * A matrix L_mu of size n_mu x m_mu is column-major with leading dimension
+ *    ldL >= n_mu: element (i, j) at L[i + ldL * j].  With trans = 1 the call
+ *    uses L^T instead, L then being m_mu x n_mu with ldL >= m_mu.
+ *  * Every tensor/matrix pointer is a DEVICE pointer owned by the caller.
+ *    Shape arrays and arrays of pointers live in HOST memory.  Element type is
+ *    given by kron_dtype (double or float) and is the same for all tensors and
+ *    matrices of a call, except where a call says otherwise.
+ *  * Calls are asynchronous and ordered on the given CUDA stream (0 = legacy
+ *    default stream).  No call synchronises the device, except
+ *    kron_get_device_error.  The library allocates no device memory in any
+ *    compute call: scratch comes from the caller's workspace `ws`
+ *    (`ws_bytes` long, 256-byte aligned), whose required size the matching
+ *    *_workspace_size call reports.  Plans are host-only objects.
+ *  * Output tensors must not overlap inputs or the workspace (except where a
+ *    call states an in-place update).
+ *  * Errors: invalid host-side arguments are reported synchronously by the
+ *    returned status and nothing is launched.  Errors detected by a kernel
+ *    (a bounded wait that timed out) are latched in a per-device error word
+ *    read by kron_get_device_error.  No C++ exception crosses this ABI.
+ *  * Effective FLOPs of a Tucker operator are the algorithmic
+ *    sum_mu 2 n_mu m_mu prod(other current sizes), independent of precision.
+ */
+#ifndef KRON_H
+#define KRON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define KRON_API __attribute__((visibility("default")))
+#else
+#define KRON_API
+#endif
+
+/* CUDA stream handle; identical to cudaStream_t. */
+typedef struct CUstream_st *kron_stream_t;
+
+#define KRON_MAX_D 6
+
+typedef enum kron_status {
+    KRON_OK = 0,
+    KRON_ERR_INVALID_ARG = 1, /* bad size, null pointer, bad enum, ld too small */
+    KRON_ERR_UNSUPPORTED = 2, /* valid but not provided (e.g. a size above a limit) */
+    KRON_ERR_ALIGNMENT = 3,   /* a pointer is not aligned to its element size / 256 B workspace */
+    KRON_ERR_WORKSPACE = 4,   /* ws_bytes smaller than the reported requirement */
+    KRON_ERR_CUDA = 5,        /* a CUDA runtime call failed (launch error, ...) */
+    KRON_ERR_TIMEOUT = 6,     /* a kernel's bounded wait ran out (device error word) */
+    KRON_ERR_NUMERIC = 7      /* non-finite input where a finite one is required */
+} kron_status;
+
+typedef enum kron_dtype { KRON_F64 = 0, KRON_F32 = 1 } kron_dtype;
+
+/*
+ * Arithmetic used for the contractions.
+ *  KRON_PREC_FP64   : FP64 fused multiply-add on CUDA cores, FP64 intermediates.
+ *  KRON_PREC_FP32   : FP32 fused multiply-add on CUDA cores, FP32 intermediates.
+ *  KRON_PREC_3XTF32 : tensor cores (tcgen05 kind::tf32); each operand split
+ *                     x = x_hi + x_lo into two TF32 pieces (round to nearest),
+ *                     three products lo*hi + hi*lo + hi*hi accumulated in FP32.
+ *  KRON_PREC_BF16X3 : tensor cores (tcgen05 kind::f16, bf16 operands); two
+ *                     bf16 pieces per operand, three products, FP32 accumulate.
+ *  KRON_PREC_BF16X6 : three bf16 pieces per operand, the six products with
+ *                     piece-index sum <= 2, FP32 accumulate.
+ * Split forms keep intermediates in FP32.  Inputs stored as double are split
+ * from their double value.
+ */
+typedef enum kron_prec {
+    KRON_PREC_FP64 = 0,
+    KRON_PREC_FP32 = 1,
+    KRON_PREC_3XTF32 = 2,
+    KRON_PREC_BF16X3 = 3,
+    KRON_PREC_BF16X6 = 4
+} kron_prec;
+
+/* Plan flags. */
+#define KRON_PLAN_TRANS_L 0x1u     /* use L_mu^T for every mode (cf. the paper's cttucker) */
+#define KRON_PLAN_NATURAL_ORDER 0x2u /* apply modes in order 1..d instead of the cost-minimising order */
+
+typedef struct kron_plan_s *kron_plan;
+
+KRON_API const char *kron_status_string(kron_status s);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+KRON_API int kron_version(void);
+
+/*
+ * Reads, and with clear != 0 resets, the device error word of the current
+ * device (bit 0: a bounded wait inside a kernel timed out).  Synchronises the
+ * device first.  *code receives the word; returns KRON_ERR_TIMEOUT if bit 0 is
+ * set, KRON_OK otherwise.
+ */
+KRON_API kron_status kron_get_device_error(int *code, int clear);
+
+/* ------------------------------------------------------------------------ */
+/* mu-mode product: Definition "mu-mode product", Eq. (mmp)                  */
+/* ------------------------------------------------------------------------ */
+/*
+ * S = T x_mu op(L):  S^{(mu)} = op(L) T^{(mu)}, i.e. op(L) (n x m_mu) applied
+ * to every mu-fibre of T.  mu is 0-based (0 <= mu < d).  T has sizes
+ * m[0..d-1]; S has the same sizes with n in position mu.  The unfolding is
+ * never formed: for mu > 0 the call runs a strided batched contraction over
+ * the slabs T(:, :, q), for mu == 0 a plain GEMM.  n >= 1, all m >= 1.
+ */
+KRON_API kron_status kron_mump_workspace_size(int d, const int64_t *m, int mu, int64_t n,
+                                     kron_dtype dtype, kron_prec prec, size_t *bytes);
+KRON_API kron_status kron_mump(int d, const int64_t *m, int mu, int64_t n, const void *T,
+                      const void *L, int64_t ldL, int transL, void *S,
+                      kron_dtype dtype, kron_prec prec, void *ws, size_t ws_bytes,
+                      kron_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Tucker operator: Definition "Tucker operator", Eq. (tuckerop)             */
+/* ------------------------------------------------------------------------ */
+/*
+ * A plan fixes d, the sizes m (input) and n (output), the storage dtype, the
+ * precision and the flags; it chooses the order in which the d mu-mode
+ * products run (the result is independent of the order, Section 2) so as to
+ * minimise the flop count, unless KRON_PLAN_NATURAL_ORDER is given.
+ */
+KRON_API kron_status kron_plan_create(kron_plan *plan, int d, const int64_t *m, const int64_t *n,
+                             kron_dtype dtype, kron_prec prec, unsigned flags);
+KRON_API kron_status kron_plan_destroy(kron_plan plan);
+/* Workspace of kron_tucker for this plan. */
+KRON_API kron_status kron_plan_workspace_size(kron_plan plan, size_t *bytes);
+/* The 0-based mode order the plan applies (d entries). */
+KRON_API kron_status kron_plan_order(kron_plan plan, int *order);
+/* Algorithmic FLOPs of one Tucker operator of this plan (see header comment). */
+KRON_API double kron_plan_flops(kron_plan plan);
+
+/*
+ * S = T x_1 op(L_1) x_2 ... x_d op(L_d)   (Eq. (tuckerop); Eq. (nestedmumode)
+ * element-wise; vec(S) = (L_d (x) ... (x) L_1) vec(T), Lemma "krontomu").
+ * L[mu] / ldL[mu]: host arrays of d device pointers / leading dimensions.
+ */
+KRON_API kron_status kron_tucker(kron_plan plan, const void *T, const void *const *L,
+                        const int64_t *ldL, void *S, void *ws, size_t ws_bytes,
+                        kron_stream_t stream);
+
+/*
+ * Adjoint of the Tucker operator, for S = T x_1 L_1 ... x_d L_d (the plan must
+ * not carry KRON_PLAN_TRANS_L).  Given the cotangent dS (sizes n):
+ *   dT = dS x_1 L_1^T ... x_d L_d^T   (Appendix A, property 5, transposed
+ *                                      Kronecker form of Lemma "krontomu");
+ *   dL_mu = G_{mu+1}^{(mu)} (X_mu^{(mu)})^T  (from Eq. (mmp)), where
+ *   X_mu = T x_1 L_1 ... x_{mu-1} L_{mu-1} and G_{mu+1} = dS pulled back
+ *   through the modes after mu.  X_mu is recomputed from T, not stored.
+ * dT (sizes m) may be NULL; dL[mu] (n_mu x m_mu, ld n_mu) may be NULL per mode
+ * (dL itself may be NULL).  The contraction order is fixed (modes 1..d), so
+ * results are deterministic.
+ */
+KRON_API kron_status kron_adjoint_workspace_size(kron_plan plan, size_t *bytes);
+KRON_API kron_status kron_tucker_adjoint(kron_plan plan, const void *T, const void *const *L,
+                                const int64_t *ldL, const void *dS, void *dT,
+                                void *const *dL, void *ws, size_t ws_bytes,
+                                kron_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Exponential of a Kronecker sum: Section 3.3, Eqs. (expmat), (exptucker)   */
+/* ------------------------------------------------------------------------ */
+/*
+ * E = exp(tau A) for a dense n x n FP64 matrix (device, ld ldA >= n), E dense
+ * n x n (ld n), by scaling and squaring with the [13/13] Pade approximant
+ * (Higham, SIAM J. Matrix Anal. Appl. 26, 2005), all in FP64 on the GPU; the
+ * Pade linear system is solved by LU with partial pivoting followed by one
+ * step of iterative refinement with an FP64 residual.  1 <= n <= 1024.
+ */
+KRON_API kron_status kron_expm_workspace_size(int64_t n, size_t *bytes);
+KRON_API kron_status kron_expm(int64_t n, const double *A, int64_t ldA, double tau, double *E,
+                      void *ws, size_t ws_bytes, kron_stream_t stream);
+
+/*
+ * nsteps steps of u <- exp(tau (A_d (+) ... (+) A_1)) u, i.e. in tensor form
+ * U <- U x_1 E_1 x_2 ... x_d E_d with E_mu = exp(tau A_mu) (Eq. (exptucker)).
+ * The plan must be square (m == n) and unflagged; U (sizes n) is updated in
+ * place, stored with the plan's dtype.  A[mu] are FP64 device matrices with
+ * leading dimensions ldA[mu].  The E_mu are computed once per call by
+ * kron_expm (FP64); the steps use the plan's precision, split forms keeping
+ * the state in FP32 between steps and converting back at the end.
+ * kron_expkronsum_apply does the same with given E_mu (FP64, ld ldE[mu]).
+ */
+KRON_API kron_status kron_expkronsum_workspace_size(kron_plan plan, size_t *bytes);
+KRON_API kron_status kron_expkronsum_step(kron_plan plan, const double *const *A, const int64_t *ldA,
+                                 double tau, int nsteps, void *U, void *ws, size_t ws_bytes,
+                                 kron_stream_t stream);
+KRON_API kron_status kron_expkronsum_apply(kron_plan plan, const double *const *E, const int64_t *ldE,
+                                  int nsteps, void *U, void *ws, size_t ws_bytes,
+                                  kron_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batched Tucker operators (Section 3.2, Eq. (tensinterp); Section 4.3)     */
+/* ------------------------------------------------------------------------ */
+/*
+ * Many independent Tucker operators of possibly different sizes (same d,
+ * dtype, precision) in one persistent kernel launch.  The plan fixes the
+ * shapes; bind uploads the pointer tables of one set of operands into the
+ * workspace; run launches the work (one L-splitting launch and one persistent
+ * launch), so a bound run can be captured in a CUDA graph and replayed.
+ *   m, n     : host arrays batch*d (row b holds the sizes of problem b).
+ *   T[b]     : input of problem b;  S[b]: output;  L[b*d + mu]: L_mu of b,
+ *              dense with ld n (no transpose).
+ * Split precisions only (3XTF32, BF16X3, BF16X6).  1 <= batch <= 65536.
+ */
+typedef struct kron_batched_plan_s *kron_batched_plan;
+KRON_API kron_status kron_batched_plan_create(kron_batched_plan *plan, int batch, int d,
+                                     const int64_t *m, const int64_t *n, kron_dtype dtype,
+                                     kron_prec prec, unsigned flags);
+KRON_API kron_status kron_batched_plan_destroy(kron_batched_plan plan);
+KRON_API kron_status kron_batched_workspace_size(kron_batched_plan plan, size_t *bytes);
+KRON_API double kron_batched_flops(kron_batched_plan plan);
+KRON_API kron_status kron_batched_bind(kron_batched_plan plan, const void *const *T,
+                              const void *const *L, void *const *S, void *ws,
+                              size_t ws_bytes, kron_stream_t stream);
+KRON_API kron_status kron_batched_run(kron_batched_plan plan, void *ws, size_t ws_bytes,
+                             kron_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KRON_H */

@@ -1,0 +1,443 @@
+"""Python binding of libkron: mu-mode products and Tucker operators on GB300.
+
+A thin ctypes layer over the C ABI of ``include/kron.h``: it marshals torch
+tensors (device memory) and the current CUDA stream into the C calls and
+allocates workspaces with torch.  Every arithmetic step runs in libkron's
+kernels.  There is no CPU fallback: importing this package fails if
+``libkron.so`` has not been built (``python paper_2112_11238_gb300/build.py``).
+
+Layout convention (Appendix A, vec operator): tensors are column-major.  A
+torch tensor of shape (m_1, ..., m_d) is accepted when its strides are
+column-major (stride 1 along the first index); ``colmajor(t)`` returns such a
+copy, and outputs are allocated that way.  A matrix L of shape (n, m) needs
+stride 1 along its rows and a column stride ``ld >= n``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkron.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"libkron.so not found at {LIB_PATH}; build it with "
+        "`python paper_2112_11238_gb300/build.py` (nvcc, sm_103a)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# ---------------------------------------------------------------- C types
+KRON_OK = 0
+STATUS = {0: "KRON_OK", 1: "KRON_ERR_INVALID_ARG", 2: "KRON_ERR_UNSUPPORTED",
+          3: "KRON_ERR_ALIGNMENT", 4: "KRON_ERR_WORKSPACE", 5: "KRON_ERR_CUDA",
+          6: "KRON_ERR_TIMEOUT", 7: "KRON_ERR_NUMERIC"}
+F64, F32 = 0, 1
+PREC = {"fp64": 0, "fp32": 1, "3xtf32": 2, "bf16x3": 3, "bf16x6": 4}
+SPLIT_PRECS = ("3xtf32", "bf16x3", "bf16x6")
+PLAN_TRANS_L = 0x1
+PLAN_NATURAL_ORDER = 0x2
+MAX_D = 6
+
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+_ci = ctypes.c_int
+
+
+def _sig(name, args, res=ctypes.c_int):
+    f = getattr(_lib, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+_sig("kron_status_string", [_ci], ctypes.c_char_p)
+_sig("kron_version", [], _ci)
+_sig("kron_get_device_error", [ctypes.POINTER(_ci), _ci])
+_sig("kron_mump_workspace_size", [_ci, _i64p, _ci, ctypes.c_int64, _ci, _ci, ctypes.POINTER(_sz)])
+_sig("kron_mump", [_ci, _i64p, _ci, ctypes.c_int64, _vp, _vp, ctypes.c_int64, _ci, _vp, _ci, _ci, _vp, _sz, _vp])
+_sig("kron_plan_create", [ctypes.POINTER(_vp), _ci, _i64p, _i64p, _ci, _ci, ctypes.c_uint])
+_sig("kron_plan_destroy", [_vp])
+_sig("kron_plan_workspace_size", [_vp, ctypes.POINTER(_sz)])
+_sig("kron_plan_order", [_vp, ctypes.POINTER(_ci)])
+_sig("kron_plan_flops", [_vp], ctypes.c_double)
+_sig("kron_tucker", [_vp, _vp, ctypes.POINTER(_vp), _i64p, _vp, _vp, _sz, _vp])
+_sig("kron_adjoint_workspace_size", [_vp, ctypes.POINTER(_sz)])
+_sig("kron_tucker_adjoint", [_vp, _vp, ctypes.POINTER(_vp), _i64p, _vp, _vp, ctypes.POINTER(_vp), _vp, _sz, _vp])
+_sig("kron_expm_workspace_size", [ctypes.c_int64, ctypes.POINTER(_sz)])
+_sig("kron_expm", [ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_double, _vp, _vp, _sz, _vp])
+_sig("kron_expkronsum_workspace_size", [_vp, ctypes.POINTER(_sz)])
+_sig("kron_expkronsum_step", [_vp, ctypes.POINTER(_vp), _i64p, ctypes.c_double, _ci, _vp, _vp, _sz, _vp])
+_sig("kron_expkronsum_apply", [_vp, ctypes.POINTER(_vp), _i64p, _ci, _vp, _vp, _sz, _vp])
+_sig("kron_batched_plan_create", [ctypes.POINTER(_vp), _ci, _ci, _i64p, _i64p, _ci, _ci, ctypes.c_uint])
+_sig("kron_batched_plan_destroy", [_vp])
+_sig("kron_batched_workspace_size", [_vp, ctypes.POINTER(_sz)])
+_sig("kron_batched_flops", [_vp], ctypes.c_double)
+_sig("kron_batched_bind", [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, _sz, _vp])
+_sig("kron_batched_run", [_vp, _vp, _sz, _vp])
+
+EXPORTS = [
+    "kron_status_string", "kron_version", "kron_get_device_error", "kron_mump_workspace_size",
+    "kron_mump", "kron_plan_create", "kron_plan_destroy", "kron_plan_workspace_size",
+    "kron_plan_order", "kron_plan_flops", "kron_tucker", "kron_adjoint_workspace_size",
+    "kron_tucker_adjoint", "kron_expm_workspace_size", "kron_expm",
+    "kron_expkronsum_workspace_size", "kron_expkronsum_step", "kron_expkronsum_apply",
+    "kron_batched_plan_create", "kron_batched_plan_destroy", "kron_batched_workspace_size",
+    "kron_batched_flops", "kron_batched_bind", "kron_batched_run",
+]
+
+
+class KronError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != KRON_OK:
+        raise KronError(rc, what)
+
+
+def version() -> int:
+    return int(_lib.kron_version())
+
+
+def device_error(clear: bool = True) -> int:
+    """Synchronise and return (optionally clearing) the device error word."""
+    code = ctypes.c_int(0)
+    rc = _lib.kron_get_device_error(ctypes.byref(code), int(clear))
+    if rc not in (KRON_OK, 6, 7):
+        _check(rc, "kron_get_device_error")
+    return int(code.value)
+
+
+# ----------------------------------------------------------------- helpers
+
+def _i64(vals):
+    return (ctypes.c_int64 * len(vals))(*[int(v) for v in vals])
+
+
+def _ptrs(ts):
+    return (ctypes.c_void_p * len(ts))(*[t.data_ptr() if t is not None else None for t in ts])
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32:
+        return F32
+    raise TypeError(f"libkron supports float64 and float32 tensors, got {t.dtype}")
+
+
+def colmajor_strides(shape):
+    st, acc = [], 1
+    for s in shape:
+        st.append(acc)
+        acc *= max(int(s), 1)
+    return tuple(st)
+
+
+def is_colmajor(t: torch.Tensor) -> bool:
+    return all(t.stride(k) == s or t.shape[k] == 1
+               for k, s in enumerate(colmajor_strides(t.shape)))
+
+
+def colmajor(t: torch.Tensor) -> torch.Tensor:
+    """Copy (if needed) of t with column-major strides."""
+    if is_colmajor(t):
+        return t
+    out = torch.empty_strided(tuple(t.shape), colmajor_strides(t.shape), dtype=t.dtype, device=t.device)
+    out.copy_(t)
+    return out
+
+
+def empty_colmajor(shape, dtype, device) -> torch.Tensor:
+    return torch.empty_strided(tuple(int(s) for s in shape), colmajor_strides(shape), dtype=dtype, device=device)
+
+
+def _mat(L: torch.Tensor):
+    """(tensor, ld) of a column-major matrix, copying if its layout is not one."""
+    if L.dim() != 2:
+        raise ValueError("L must be a matrix")
+    if L.stride(0) != 1 or L.stride(1) < max(L.shape[0], 1):
+        L = colmajor(L)
+    return L, max(L.stride(1), L.shape[0], 1)
+
+
+def _prec(p) -> int:
+    if isinstance(p, int):
+        return p
+    return PREC[p.lower()]
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("libkron works on CUDA tensors only (no CPU fallback)")
+
+
+# --------------------------------------------------------------- mu-mode
+
+def mump_into(T: torch.Tensor, L: torch.Tensor, mu: int, S: torch.Tensor, trans: bool = False,
+              prec="fp64", ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """S = T x_mu op(L) (Eq. (mmp)) into a preallocated column-major S."""
+    _require_cuda(T, L, S)
+    L, ld = _mat(L)
+    d = T.dim()
+    m = list(T.shape)
+    n = L.shape[1] if trans else L.shape[0]
+    dt, pc = _dtype_code(T), _prec(prec)
+    need = ctypes.c_size_t(0)
+    _check(_lib.kron_mump_workspace_size(d, _i64(m), mu, n, dt, pc, ctypes.byref(need)), "kron_mump_workspace_size")
+    if ws is None or ws.numel() < need.value:
+        ws = _workspace(need.value, T.device)
+    _check(_lib.kron_mump(d, _i64(m), mu, n, T.data_ptr(), L.data_ptr(), ld, int(trans), S.data_ptr(), dt, pc,
+                          ws.data_ptr(), ws.numel(), _stream(stream)), "kron_mump")
+    return S
+
+
+def mump(T: torch.Tensor, L: torch.Tensor, mu: int, trans: bool = False, prec="fp64", stream=None) -> torch.Tensor:
+    """T x_mu op(L): op(L) applied to every mu-fibre of T (mu 0-based)."""
+    T = colmajor(T)
+    n = L.shape[1] if trans else L.shape[0]
+    shape = list(T.shape)
+    shape[mu] = n
+    S = empty_colmajor(shape, T.dtype, T.device)
+    return mump_into(T, L.to(T.dtype), mu, S, trans, prec, stream=stream)
+
+
+# ------------------------------------------------------------------ Tucker
+
+class TuckerPlan:
+    """A libkron plan: fixed d, sizes, dtype, precision and mode order."""
+
+    def __init__(self, m, n, dtype=torch.float64, prec="fp64", trans: bool = False,
+                 natural_order: bool = False):
+        self.m = [int(v) for v in m]
+        self.n = [int(v) for v in n]
+        self.d = len(self.m)
+        self.dtype = dtype
+        self.prec = prec
+        self.trans = trans
+        flags = (PLAN_TRANS_L if trans else 0) | (PLAN_NATURAL_ORDER if natural_order else 0)
+        h = ctypes.c_void_p()
+        dt = F64 if dtype == torch.float64 else F32
+        _check(_lib.kron_plan_create(ctypes.byref(h), self.d, _i64(self.m), _i64(self.n), dt, _prec(prec), flags),
+               "kron_plan_create")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.kron_plan_destroy(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def workspace_bytes(self) -> int:
+        b = ctypes.c_size_t(0)
+        _check(_lib.kron_plan_workspace_size(self._h, ctypes.byref(b)), "kron_plan_workspace_size")
+        return b.value
+
+    def adjoint_workspace_bytes(self) -> int:
+        b = ctypes.c_size_t(0)
+        _check(_lib.kron_adjoint_workspace_size(self._h, ctypes.byref(b)), "kron_adjoint_workspace_size")
+        return b.value
+
+    def stepper_workspace_bytes(self) -> int:
+        b = ctypes.c_size_t(0)
+        _check(_lib.kron_expkronsum_workspace_size(self._h, ctypes.byref(b)), "kron_expkronsum_workspace_size")
+        return b.value
+
+    def order(self):
+        o = (ctypes.c_int * self.d)()
+        _check(_lib.kron_plan_order(self._h, o), "kron_plan_order")
+        return list(o)
+
+    def flops(self) -> float:
+        return float(_lib.kron_plan_flops(self._h))
+
+    def workspace(self, device="cuda") -> torch.Tensor:
+        return _workspace(self.workspace_bytes(), device)
+
+    def tucker_into(self, T, Ls, S, ws=None, stream=None):
+        """S = T x_1 op(L_1) ... x_d op(L_d) with preallocated column-major S."""
+        _require_cuda(T, S, *Ls)
+        mats = [_mat(L) for L in Ls]
+        if ws is None:
+            ws = self.workspace(T.device)
+        _check(_lib.kron_tucker(self._h, T.data_ptr(), _ptrs([L for L, _ in mats]), _i64([ld for _, ld in mats]),
+                                S.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)), "kron_tucker")
+        return S
+
+    def adjoint_into(self, T, Ls, dS, dT=None, dLs=None, ws=None, stream=None):
+        mats = [_mat(L) for L in Ls]
+        if ws is None:
+            ws = _workspace(self.adjoint_workspace_bytes(), dS.device)
+        dLp = _ptrs(dLs) if dLs is not None else None
+        _check(_lib.kron_tucker_adjoint(self._h, T.data_ptr() if T is not None else None,
+                                        _ptrs([L for L, _ in mats]), _i64([ld for _, ld in mats]),
+                                        dS.data_ptr(), dT.data_ptr() if dT is not None else None, dLp,
+                                        ws.data_ptr(), ws.numel(), _stream(stream)), "kron_tucker_adjoint")
+        return dT, dLs
+
+
+def tucker(T: torch.Tensor, Ls, prec="fp64", trans: bool = False, natural_order: bool = False,
+           stream=None) -> torch.Tensor:
+    """Tucker operator T x_1 op(L_1) x_2 ... x_d op(L_d) (Eq. (tuckerop))."""
+    T = colmajor(T)
+    Ls = [L.to(T.dtype) for L in Ls]
+    n = [(L.shape[1] if trans else L.shape[0]) for L in Ls]
+    plan = TuckerPlan(T.shape, n, T.dtype, prec, trans, natural_order)
+    S = empty_colmajor(n, T.dtype, T.device)
+    return plan.tucker_into(T, Ls, S, stream=stream)
+
+
+def tucker_adjoint(T: torch.Tensor, Ls, dS: torch.Tensor, prec="fp64", want_dT: bool = True,
+                   want_dL: bool = True, stream=None):
+    """(dT, [dL_mu]) of <tucker(T, L), dS> (hand-written adjoint)."""
+    T = colmajor(T)
+    dS = colmajor(dS.to(T.dtype))
+    Ls = [L.to(T.dtype) for L in Ls]
+    plan = TuckerPlan(T.shape, [L.shape[0] for L in Ls], T.dtype, prec, natural_order=True)
+    dT = empty_colmajor(T.shape, T.dtype, T.device) if want_dT else None
+    dLs = [empty_colmajor(L.shape, T.dtype, T.device) for L in Ls] if want_dL else None
+    plan.adjoint_into(T, Ls, dS, dT, dLs, stream=stream)
+    return dT, dLs
+
+
+class KronTucker(torch.autograd.Function):
+    """S = tucker(T, L_1..L_d) with the hand-written adjoint as backward."""
+
+    @staticmethod
+    def forward(ctx, prec, T, *Ls):
+        T = colmajor(T)
+        Ls = [colmajor(L) for L in Ls]
+        ctx.prec = prec
+        ctx.save_for_backward(T, *Ls)
+        return tucker(T, Ls, prec=prec, natural_order=True)
+
+    @staticmethod
+    def backward(ctx, dS):
+        T, *Ls = ctx.saved_tensors
+        need_T = ctx.needs_input_grad[1]
+        need_L = any(ctx.needs_input_grad[2:])
+        dT, dLs = tucker_adjoint(T, Ls, dS, prec=ctx.prec, want_dT=need_T, want_dL=need_L)
+        grads = [None, dT]
+        grads += dLs if dLs is not None else [None] * len(Ls)
+        return tuple(grads)
+
+
+def tucker_autograd(T, Ls, prec="3xtf32"):
+    return KronTucker.apply(prec, T, *Ls)
+
+
+# ------------------------------------------------------------ exponential
+
+def expm(A: torch.Tensor, tau: float = 1.0, stream=None) -> torch.Tensor:
+    """exp(tau A) of a square FP64 CUDA matrix (Pade [13/13], scaling and squaring)."""
+    _require_cuda(A)
+    A, ld = _mat(A.to(torch.float64))
+    n = A.shape[0]
+    need = ctypes.c_size_t(0)
+    _check(_lib.kron_expm_workspace_size(n, ctypes.byref(need)), "kron_expm_workspace_size")
+    ws = _workspace(need.value, A.device)
+    E = empty_colmajor((n, n), torch.float64, A.device)
+    _check(_lib.kron_expm(n, A.data_ptr(), ld, float(tau), E.data_ptr(), ws.data_ptr(), ws.numel(),
+                          _stream(stream)), "kron_expm")
+    return E
+
+
+class StepperPlan:
+    """Exponential-of-Kronecker-sum stepper U <- U x_1 exp(tau A_1) ... (Eq. (exptucker))."""
+
+    def __init__(self, n, dtype=torch.float64, prec="3xtf32"):
+        self.plan = TuckerPlan(n, n, dtype, prec)
+        self.n = list(n)
+
+    def workspace(self, device="cuda"):
+        return _workspace(self.plan.stepper_workspace_bytes(), device)
+
+    def step(self, U, As, tau: float, nsteps: int, ws=None, stream=None):
+        """nsteps steps in place on the column-major tensor U; A_mu FP64 matrices."""
+        _require_cuda(U, *As)
+        mats = [_mat(A) for A in As]
+        if ws is None:
+            ws = self.workspace(U.device)
+        _check(_lib.kron_expkronsum_step(self.plan.handle, _ptrs([A for A, _ in mats]),
+                                         _i64([ld for _, ld in mats]), float(tau), int(nsteps), U.data_ptr(),
+                                         ws.data_ptr(), ws.numel(), _stream(stream)), "kron_expkronsum_step")
+        return U
+
+    def apply(self, U, Es, nsteps: int, ws=None, stream=None):
+        """nsteps steps with given FP64 E_mu = exp(tau A_mu)."""
+        _require_cuda(U, *Es)
+        mats = [_mat(E) for E in Es]
+        if ws is None:
+            ws = self.workspace(U.device)
+        _check(_lib.kron_expkronsum_apply(self.plan.handle, _ptrs([E for E, _ in mats]),
+                                          _i64([ld for _, ld in mats]), int(nsteps), U.data_ptr(),
+                                          ws.data_ptr(), ws.numel(), _stream(stream)), "kron_expkronsum_apply")
+        return U
+
+
+def expkronsum_step(U: torch.Tensor, As, tau: float, nsteps: int, prec="3xtf32", stream=None) -> torch.Tensor:
+    """Returns U after nsteps steps of exp(tau (A_d (+) ... (+) A_1)) (a new tensor)."""
+    U = colmajor(U).clone()
+    StepperPlan(U.shape, U.dtype, prec).step(U, [A.to(torch.float64) for A in As], tau, nsteps, stream=stream)
+    return U
+
+
+# ----------------------------------------------------------------- batched
+
+class BatchedPlan:
+    """Many independent Tucker operators (same d) in one persistent launch."""
+
+    def __init__(self, m, n, dtype=torch.float32, prec="3xtf32"):
+        import numpy as np
+        m = np.asarray(m, dtype=np.int64)
+        n = np.asarray(n, dtype=np.int64)
+        self.batch, self.d = m.shape
+        self.m, self.n = m, n
+        h = ctypes.c_void_p()
+        dt = F64 if dtype == torch.float64 else F32
+        _check(_lib.kron_batched_plan_create(ctypes.byref(h), self.batch, self.d, _i64(m.ravel()),
+                                             _i64(n.ravel()), dt, _prec(prec), 0), "kron_batched_plan_create")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.kron_batched_plan_destroy(h)
+            self._h = None
+
+    def workspace(self, device="cuda"):
+        b = ctypes.c_size_t(0)
+        _check(_lib.kron_batched_workspace_size(self._h, ctypes.byref(b)), "kron_batched_workspace_size")
+        return _workspace(b.value, device)
+
+    def flops(self) -> float:
+        return float(_lib.kron_batched_flops(self._h))
+
+    def bind(self, Ts, Ls, Ss, ws, stream=None):
+        """Uploads the pointer tables; Ls is a list (per problem) of d matrices (ld = n)."""
+        flatL = [L for row in Ls for L in row]
+        _check(_lib.kron_batched_bind(self._h, _ptrs(Ts), _ptrs(flatL), _ptrs(Ss), ws.data_ptr(), ws.numel(),
+                                      _stream(stream)), "kron_batched_bind")
+
+    def run(self, ws, stream=None):
+        _check(_lib.kron_batched_run(self._h, ws.data_ptr(), ws.numel(), _stream(stream)), "kron_batched_run")

@@ -1,0 +1,731 @@
+// api.cu -- the extern "C" boundary of libkron (declared in include/kron.h):
+// argument validation, plans, workspace layout, and the host drivers of the
+// mu-mode product, the Tucker chain, its adjoint and the exponential stepper.
+// Every step of the computation runs in the kernels of tc.cu / simt.cu /
+// expm.cu / batched.cu; this file only decides what to launch.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using namespace kron;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+kron_status cuda_status(cudaError_t e) { return e == cudaSuccess ? KRON_OK : KRON_ERR_CUDA; }
+
+bool valid_dtype(kron_dtype t) { return t == KRON_F64 || t == KRON_F32; }
+bool valid_prec(kron_prec p) { return p >= KRON_PREC_FP64 && p <= KRON_PREC_BF16X6; }
+size_t esize(kron_dtype t) { return t == KRON_F64 ? 8 : 4; }
+
+// Element size of the intermediates of a precision.
+size_t inter_size(kron_prec p) { return p == KRON_PREC_FP64 ? 8 : 4; }
+
+int64_t prod(const int64_t *v, int lo, int hi) {
+    int64_t p = 1;
+    for (int k = lo; k < hi; ++k) p *= v[k];
+    return p;
+}
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Geometry of one mu-mode product inside a chain: the input has sizes cur[],
+// mode mu (0-based) of size m is mapped to n.
+struct ModeGeom {
+    int64_t P, Q, m, n;
+};
+
+ModeGeom mode_geom(int d, const int64_t *cur, int mu, int64_t n) {
+    return ModeGeom{prod(cur, 0, mu), prod(cur, mu + 1, d), cur[mu], n};
+}
+
+// Contraction of a mu-mode product for the tensor-core path: rows are the
+// fibres (p, q) of the tensor, columns the n outputs of a fibre, k the mode.
+Contraction tc_mode_contraction(const ModeGeom &g, const void *src, bool src64, const void *L,
+                                bool L64, int64_t ldL, bool transL, void *dst, bool dst64) {
+    Contraction c;
+    c.M = g.P * g.Q;
+    c.N = g.n;
+    c.K = g.m;
+    c.A = src;
+    c.A_f64 = src64;
+    if (g.P == 1) {
+        c.rowA = IdxMap{0, g.m, 0};
+        c.rowC = IdxMap{0, g.n, 0};
+    } else {
+        c.rowA = IdxMap{g.P, 1, g.P * g.m};
+        c.rowC = IdxMap{g.P, 1, g.P * g.n};
+    }
+    c.kA = IdxMap{0, g.P, 0};
+    c.B = L;
+    c.B_f64 = L64;
+    if (!transL) {
+        c.colB = IdxMap{0, 1, 0};
+        c.kB = IdxMap{0, ldL, 0};
+    } else {
+        c.colB = IdxMap{0, ldL, 0};
+        c.kB = IdxMap{0, 1, 0};
+    }
+    c.C = dst;
+    c.C_f64 = dst64;
+    c.colC = IdxMap{0, g.P, 0};
+    return c;
+}
+
+// Contraction of a mu-mode product for the CUDA-core path.  For mu with
+// P == 1 the roles are swapped (rows = outputs of a fibre, columns = fibres)
+// so that both loads and stores stay contiguous.
+Contraction simt_mode_contraction(const ModeGeom &g, const void *src, bool src64, const void *L,
+                                  bool L64, int64_t ldL, bool transL, void *dst, bool dst64) {
+    if (g.P != 1) return tc_mode_contraction(g, src, src64, L, L64, ldL, transL, dst, dst64);
+    Contraction c;
+    c.M = g.n;
+    c.N = g.Q;
+    c.K = g.m;
+    c.A = L;
+    c.A_f64 = L64;
+    if (!transL) {
+        c.rowA = IdxMap{0, 1, 0};
+        c.kA = IdxMap{0, ldL, 0};
+    } else {
+        c.rowA = IdxMap{0, ldL, 0};
+        c.kA = IdxMap{0, 1, 0};
+    }
+    c.B = src;
+    c.B_f64 = src64;
+    c.colB = IdxMap{0, g.m, 0};
+    c.kB = IdxMap{0, 1, 0};
+    c.C = dst;
+    c.C_f64 = dst64;
+    c.rowC = IdxMap{0, 1, 0};
+    c.colC = IdxMap{0, g.n, 0};
+    return c;
+}
+
+kron_status check_shape(int d, const int64_t *m, const int64_t *n) {
+    if (d < 1 || d > KRON_MAX_D || !m || !n) return KRON_ERR_INVALID_ARG;
+    long double in = 1, out = 1;
+    for (int k = 0; k < d; ++k) {
+        if (m[k] < 1 || n[k] < 1) return KRON_ERR_INVALID_ARG;
+        in *= (long double)m[k];
+        out *= (long double)n[k];
+    }
+    // every intermediate is bounded by prod(max(m, n))
+    long double mx = 1;
+    for (int k = 0; k < d; ++k) mx *= (long double)std::max(m[k], n[k]);
+    if (mx > (long double)(1ll << 40)) return KRON_ERR_UNSUPPORTED;
+    (void)in;
+    (void)out;
+    return KRON_OK;
+}
+
+}  // namespace
+
+struct kron_plan_s {
+    int d;
+    int64_t m[KRON_MAX_D], n[KRON_MAX_D];
+    kron_dtype dtype;
+    kron_prec prec;
+    unsigned flags;
+    int order[KRON_MAX_D];
+    // workspace layout of kron_tucker
+    size_t img_off[KRON_MAX_D], img_bytes[KRON_MAX_D];
+    size_t buf_off[2], buf_bytes;
+    size_t ws_bytes;
+};
+
+namespace {
+
+// Applies the chain of the plan in its order.  src (dtype of the plan) ->
+// dst (dtype); intermediates in ws buffers.  Images of the split L live in
+// ws at the plan's offsets.
+kron_status run_chain(const kron_plan_s *pl, const void *T, const void *const *L, const int64_t *ldL,
+                      void *S, uint8_t *ws, cudaStream_t st, bool trans) {
+    const int d = pl->d;
+    const bool io64 = pl->dtype == KRON_F64;
+    const bool split = is_split(pl->prec);
+    const int form = form_of(pl->prec);
+    const bool i64 = pl->prec == KRON_PREC_FP64;
+    int64_t cur[KRON_MAX_D];
+    for (int k = 0; k < d; ++k) cur[k] = pl->m[k];
+    const void *src = T;
+    bool src64 = io64;
+    for (int s = 0; s < d; ++s) {
+        const int mu = pl->order[s];
+        const ModeGeom g = mode_geom(d, cur, mu, pl->n[mu]);
+        const bool last = (s == d - 1);
+        void *dst = last ? S : (void *)(ws + pl->buf_off[s & 1]);
+        const bool dst64 = last ? io64 : (split ? false : i64);
+        cudaError_t e;
+        if (split) {
+            Contraction c = tc_mode_contraction(g, src, src64, L[mu], io64, ldL[mu], trans, dst, dst64);
+            void *img = ws + pl->img_off[mu];
+            e = tc_build_bimage(form, c, img, st);
+            if (e == cudaSuccess) e = tc_contract_bimage(form, c, img, st);
+        } else {
+            Contraction c =
+                simt_mode_contraction(g, src, src64, L[mu], io64, ldL[mu], trans, dst, dst64);
+            e = simt_contract(i64, c, st);
+        }
+        if (e != cudaSuccess) return KRON_ERR_CUDA;
+        cur[mu] = pl->n[mu];
+        src = dst;
+        src64 = dst64;
+    }
+    return KRON_OK;
+}
+
+void plan_layout(kron_plan_s *pl) {
+    const int d = pl->d;
+    size_t off = 0;
+    const int form = form_of(pl->prec);
+    for (int k = 0; k < d; ++k) {
+        pl->img_off[k] = off;
+        pl->img_bytes[k] = form >= 0 ? tc_bimage_bytes(form, pl->n[k], pl->m[k]) : 0;
+        off += align_up(pl->img_bytes[k]);
+    }
+    // largest intermediate (outputs of steps 0..d-2)
+    int64_t cur[KRON_MAX_D];
+    for (int k = 0; k < d; ++k) cur[k] = pl->m[k];
+    int64_t mx = 0;
+    for (int s = 0; s < d - 1; ++s) {
+        cur[pl->order[s]] = pl->n[pl->order[s]];
+        mx = std::max(mx, prod(cur, 0, d));
+    }
+    pl->buf_bytes = align_up((size_t)mx * inter_size(pl->prec));
+    pl->buf_off[0] = off;
+    pl->buf_off[1] = off + pl->buf_bytes;
+    off += 2 * pl->buf_bytes;
+    pl->ws_bytes = std::max<size_t>(off, kAlign);
+}
+
+void choose_order(kron_plan_s *pl) {
+    const int d = pl->d;
+    int perm[KRON_MAX_D];
+    for (int k = 0; k < d; ++k) perm[k] = pl->order[k] = k;
+    if (pl->flags & KRON_PLAN_NATURAL_ORDER) return;
+    long double best = -1;
+    do {
+        int64_t cur[KRON_MAX_D];
+        for (int k = 0; k < d; ++k) cur[k] = pl->m[k];
+        long double fl = 0;
+        for (int s = 0; s < d; ++s) {
+            const int mu = perm[s];
+            fl += 2.0L * pl->n[mu] * (long double)prod(cur, 0, d);
+            cur[mu] = pl->n[mu];
+        }
+        if (best < 0 || fl < best * (1 - 1e-12L)) {
+            best = fl;
+            for (int k = 0; k < d; ++k) pl->order[k] = perm[k];
+        }
+    } while (std::next_permutation(perm, perm + d));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *kron_status_string(kron_status s) {
+    switch (s) {
+        case KRON_OK: return "KRON_OK";
+        case KRON_ERR_INVALID_ARG: return "KRON_ERR_INVALID_ARG";
+        case KRON_ERR_UNSUPPORTED: return "KRON_ERR_UNSUPPORTED";
+        case KRON_ERR_ALIGNMENT: return "KRON_ERR_ALIGNMENT";
+        case KRON_ERR_WORKSPACE: return "KRON_ERR_WORKSPACE";
+        case KRON_ERR_CUDA: return "KRON_ERR_CUDA";
+        case KRON_ERR_TIMEOUT: return "KRON_ERR_TIMEOUT";
+        case KRON_ERR_NUMERIC: return "KRON_ERR_NUMERIC";
+    }
+    return "KRON_ERR_UNKNOWN";
+}
+
+int kron_version(void) { return 100; }
+
+kron_status kron_get_device_error(int *code, int clear) {
+    if (!code) return KRON_ERR_INVALID_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) return KRON_ERR_CUDA;
+    unsigned a = 0, b = 0, c = 0;
+    if (tc_error_word(&a, clear != 0) != cudaSuccess) return KRON_ERR_CUDA;
+    if (expm_error_word(&b, clear != 0) != cudaSuccess) return KRON_ERR_CUDA;
+    if (batched_error_word(&c, clear != 0) != cudaSuccess) return KRON_ERR_CUDA;
+    const unsigned w = a | b | c;
+    *code = (int)w;
+    if (w & 1u) return KRON_ERR_TIMEOUT;
+    if (w & 2u) return KRON_ERR_NUMERIC;
+    return KRON_OK;
+}
+
+// ------------------------------------------------------------ mu-mode product
+
+kron_status kron_mump_workspace_size(int d, const int64_t *m, int mu, int64_t n, kron_dtype dtype,
+                                     kron_prec prec, size_t *bytes) {
+    if (!bytes || !valid_dtype(dtype) || !valid_prec(prec)) return KRON_ERR_INVALID_ARG;
+    if (d < 1 || d > KRON_MAX_D || !m || mu < 0 || mu >= d || n < 1) return KRON_ERR_INVALID_ARG;
+    for (int k = 0; k < d; ++k)
+        if (m[k] < 1) return KRON_ERR_INVALID_ARG;
+    const int form = form_of(prec);
+    *bytes = align_up(form >= 0 ? tc_bimage_bytes(form, n, m[mu]) : 0);
+    if (*bytes == 0) *bytes = kAlign;
+    return KRON_OK;
+}
+
+kron_status kron_mump(int d, const int64_t *m, int mu, int64_t n, const void *T, const void *L,
+                      int64_t ldL, int transL, void *S, kron_dtype dtype, kron_prec prec, void *ws,
+                      size_t ws_bytes, kron_stream_t stream) {
+    size_t need = 0;
+    kron_status st = kron_mump_workspace_size(d, m, mu, n, dtype, prec, &need);
+    if (st != KRON_OK) return st;
+    if (!T || !L || !S) return KRON_ERR_INVALID_ARG;
+    if (transL ? ldL < m[mu] : ldL < n) return KRON_ERR_INVALID_ARG;
+    const size_t es = esize(dtype);
+    if (!aligned(T, es) || !aligned(L, es) || !aligned(S, es)) return KRON_ERR_ALIGNMENT;
+    if (is_split(prec)) {
+        if (!ws) return KRON_ERR_INVALID_ARG;
+        if (!aligned(ws, kAlign)) return KRON_ERR_ALIGNMENT;
+        if (ws_bytes < need) return KRON_ERR_WORKSPACE;
+    }
+    const ModeGeom g = mode_geom(d, m, mu, n);
+    const bool io64 = dtype == KRON_F64;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (is_split(prec)) {
+        const int form = form_of(prec);
+        Contraction c = tc_mode_contraction(g, T, io64, L, io64, ldL, transL != 0, S, io64);
+        e = tc_build_bimage(form, c, ws, cs);
+        if (e == cudaSuccess) e = tc_contract_bimage(form, c, ws, cs);
+    } else {
+        Contraction c = simt_mode_contraction(g, T, io64, L, io64, ldL, transL != 0, S, io64);
+        e = simt_contract(prec == KRON_PREC_FP64, c, cs);
+    }
+    return cuda_status(e);
+}
+
+// ------------------------------------------------------------------- plans
+
+kron_status kron_plan_create(kron_plan *plan, int d, const int64_t *m, const int64_t *n, kron_dtype dtype,
+                             kron_prec prec, unsigned flags) {
+    if (!plan) return KRON_ERR_INVALID_ARG;
+    *plan = nullptr;
+    if (!valid_dtype(dtype) || !valid_prec(prec)) return KRON_ERR_INVALID_ARG;
+    if (flags & ~(KRON_PLAN_TRANS_L | KRON_PLAN_NATURAL_ORDER)) return KRON_ERR_INVALID_ARG;
+    kron_status st = check_shape(d, m, n);
+    if (st != KRON_OK) return st;
+    auto *pl = new (std::nothrow) kron_plan_s();
+    if (!pl) return KRON_ERR_INVALID_ARG;
+    pl->d = d;
+    for (int k = 0; k < d; ++k) {
+        pl->m[k] = m[k];
+        pl->n[k] = n[k];
+    }
+    pl->dtype = dtype;
+    pl->prec = prec;
+    pl->flags = flags;
+    choose_order(pl);
+    plan_layout(pl);
+    *plan = pl;
+    return KRON_OK;
+}
+
+kron_status kron_plan_destroy(kron_plan plan) {
+    delete plan;
+    return KRON_OK;
+}
+
+kron_status kron_plan_workspace_size(kron_plan plan, size_t *bytes) {
+    if (!plan || !bytes) return KRON_ERR_INVALID_ARG;
+    *bytes = plan->ws_bytes;
+    return KRON_OK;
+}
+
+kron_status kron_plan_order(kron_plan plan, int *order) {
+    if (!plan || !order) return KRON_ERR_INVALID_ARG;
+    for (int k = 0; k < plan->d; ++k) order[k] = plan->order[k];
+    return KRON_OK;
+}
+
+double kron_plan_flops(kron_plan plan) {
+    if (!plan) return 0.0;
+    int64_t cur[KRON_MAX_D];
+    for (int k = 0; k < plan->d; ++k) cur[k] = plan->m[k];
+    double fl = 0;
+    for (int s = 0; s < plan->d; ++s) {
+        const int mu = plan->order[s];
+        fl += 2.0 * (double)plan->n[mu] * (double)prod(cur, 0, plan->d);
+        cur[mu] = plan->n[mu];
+    }
+    return fl;
+}
+
+static kron_status check_L(const kron_plan_s *pl, const void *const *L, const int64_t *ldL, bool trans) {
+    if (!L || !ldL) return KRON_ERR_INVALID_ARG;
+    const size_t es = esize(pl->dtype);
+    for (int k = 0; k < pl->d; ++k) {
+        if (!L[k]) return KRON_ERR_INVALID_ARG;
+        if (!aligned(L[k], es)) return KRON_ERR_ALIGNMENT;
+        if (trans ? ldL[k] < pl->m[k] : ldL[k] < pl->n[k]) return KRON_ERR_INVALID_ARG;
+    }
+    return KRON_OK;
+}
+
+static kron_status check_ws(const void *ws, size_t ws_bytes, size_t need) {
+    if (need > 0 && !ws) return KRON_ERR_INVALID_ARG;
+    if (ws && !aligned(ws, kAlign)) return KRON_ERR_ALIGNMENT;
+    if (ws_bytes < need) return KRON_ERR_WORKSPACE;
+    return KRON_OK;
+}
+
+kron_status kron_tucker(kron_plan plan, const void *T, const void *const *L, const int64_t *ldL, void *S,
+                        void *ws, size_t ws_bytes, kron_stream_t stream) {
+    if (!plan || !T || !S) return KRON_ERR_INVALID_ARG;
+    const bool trans = (plan->flags & KRON_PLAN_TRANS_L) != 0;
+    kron_status st = check_L(plan, L, ldL, trans);
+    if (st != KRON_OK) return st;
+    const size_t es = esize(plan->dtype);
+    if (!aligned(T, es) || !aligned(S, es)) return KRON_ERR_ALIGNMENT;
+    st = check_ws(ws, ws_bytes, plan->ws_bytes);
+    if (st != KRON_OK) return st;
+    return run_chain(plan, T, L, ldL, S, static_cast<uint8_t *>(ws),
+                     reinterpret_cast<cudaStream_t>(stream), trans);
+}
+
+// ----------------------------------------------------------------- adjoint
+//
+// Workspace: [img fwd x d][img trans x d][X0][X1][G0][G1][partial]
+namespace {
+struct AdjLayout {
+    size_t img_f[KRON_MAX_D], img_t[KRON_MAX_D];
+    size_t x[2], g[2], partial, total;
+    size_t xbytes, gbytes;
+};
+
+AdjLayout adjoint_layout(const kron_plan_s *pl) {
+    AdjLayout a{};
+    const int d = pl->d;
+    const int form = form_of(pl->prec);
+    const size_t isz = inter_size(pl->prec);
+    size_t off = 0;
+    for (int k = 0; k < d; ++k) {
+        a.img_f[k] = off;
+        off += align_up(form >= 0 ? tc_bimage_bytes(form, pl->n[k], pl->m[k]) : 0);
+        a.img_t[k] = off;
+        off += align_up(form >= 0 ? tc_bimage_bytes(form, pl->m[k], pl->n[k]) : 0);
+    }
+    // X_mu (mu >= 1): sizes n_1..n_{mu-1}, m_mu..m_d ; G_mu: n_1..n_{mu-1}, m_mu.. and n_mu..
+    int64_t mx = 1;
+    int64_t cur[KRON_MAX_D];
+    for (int k = 0; k < d; ++k) cur[k] = pl->m[k];
+    for (int s = 0; s <= d; ++s) {
+        mx = std::max(mx, prod(cur, 0, d));
+        if (s < d) cur[s] = pl->n[s];
+    }
+    a.xbytes = a.gbytes = align_up((size_t)mx * isz);
+    a.x[0] = off; off += a.xbytes;
+    a.x[1] = off; off += a.xbytes;
+    a.g[0] = off; off += a.gbytes;
+    a.g[1] = off; off += a.gbytes;
+    size_t pb = 0;
+    for (int mu = 0; mu < d; ++mu) {
+        // dL_mu contraction: M = n_mu, N = m_mu, K = prod of the others
+        int64_t K = 1;
+        for (int k = 0; k < mu; ++k) K *= pl->n[k];
+        for (int k = mu + 1; k < d; ++k) K *= pl->m[k];
+        const size_t b = form >= 0 ? tc_splitk_partial_bytes(pl->n[mu], pl->m[mu], K)
+                                   : simt_splitk_partial_bytes(pl->prec == KRON_PREC_FP64, pl->n[mu],
+                                                               pl->m[mu], K);
+        pb = std::max(pb, b);
+    }
+    a.partial = off;
+    off += align_up(pb);
+    a.total = std::max<size_t>(off, kAlign);
+    return a;
+}
+
+// One mode product inside the adjoint (either path).
+cudaError_t adj_mode(const kron_plan_s *pl, const ModeGeom &g, const void *src, bool src64, const void *L,
+                     int64_t ldL, bool trans, void *dst, bool dst64, uint8_t *img, cudaStream_t st) {
+    const bool io64 = pl->dtype == KRON_F64;
+    if (is_split(pl->prec)) {
+        const int form = form_of(pl->prec);
+        Contraction c = tc_mode_contraction(g, src, src64, L, io64, ldL, trans, dst, dst64);
+        cudaError_t e = tc_build_bimage(form, c, img, st);
+        if (e != cudaSuccess) return e;
+        return tc_contract_bimage(form, c, img, st);
+    }
+    Contraction c = simt_mode_contraction(g, src, src64, L, io64, ldL, trans, dst, dst64);
+    return simt_contract(pl->prec == KRON_PREC_FP64, c, st);
+}
+}  // namespace
+
+kron_status kron_adjoint_workspace_size(kron_plan plan, size_t *bytes) {
+    if (!plan || !bytes) return KRON_ERR_INVALID_ARG;
+    *bytes = adjoint_layout(plan).total;
+    return KRON_OK;
+}
+
+kron_status kron_tucker_adjoint(kron_plan plan, const void *T, const void *const *L, const int64_t *ldL,
+                                const void *dS, void *dT, void *const *dL, void *ws, size_t ws_bytes,
+                                kron_stream_t stream) {
+    if (!plan || !dS) return KRON_ERR_INVALID_ARG;
+    if (plan->flags & KRON_PLAN_TRANS_L) return KRON_ERR_UNSUPPORTED;
+    kron_status st = check_L(plan, L, ldL, false);
+    if (st != KRON_OK) return st;
+    const int d = plan->d;
+    bool want_dL = false;
+    if (dL)
+        for (int k = 0; k < d; ++k) want_dL |= dL[k] != nullptr;
+    if (want_dL && !T) return KRON_ERR_INVALID_ARG;
+    const size_t es = esize(plan->dtype);
+    if (!aligned(dS, es) || (dT && !aligned(dT, es)) || (T && !aligned(T, es))) return KRON_ERR_ALIGNMENT;
+    if (dL)
+        for (int k = 0; k < d; ++k)
+            if (dL[k] && !aligned(dL[k], es)) return KRON_ERR_ALIGNMENT;
+    const AdjLayout lay = adjoint_layout(plan);
+    st = check_ws(ws, ws_bytes, lay.total);
+    if (st != KRON_OK) return st;
+    auto *w = static_cast<uint8_t *>(ws);
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    const bool io64 = plan->dtype == KRON_F64;
+    const bool i64 = plan->prec == KRON_PREC_FP64;
+    const bool split = is_split(plan->prec);
+    const int form = form_of(plan->prec);
+
+    // G holds the cotangent of X_{mu+1}; sizes gcur.
+    int64_t gcur[KRON_MAX_D];
+    for (int k = 0; k < d; ++k) gcur[k] = plan->n[k];
+    const void *G = dS;
+    bool G64 = io64;
+    int gsel = 0;
+    for (int mu = d - 1; mu >= 0; --mu) {
+        if (dL && dL[mu]) {
+            // X_mu = T x_1 L_1 ... x_{mu-1} L_{mu-1}, recomputed from T
+            int64_t xcur[KRON_MAX_D];
+            for (int k = 0; k < d; ++k) xcur[k] = plan->m[k];
+            const void *X = T;
+            bool X64 = io64;
+            for (int nu = 0; nu < mu; ++nu) {
+                const ModeGeom g = mode_geom(d, xcur, nu, plan->n[nu]);
+                void *dst = w + lay.x[nu & 1];
+                if (adj_mode(plan, g, X, X64, L[nu], ldL[nu], false, dst, i64, w + lay.img_f[nu], cs) !=
+                    cudaSuccess)
+                    return KRON_ERR_CUDA;
+                xcur[nu] = plan->n[nu];
+                X = dst;
+                X64 = i64;
+            }
+            // dL_mu(i, j) = sum_{p,q} G(p, i, q) X(p, j, q): M = n_mu, N = m_mu
+            const int64_t P = prod(xcur, 0, mu), Q = prod(xcur, mu + 1, d);
+            const int64_t nm = plan->n[mu], mm = plan->m[mu];
+            Contraction c;
+            c.M = nm;
+            c.N = mm;
+            c.K = P * Q;
+            c.A = G;
+            c.A_f64 = G64;
+            c.rowA = IdxMap{0, P, 0};
+            c.kA = (P == 1) ? IdxMap{0, nm, 0} : IdxMap{P, 1, P * nm};
+            c.B = X;
+            c.B_f64 = X64;
+            c.colB = IdxMap{0, P, 0};
+            c.kB = (P == 1) ? IdxMap{0, mm, 0} : IdxMap{P, 1, P * mm};
+            c.C = dL[mu];
+            c.C_f64 = io64;
+            c.rowC = IdxMap{0, 1, 0};
+            c.colC = IdxMap{0, nm, 0};
+            cudaError_t e = split ? tc_contract_splitk(form, c, reinterpret_cast<float *>(w + lay.partial), cs)
+                                  : simt_contract_splitk(i64, c, w + lay.partial, cs);
+            if (e != cudaSuccess) return KRON_ERR_CUDA;
+        }
+        if (mu == 0 && !dT) break;
+        // G_mu = G_{mu+1} x_mu L_mu^T
+        const ModeGeom g = mode_geom(d, gcur, mu, plan->m[mu]);
+        const bool lastg = (mu == 0);
+        void *dst = lastg ? dT : (void *)(w + lay.g[gsel]);
+        const bool dst64 = lastg ? io64 : i64;
+        if (adj_mode(plan, g, G, G64, L[mu], ldL[mu], true, dst, dst64, w + lay.img_t[mu], cs) != cudaSuccess)
+            return KRON_ERR_CUDA;
+        gcur[mu] = plan->m[mu];
+        G = dst;
+        G64 = dst64;
+        gsel ^= 1;
+    }
+    return KRON_OK;
+}
+
+// ------------------------------------------------------- matrix exponential
+
+kron_status kron_expm_workspace_size(int64_t n, size_t *bytes) {
+    if (!bytes || n < 1 || n > 1024) return KRON_ERR_INVALID_ARG;
+    *bytes = align_up(expm_workspace_bytes(n));
+    return KRON_OK;
+}
+
+kron_status kron_expm(int64_t n, const double *A, int64_t ldA, double tau, double *E, void *ws,
+                      size_t ws_bytes, kron_stream_t stream) {
+    size_t need = 0;
+    kron_status st = kron_expm_workspace_size(n, &need);
+    if (st != KRON_OK) return st;
+    if (!A || !E || ldA < n) return KRON_ERR_INVALID_ARG;
+    if (!aligned(A, 8) || !aligned(E, 8)) return KRON_ERR_ALIGNMENT;
+    st = check_ws(ws, ws_bytes, need);
+    if (st != KRON_OK) return st;
+    return cuda_status(expm_pade13(n, A, ldA, tau, E, ws, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+// ------------------------------------------------ exponential-of-Kronecker-sum stepper
+//
+// Workspace: [expm ws][E_0..E_{d-1} (FP64)][images x d][state0][state1]
+namespace {
+struct StepLayout {
+    size_t expm, E[KRON_MAX_D], img[KRON_MAX_D], st[2], stbytes, total;
+};
+
+StepLayout step_layout(const kron_plan_s *pl) {
+    StepLayout s{};
+    size_t off = 0;
+    int64_t nmax = 1;
+    for (int k = 0; k < pl->d; ++k) nmax = std::max(nmax, pl->n[k]);
+    s.expm = off;
+    off += align_up(expm_workspace_bytes(nmax));
+    for (int k = 0; k < pl->d; ++k) {
+        s.E[k] = off;
+        off += align_up((size_t)pl->n[k] * pl->n[k] * 8);
+    }
+    const int form = form_of(pl->prec);
+    for (int k = 0; k < pl->d; ++k) {
+        s.img[k] = off;
+        off += align_up(form >= 0 ? tc_bimage_bytes(form, pl->n[k], pl->n[k]) : 0);
+    }
+    s.stbytes = align_up((size_t)prod(pl->n, 0, pl->d) * std::max(inter_size(pl->prec), esize(pl->dtype)));
+    s.st[0] = off;
+    off += s.stbytes;
+    s.st[1] = off;
+    off += s.stbytes;
+    s.total = off;
+    return s;
+}
+
+kron_status check_step_plan(const kron_plan_s *pl) {
+    if (pl->flags & KRON_PLAN_TRANS_L) return KRON_ERR_UNSUPPORTED;
+    for (int k = 0; k < pl->d; ++k)
+        if (pl->m[k] != pl->n[k]) return KRON_ERR_INVALID_ARG;
+    return KRON_OK;
+}
+
+kron_status run_steps(const kron_plan_s *pl, const double *const *E, const int64_t *ldE, int nsteps, void *U,
+                      uint8_t *w, const StepLayout &lay, cudaStream_t cs) {
+    const int d = pl->d;
+    const bool io64 = pl->dtype == KRON_F64;
+    const bool split = is_split(pl->prec);
+    const int form = form_of(pl->prec);
+    const bool i64 = pl->prec == KRON_PREC_FP64;
+    const int total = nsteps * d;
+    if (total == 0) return KRON_OK;
+    // Images of the split E_mu, built once for all steps.
+    if (split) {
+        for (int k = 0; k < d; ++k) {
+            const ModeGeom g{1, 1, pl->n[k], pl->n[k]};
+            Contraction c = tc_mode_contraction(g, nullptr, false, E[k], true, ldE[k], false, nullptr, false);
+            if (tc_build_bimage(form, c, w + lay.img[k], cs) != cudaSuccess) return KRON_ERR_CUDA;
+        }
+    }
+    const void *src = U;
+    bool src64 = io64;
+    int sel = 0;
+    int idx = 0;
+    for (int s = 0; s < nsteps; ++s) {
+        for (int j = 0; j < d; ++j, ++idx) {
+            const int mu = pl->order[j];
+            const ModeGeom g = mode_geom(d, pl->n, mu, pl->n[mu]);
+            const bool last = (idx == total - 1);
+            // a single contraction would read and write U: go through a buffer
+            const bool via_buf = last && total == 1;
+            void *dst = (last && !via_buf) ? U : (void *)(w + lay.st[sel]);
+            const bool dst64 = last ? io64 : i64;
+            cudaError_t e;
+            if (split) {
+                Contraction c = tc_mode_contraction(g, src, src64, E[mu], true, ldE[mu], false, dst, dst64);
+                e = tc_contract_bimage(form, c, w + lay.img[mu], cs);
+            } else {
+                Contraction c = simt_mode_contraction(g, src, src64, E[mu], true, ldE[mu], false, dst, dst64);
+                e = simt_contract(i64, c, cs);
+            }
+            if (e != cudaSuccess) return KRON_ERR_CUDA;
+            if (via_buf) {
+                const size_t bytes = (size_t)prod(pl->n, 0, d) * esize(pl->dtype);
+                if (cudaMemcpyAsync(U, dst, bytes, cudaMemcpyDeviceToDevice, cs) != cudaSuccess)
+                    return KRON_ERR_CUDA;
+            }
+            src = dst;
+            src64 = dst64;
+            sel ^= 1;
+        }
+    }
+    return KRON_OK;
+}
+}  // namespace
+
+kron_status kron_expkronsum_workspace_size(kron_plan plan, size_t *bytes) {
+    if (!plan || !bytes) return KRON_ERR_INVALID_ARG;
+    kron_status st = check_step_plan(plan);
+    if (st != KRON_OK) return st;
+    *bytes = step_layout(plan).total;
+    return KRON_OK;
+}
+
+kron_status kron_expkronsum_apply(kron_plan plan, const double *const *E, const int64_t *ldE, int nsteps,
+                                  void *U, void *ws, size_t ws_bytes, kron_stream_t stream) {
+    if (!plan || !E || !ldE || !U || nsteps < 0) return KRON_ERR_INVALID_ARG;
+    kron_status st = check_step_plan(plan);
+    if (st != KRON_OK) return st;
+    for (int k = 0; k < plan->d; ++k) {
+        if (!E[k] || ldE[k] < plan->n[k]) return KRON_ERR_INVALID_ARG;
+        if (!aligned(E[k], 8)) return KRON_ERR_ALIGNMENT;
+    }
+    if (!aligned(U, esize(plan->dtype))) return KRON_ERR_ALIGNMENT;
+    const StepLayout lay = step_layout(plan);
+    st = check_ws(ws, ws_bytes, lay.total);
+    if (st != KRON_OK) return st;
+    return run_steps(plan, E, ldE, nsteps, U, static_cast<uint8_t *>(ws), lay,
+                     reinterpret_cast<cudaStream_t>(stream));
+}
+
+kron_status kron_expkronsum_step(kron_plan plan, const double *const *A, const int64_t *ldA, double tau,
+                                 int nsteps, void *U, void *ws, size_t ws_bytes, kron_stream_t stream) {
+    if (!plan || !A || !ldA || !U || nsteps < 0) return KRON_ERR_INVALID_ARG;
+    kron_status st = check_step_plan(plan);
+    if (st != KRON_OK) return st;
+    for (int k = 0; k < plan->d; ++k) {
+        if (!A[k] || ldA[k] < plan->n[k]) return KRON_ERR_INVALID_ARG;
+        if (!aligned(A[k], 8)) return KRON_ERR_ALIGNMENT;
+        if (plan->n[k] > 1024) return KRON_ERR_UNSUPPORTED;
+    }
+    if (!aligned(U, esize(plan->dtype))) return KRON_ERR_ALIGNMENT;
+    const StepLayout lay = step_layout(plan);
+    st = check_ws(ws, ws_bytes, lay.total);
+    if (st != KRON_OK) return st;
+    auto *w = static_cast<uint8_t *>(ws);
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    const double *Ep[KRON_MAX_D];
+    int64_t ldE[KRON_MAX_D];
+    for (int k = 0; k < plan->d; ++k) {
+        int same = -1;
+        for (int j = 0; j < k; ++j)
+            if (A[j] == A[k] && ldA[j] == ldA[k] && plan->n[j] == plan->n[k]) same = j;
+        ldE[k] = plan->n[k];
+        if (same >= 0) {
+            Ep[k] = Ep[same];
+            continue;
+        }
+        double *Ek = reinterpret_cast<double *>(w + lay.E[k]);
+        if (expm_pade13(plan->n[k], A[k], ldA[k], tau, Ek, w + lay.expm, cs) != cudaSuccess) return KRON_ERR_CUDA;
+        Ep[k] = Ek;
+    }
+    return run_steps(plan, Ep, ldE, nsteps, U, w, lay, cs);
+}
+
+}  // extern "C"

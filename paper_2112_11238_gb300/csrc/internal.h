@@ -1,0 +1,88 @@
+// internal.h -- host-side interfaces between the C ABI layer and the kernels.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/kron.h"
+
+namespace kron {
+
+// A 2-level index map used for rows, columns and the contracted index of
+// every contraction in the library: index x -> (x % R0) * s0 + (x / R0) * s1.
+// R0 == 0 means "no split": x -> x * s0.
+struct IdxMap {
+    int64_t R0 = 0;
+    int64_t s0 = 0;
+    int64_t s1 = 0;
+};
+
+// Strided generic contraction
+//     C[r, c] = sum_k A[r, k] * B[k, c]
+// with A[r, k] at A.ptr + rowA(r) + kA(k), B[k, c] at B.ptr + colB(c) + kB(k),
+// C[r, c] at C.ptr + rowC(r) + colC(c).  Every mu-mode product, every
+// step of the Tucker chain and the dL contraction of the adjoint is one of
+// these with suitable maps (no permute is ever formed).
+struct Contraction {
+    int64_t M = 0, N = 0, K = 0;
+    const void *A = nullptr;
+    bool A_f64 = false;
+    IdxMap rowA, kA;
+    const void *B = nullptr;
+    bool B_f64 = false;
+    IdxMap colB, kB;
+    void *C = nullptr;
+    bool C_f64 = false;
+    IdxMap rowC, colC;
+    // C = acc (+ C if accumulate)
+    bool accumulate = false;
+};
+
+// The split-precision forms of the tensor-core path.
+enum TcForm { kTF32x3 = 0, kBF16x3 = 1, kBF16x6 = 2 };
+
+inline int form_of(kron_prec p) {
+    switch (p) {
+        case KRON_PREC_3XTF32: return kTF32x3;
+        case KRON_PREC_BF16X3: return kBF16x3;
+        case KRON_PREC_BF16X6: return kBF16x6;
+        default: return -1;
+    }
+}
+inline bool is_split(kron_prec p) { return form_of(p) >= 0; }
+
+// ---- tensor-core path (tc.cu) ----
+// Bytes of the pre-split, pre-swizzled image of an (N x K) B operand.
+size_t tc_bimage_bytes(int form, int64_t N, int64_t K);
+// N-tile width the tensor-core kernels use for a given N.
+int tc_tile_n(int form, int64_t N);
+// Writes the image of B (given as a Contraction's B side: colB/kB maps over
+// N x K) into `img` (device, tc_bimage_bytes long).
+cudaError_t tc_build_bimage(int form, const Contraction &c, void *img, cudaStream_t st);
+// C = A * B with the B operand from an image made by tc_build_bimage.
+cudaError_t tc_contract_bimage(int form, const Contraction &c, const void *img, cudaStream_t st);
+// Split-K contraction with both operands converted on load (the adjoint's
+// dL); partial sums go to `partial` (FP32, splits * M * N), then reduced in a
+// fixed order into C.  Returns the number of splits used via *splits.
+size_t tc_splitk_partial_bytes(int64_t M, int64_t N, int64_t K);
+cudaError_t tc_contract_splitk(int form, const Contraction &c, float *partial, cudaStream_t st);
+
+// ---- CUDA-core path (simt.cu) ----
+// FP64 (f64 = true) or FP32 fused multiply-add.
+cudaError_t simt_contract(bool f64, const Contraction &c, cudaStream_t st);
+// Split-K variant for a long contracted index (the adjoint's dL): partials
+// (FP64 or FP32, splits * M * N) summed in a fixed order into C.
+size_t simt_splitk_partial_bytes(bool f64, int64_t M, int64_t N, int64_t K);
+cudaError_t simt_contract_splitk(bool f64, const Contraction &c, void *partial, cudaStream_t st);
+
+// ---- FP64 dense helpers (expm.cu) ----
+size_t expm_workspace_bytes(int64_t n);
+cudaError_t expm_pade13(int64_t n, const double *A, int64_t ldA, double tau, double *E, void *ws,
+                        cudaStream_t st);
+
+// Device error words of the translation units that have bounded waits.
+cudaError_t tc_error_word(unsigned int *out, bool clear);
+cudaError_t expm_error_word(unsigned int *out, bool clear);
+cudaError_t batched_error_word(unsigned int *out, bool clear);
+
+}  // namespace kron

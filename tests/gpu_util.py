@@ -1,0 +1,47 @@
+"""Shared helpers of the GPU parity tests (numpy <-> CUDA tensors, tolerances)."""
+import numpy as np
+
+# Max-norm relative error bound per precision, against the FP64 oracle.
+#  fp64   : the plain FP64 path, 1e-12.
+#  3xtf32 : 2e-6, the split-form budget.
+#  bf16x6 : 2e-6.
+#  bf16x3 : two bf16 pieces keep about 16 significant bits (unit roundoff
+#           2^-17 = 7.6e-6 per product); it is NOT expected to meet 2e-6, the
+#           bound here is 6e-5 and the measured value is reported.
+#  fp32   : FP32 fused multiply-add chains, 1e-5.
+TOL = {"fp64": 1e-12, "3xtf32": 2e-6, "bf16x6": 2e-6, "bf16x3": 6e-5, "fp32": 1e-5}
+
+
+def tol(prec, ksum):
+    """Bound for a chain whose contracted lengths add up to ksum.
+
+    The split forms accumulate in FP32 inside tensor memory, where every MMA
+    step may drop up to one unit in the last place of the running sum; with
+    one fresh accumulator per K-block of 32 (up to four, summed in FP32 at
+    the end) the error of random-sign data grows about linearly in the
+    contracted length.  Above 256 accumulated terms the budget is widened
+    in proportion: u_fp32 / 8 = 7.5e-9 per term."""
+    base = TOL[prec]
+    if prec in ("3xtf32", "bf16x6", "fp32"):
+        return max(base, 7.5e-9 * ksum)
+    return base
+
+
+def to_dev(a, dtype=None):
+    import torch
+    import paper_2112_11238_gb300 as kron
+    a = np.asfortranarray(a)
+    t = torch.from_numpy(a)
+    if dtype is not None:
+        t = t.to(dtype)
+    return kron.colmajor(t.cuda())
+
+
+def to_host(t):
+    return np.asfortranarray(t.detach().double().cpu().numpy())
+
+
+def rel_err(x, ref):
+    x = np.asarray(x, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.max(np.abs(x - ref)) / max(np.max(np.abs(ref)), 1e-300))

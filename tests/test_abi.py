@@ -1,0 +1,114 @@
+"""Host-side checks of the C ABI: the library loads, exports every symbol
+include/kron.h declares, and validates arguments without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "kron.h")
+
+
+def _declared_symbols():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"KRON_API\s+[\w\s\*]*?\b(kron_\w+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "kron_build", os.path.join(ROOT, "paper_2112_11238_gb300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    path = mod.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_entry_points():
+    syms = _declared_symbols()
+    for name in ("kron_mump", "kron_tucker", "kron_tucker_adjoint", "kron_expkronsum_step",
+                 "kron_batched_run", "kron_expm"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [s for s in _declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_symbol(lib):
+    import paper_2112_11238_gb300 as kron
+    assert sorted(kron.EXPORTS) == _declared_symbols()
+
+
+def _i64(v):
+    return (ctypes.c_int64 * len(v))(*v)
+
+
+def test_status_strings(lib):
+    lib.kron_status_string.restype = ctypes.c_char_p
+    assert lib.kron_status_string(0) == b"KRON_OK"
+    assert lib.kron_status_string(6) == b"KRON_ERR_TIMEOUT"
+
+
+def test_plan_validation_and_order(lib):
+    h = ctypes.c_void_p()
+    assert lib.kron_plan_create(ctypes.byref(h), 0, _i64([1]), _i64([1]), 0, 0, 0) == 1
+    assert lib.kron_plan_create(ctypes.byref(h), 7, _i64([1] * 7), _i64([1] * 7), 0, 0, 0) == 1
+    assert lib.kron_plan_create(ctypes.byref(h), 2, _i64([3, 0]), _i64([3, 3]), 0, 0, 0) == 1
+    assert lib.kron_plan_create(ctypes.byref(h), 2, _i64([3, 3]), _i64([3, 3]), 5, 0, 0) == 1
+    assert lib.kron_plan_create(ctypes.byref(h), 2, _i64([3, 3]), _i64([3, 3]), 0, 9, 0) == 1
+    # cost-minimising order: shrink the big mode first
+    assert lib.kron_plan_create(ctypes.byref(h), 3, _i64([50, 4, 4]), _i64([2, 40, 40]), 0, 2, 0) == 0
+    order = (ctypes.c_int * 3)()
+    assert lib.kron_plan_order(h, order) == 0
+    assert list(order)[0] == 0
+    lib.kron_plan_flops.restype = ctypes.c_double
+    assert lib.kron_plan_flops(h) > 0
+    ws = ctypes.c_size_t(0)
+    assert lib.kron_plan_workspace_size(h, ctypes.byref(ws)) == 0 and ws.value > 0
+    assert lib.kron_plan_destroy(h) == 0
+
+
+def test_natural_order_flag(lib):
+    h = ctypes.c_void_p()
+    assert lib.kron_plan_create(ctypes.byref(h), 3, _i64([4, 4, 50]), _i64([40, 40, 2]), 1, 0, 2) == 0
+    order = (ctypes.c_int * 3)()
+    lib.kron_plan_order(h, order)
+    assert list(order) == [0, 1, 2]
+    lib.kron_plan_destroy(h)
+
+
+def test_call_validation_without_gpu(lib):
+    h = ctypes.c_void_p()
+    assert lib.kron_plan_create(ctypes.byref(h), 2, _i64([3, 3]), _i64([3, 3]), 0, 0, 0) == 0
+    L = (ctypes.c_void_p * 2)(8, 8)
+    ld = _i64([3, 3])
+    # null tensor
+    assert lib.kron_tucker(h, None, L, ld, ctypes.c_void_p(8), None, ctypes.c_size_t(0), None) == 1
+    # ld too small
+    assert lib.kron_tucker(h, ctypes.c_void_p(8), L, _i64([2, 3]), ctypes.c_void_p(8), None, ctypes.c_size_t(0), None) == 1
+    # misaligned tensor pointer
+    assert lib.kron_tucker(h, ctypes.c_void_p(12), L, ld, ctypes.c_void_p(8), None, ctypes.c_size_t(0), None) == 3
+    # workspace too small
+    ws = ctypes.c_size_t(0)
+    lib.kron_plan_workspace_size(h, ctypes.byref(ws))
+    assert lib.kron_tucker(h, ctypes.c_void_p(8), L, ld, ctypes.c_void_p(8), ctypes.c_void_p(256), ctypes.c_size_t(0), None) == 4
+    lib.kron_plan_destroy(h)
+    # stepper needs a square plan
+    assert lib.kron_plan_create(ctypes.byref(h), 2, _i64([3, 4]), _i64([3, 3]), 0, 0, 0) == 0
+    assert lib.kron_expkronsum_workspace_size(h, ctypes.byref(ws)) == 1
+    lib.kron_plan_destroy(h)
+    # expm size limits
+    assert lib.kron_expm_workspace_size(0, ctypes.byref(ws)) == 1
+    assert lib.kron_expm_workspace_size(2048, ctypes.byref(ws)) == 1
+    assert lib.kron_expm_workspace_size(256, ctypes.byref(ws)) == 0
+
+
+def test_mump_workspace_query(lib):
+    ws = ctypes.c_size_t(0)
+    assert lib.kron_mump_workspace_size(3, _i64([5, 6, 7]), 1, 9, 1, 2, ctypes.byref(ws)) == 0
+    assert ws.value >= 256
+    assert lib.kron_mump_workspace_size(3, _i64([5, 6, 7]), 3, 9, 1, 2, ctypes.byref(ws)) == 1

@@ -1,0 +1,165 @@
+"""Parity at the full workload sizes, against the FP64 oracle.
+
+* Tucker d=3, n=m=100 (random normal): every output against the oracle.
+* Tucker d=6, n=m=20 (Chebyshev-Vandermonde L): a sampled sub-grid of outputs,
+  S[I_1, ..., I_6] = T x_1 L_1[I_1, :] ... x_6 L_6[I_6, :], computed by the
+  oracle with row-subsampled matrices.
+* Stepper, 256^3, tau = 1e-4, 100 steps: the rank-4 initial field makes the
+  exact U_100 = sum_r (E^100 f_r1) o (E^100 f_r2) o (E^100 f_r3) with the
+  closed-form E^100 = exp(100 tau A) (oracle, long double).
+* Adjoint d=4, n=m=48: gradients against the oracle gradient and against
+  central differences of the FP64 loss.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_util import TOL, rel_err, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kron():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2112_11238_gb300 as k
+    return k
+
+
+@pytest.fixture(scope="module")
+def cfg_d3():
+    c = W.tucker_d3(100)
+    return c, oracle.tucker(c.T, c.L)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "3xtf32", "bf16x3", "bf16x6"])
+def test_tucker_d3_n100(kron, cfg_d3, prec):
+    c, ref = cfg_d3
+    S = kron.tucker(to_dev(c.T), [to_dev(L) for L in c.L], prec=prec)
+    err = rel_err(to_host(S), ref)
+    print(f"tucker d=3 n=100 {prec}: max-norm rel err {err:.3e}")
+    assert err <= TOL[prec], err
+
+
+@pytest.fixture(scope="module")
+def cfg_d6():
+    c = W.tucker_d6()
+    g = np.random.default_rng(99)
+    idx = [np.sort(g.choice(20, 3, replace=False)) for _ in range(6)]
+    ref = oracle.tucker(c.T, [L[i, :] for L, i in zip(c.L, idx)])
+    return c, idx, ref
+
+
+@pytest.mark.parametrize("prec", ["fp64", "3xtf32", "bf16x3", "bf16x6", "fp32"])
+def test_tucker_d6_n20_sampled(kron, cfg_d6, prec):
+    import torch
+    c, idx, ref = cfg_d6
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    S = kron.tucker(to_dev(c.T, dtype), [to_dev(L, dtype) for L in c.L], prec=prec)
+    ix = [torch.as_tensor(i, device=S.device) for i in idx]
+    sub = S
+    for mu, i in enumerate(ix):
+        sub = sub.index_select(mu, i)
+    err = rel_err(to_host(sub), ref)
+    print(f"tucker d=6 n=20 {prec}: sampled max-norm rel err {err:.3e}")
+    assert err <= max(TOL[prec], 1e-7 if dtype == torch.float32 else 0), err
+
+
+@pytest.fixture(scope="module")
+def cfg_stepper():
+    c = W.stepper()
+    E = oracle.expm_tridiag_toeplitz(c.n, *c.tri, c.nsteps * c.tau)
+    g = np.einsum("ij,rdj->rdi", E, c.factors)
+    return c, W.outer_sum(g)
+
+
+def test_stepper_fp64_100_steps(kron, cfg_stepper):
+    c, ref = cfg_stepper
+    U = kron.expkronsum_step(to_dev(c.U0), [to_dev(A) for A in c.A], c.tau, c.nsteps, prec="fp64")
+    err = rel_err(to_host(U), ref)
+    print(f"stepper fp64 100 steps: {err:.3e}")
+    assert err <= 1e-12
+    assert kron.device_error() == 0
+
+
+@pytest.mark.parametrize("prec", ["3xtf32", "bf16x6"])
+def test_stepper_split_100_steps_fp32_accumulate(kron, cfg_stepper, prec):
+    """FP32-accumulating split forms: the per-step error (~1e-6) is
+    systematic, so it grows linearly over the 100 steps (300 chained mode
+    products); the bound is 300 * 1e-6."""
+    c, ref = cfg_stepper
+    U = kron.expkronsum_step(to_dev(c.U0), [to_dev(A) for A in c.A], c.tau, c.nsteps, prec=prec)
+    err = rel_err(to_host(U), ref)
+    print(f"stepper {prec} 100 steps: {err:.3e}")
+    assert err <= 3e-4
+
+
+@pytest.fixture(scope="module")
+def cfg_adjoint():
+    c, target = W.adjoint()
+    S = oracle.tucker(c.T, c.L)
+    dS = S - target
+    dT, dL = oracle.tucker_adjoint(c.T, c.L, dS)
+    return c, target, dT, dL
+
+
+@pytest.mark.parametrize("prec", ["fp64", "3xtf32", "bf16x6"])
+def test_adjoint_d4_n48_against_oracle_gradient(kron, cfg_adjoint, prec):
+    import torch
+    c, target, dT_ref, dL_ref = cfg_adjoint
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    T = to_dev(c.T, dtype).requires_grad_(True)
+    Ls = [to_dev(L, dtype).requires_grad_(True) for L in c.L]
+    S = kron.tucker_autograd(T, Ls, prec=prec)
+    loss = 0.5 * ((S - to_dev(target, dtype)) ** 2).sum()
+    loss.backward()
+    tol = 1e-12 if prec == "fp64" else 2e-5
+    e = rel_err(to_host(T.grad), dT_ref)
+    print(f"adjoint {prec}: dT {e:.3e}", end="")
+    assert e <= tol
+    for k in range(4):
+        e = rel_err(to_host(Ls[k].grad), dL_ref[k])
+        print(f" dL{k} {e:.3e}", end="")
+        assert e <= tol
+    print()
+
+
+def _loss64(T, Ls, target):
+    r = oracle.tucker(T, Ls) - target
+    return 0.5 * float(np.sum(r * r))
+
+
+@pytest.mark.parametrize("prec", ["3xtf32", "bf16x6"])
+def test_adjoint_d4_n48_central_differences(kron, cfg_adjoint, prec):
+    """<grad, v> of the split-precision adjoint against central differences of
+    the FP64 loss (h = 1e-6 relative); the loss is quadratic along v, so the
+    difference quotient is exact up to rounding.  Bound: 1e-6 relative."""
+    import torch
+    c, target, _, _ = cfg_adjoint
+    T = to_dev(c.T, torch.float32).requires_grad_(True)
+    Ls = [to_dev(L, torch.float32).requires_grad_(True) for L in c.L]
+    S = kron.tucker_autograd(T, Ls, prec=prec)
+    loss = 0.5 * ((S - to_dev(target, torch.float32)) ** 2).sum()
+    loss.backward()
+    # the FD reference is evaluated on the same (FP32-rounded) inputs
+    T32 = c.T.astype(np.float32).astype(np.float64)
+    L32 = [L.astype(np.float32).astype(np.float64) for L in c.L]
+    tg = target.astype(np.float32).astype(np.float64)
+    g = np.random.default_rng(3)
+    V = np.asfortranarray(g.standard_normal(T32.shape))
+    h = 1e-6 * np.linalg.norm(T32) / np.linalg.norm(V)
+    fd = (_loss64(T32 + h * V, L32, tg) - _loss64(T32 - h * V, L32, tg)) / (2 * h)
+    an = float(np.sum(to_host(T.grad) * V))
+    assert abs(an - fd) <= 1e-6 * abs(fd), (an, fd)
+    for k in range(4):
+        V = np.asfortranarray(g.standard_normal(L32[k].shape))
+        h = 1e-6 * np.linalg.norm(L32[k]) / np.linalg.norm(V)
+        Lp = list(L32); Lm = list(L32)
+        Lp[k] = L32[k] + h * V
+        Lm[k] = L32[k] - h * V
+        fd = (_loss64(T32, Lp, tg) - _loss64(T32, Lm, tg)) / (2 * h)
+        an = float(np.sum(to_host(Ls[k].grad) * V))
+        assert abs(an - fd) <= 1e-6 * abs(fd), (k, an, fd)

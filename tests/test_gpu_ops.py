@@ -1,0 +1,120 @@
+"""GPU parity of the mu-mode product, the Tucker operator and expm against the
+FP64 oracle, on small and ragged shapes (several tiles, ragged tails, P = 1
+and Q = 1 slabs, n != m, transposed L), every precision, both storage types."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import TOL, rel_err, to_dev, to_host, tol
+
+pytestmark = pytest.mark.gpu
+
+RNG = np.random.default_rng(2024)
+PRECS = ["fp64", "fp32", "3xtf32", "bf16x3", "bf16x6"]
+
+
+def rnd(*s):
+    return np.asfortranarray(RNG.standard_normal(s))
+
+
+@pytest.fixture(scope="module")
+def kron():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2112_11238_gb300 as k
+    return k
+
+
+MUMP_CASES = [
+    ((7,), 0, 5), ((37, 3), 0, 19), ((3, 37), 1, 40), ((130, 5, 3), 0, 7),
+    ((9, 33, 17), 1, 33), ((5, 6, 300), 2, 12), ((129, 2, 2), 1, 257), ((20, 20, 20, 3), 2, 20),
+    ((1, 1, 5), 2, 1), ((64, 64), 1, 64), ((17, 70), 0, 33),
+]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("shape,mu,n", MUMP_CASES)
+def test_mump_matches_oracle(kron, shape, mu, n, prec):
+    import torch
+    T = rnd(*shape)
+    L = rnd(n, shape[mu])
+    ref = oracle.mump(T, L, mu)
+    S = kron.mump(to_dev(T), to_dev(L), mu, prec=prec)
+    err = rel_err(to_host(S), ref)
+    assert err <= tol(prec, shape[mu]), (prec, shape, mu, n, err)
+    assert kron.device_error() == 0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "3xtf32", "bf16x6"])
+def test_mump_transposed(kron, prec):
+    T = rnd(11, 23, 5)
+    L = rnd(23, 30)  # op(L) = L^T is 30 x 23
+    ref = oracle.mump(T, L, 1, transL=True)
+    S = kron.mump(to_dev(T), to_dev(L), 1, trans=True, prec=prec)
+    assert rel_err(to_host(S), ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["3xtf32", "bf16x6", "fp32"])
+def test_mump_float32_storage(kron, prec):
+    import torch
+    T = rnd(40, 33, 9)
+    L = rnd(17, 33)
+    ref = oracle.mump(T, L, 1)
+    S = kron.mump(to_dev(T, torch.float32), to_dev(L, torch.float32), 1, prec=prec)
+    assert S.dtype == torch.float32
+    assert rel_err(to_host(S), ref) <= max(TOL[prec], 1e-6)
+
+
+TUCKER_CASES = [
+    ((5, 7), (9, 3)), ((13, 4, 9), (6, 11, 2)), ((33, 31, 29), (35, 30, 28)),
+    ((6, 5, 4, 3), (3, 4, 5, 6)), ((4, 3, 5, 2, 3), (2, 5, 3, 4, 2)), ((4,) * 6, (5,) * 6),
+    ((100, 1, 7), (1, 50, 7)),
+]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("m,n", TUCKER_CASES)
+def test_tucker_matches_oracle(kron, m, n, prec):
+    T = rnd(*m)
+    Ls = [rnd(n[k], m[k]) for k in range(len(m))]
+    ref = oracle.tucker(T, Ls)
+    S = kron.tucker(to_dev(T), [to_dev(L) for L in Ls], prec=prec)
+    assert tuple(S.shape) == tuple(n)
+    err = rel_err(to_host(S), ref)
+    assert err <= tol(prec, sum(m)), (prec, m, n, err)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "3xtf32"])
+def test_tucker_transposed_plan(kron, prec):
+    m, n = (7, 9, 5), (4, 10, 6)
+    T = rnd(*m)
+    Ls = [rnd(m[k], n[k]) for k in range(3)]   # op(L) = L^T
+    ref = oracle.tucker(T, Ls, transL=True)
+    S = kron.tucker(to_dev(T), [to_dev(L) for L in Ls], prec=prec, trans=True)
+    assert rel_err(to_host(S), ref) <= TOL[prec]
+
+
+def test_identity_returns_input_exactly_fp64(kron):
+    T = rnd(9, 8, 7)
+    S = kron.tucker(to_dev(T), [to_dev(np.eye(k)) for k in T.shape], prec="fp64")
+    np.testing.assert_array_equal(to_host(S), T)
+
+
+@pytest.mark.parametrize("n", [1, 5, 64, 256])
+def test_expm_matches_closed_form(kron, n):
+    import workloads as W
+    sub, diag, sup = W.fd_advection_diffusion(n)
+    tau = 1e-4
+    A = W.tridiag_dense(n, sub, diag, sup)
+    ref = oracle.expm_tridiag_toeplitz(n, sub, diag, sup, tau)
+    E = kron.expm(to_dev(A), tau)
+    assert rel_err(to_host(E), ref) <= 1e-12
+    assert kron.device_error() == 0
+
+
+def test_expm_random_matrix(kron):
+    A = rnd(12, 12)
+    ref = oracle.expm_taylor(A, 0.37)
+    E = kron.expm(to_dev(A), 0.37)
+    assert rel_err(to_host(E), ref) <= 1e-12
