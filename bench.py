@@ -1,0 +1,403 @@
+"""Benchmark: exponential-of-Kronecker-sum stepper on a 256^3 grid.
+
+One benchmark step is one call of the library's stepper on the workload
+"d = 3, n = 256, A_mu = FD Laplacian + centred advection 0.5 on [0, 1],
+tau = 1e-4, 100 steps, FP64 state": the FP64 matrix exponentials
+E_mu = exp(tau A_mu) (scaling and squaring, on the GPU) followed by 100 Tucker
+steps U <- U x_1 E_1 x_2 E_2 x_3 E_3.  The metric is effective TFLOP/s:
+the algorithmic 100 * 3 * 2 * 256^4 flops of the Tucker steps per second.
+
+Printed: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead (a bounded number of Tucker steps per
+benchmark step, scaled to the same unit).
+
+Multi-GPU: the stepper does not shard; with N ranks every GPU runs its own
+replica of the workload and the value is the work of all replicas divided by
+the slowest rank's time (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "Tucker op effective TFLOP/s and % TC peak vs plain FP64 GPU path at stated rel err"
+N, D, TAU, NSTEPS = 256, 3, 1e-4, 100
+FLOPS_PER_TSTEP = D * 2.0 * N ** (D + 1)            # one Tucker step
+FLOPS_PER_STEP = NSTEPS * FLOPS_PER_TSTEP           # one benchmark step
+WORKLOAD = "expkronsum stepper d=3 n=256 tau=1e-4 100 steps, FP64 state, FD Laplacian + advection 0.5"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# GB300 nominal dense tensor rates (PFLOP/s), used only as ratios between dtypes
+NOMINAL = {"bf16": 2.25, "tf32": 1.1}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def init_dist(world, backend):
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend=backend)
+        return dist
+    return None
+
+
+def max_over_ranks(dist, value, device=None):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for k, name in enumerate(names):
+                if s[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------------ oracle arm
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    c = W.stepper(n=N, tau=TAU, nsteps=NSTEPS)
+    E = oracle.expm_tridiag_toeplitz(N, *c.tri, TAU)
+    U = np.array(c.U0, order="F")
+    # bounded sample: `per` Tucker steps per benchmark step (about 1-3 s each)
+    per = 1
+    for _ in range(args.warmup):
+        U = oracle.expkronsum_steps(U, [E] * D, per)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        U = oracle.expkronsum_steps(U, [E] * D, per)
+        times.append(time.perf_counter() - t0)
+    sec = sum(times)
+    value = args.steps * per * FLOPS_PER_TSTEP / sec / 1e12
+    cores = oracle.num_threads()
+    sample = f"{per} of the 100 Tucker steps (256^3, FP64) per benchmark step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sec / args.steps * (NSTEPS / per), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "prec": "fp64 oracle (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_sample(target_s=12.0):
+    """The oracle timed on the host cores on a bounded sample of the workload."""
+    import oracle
+    c = W.stepper(n=N, tau=TAU, nsteps=NSTEPS)
+    E = oracle.expm_tridiag_toeplitz(N, *c.tri, TAU)
+    U = np.array(c.U0, order="F")
+    t0 = time.perf_counter()
+    U = oracle.expkronsum_steps(U, [E] * D, 1)
+    t1 = time.perf_counter() - t0
+    k = max(1, int(target_s / max(t1, 1e-3)) - 1)
+    t0 = time.perf_counter()
+    U = oracle.expkronsum_steps(U, [E] * D, k)
+    sec = time.perf_counter() - t0
+    return {"value": k * FLOPS_PER_TSTEP / sec / 1e12, "unit": "TFLOP/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"{k} Tucker steps of the 256^3 stepper (of 100), FP64, {sec:.1f} s"}
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = init_dist(world, "nccl")
+    import paper_2112_11238_gb300 as kron
+
+    prec = args.prec
+    c = W.stepper(n=N, tau=TAU, nsteps=NSTEPS)
+    U0_host = torch.from_numpy(np.asfortranarray(c.U0)).pin_memory()
+    A = [kron.colmajor(torch.from_numpy(np.asfortranarray(a)).to(dev)) for a in c.A]
+    stepper = kron.StepperPlan([N] * D, torch.float64, prec)
+    ws = stepper.workspace(dev)
+    U = kron.empty_colmajor([N] * D, torch.float64, dev)
+    U_init = kron.empty_colmajor([N] * D, torch.float64, dev)
+    U_init.copy_(U0_host)
+    stream = torch.cuda.current_stream(dev)
+    l2_flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def one_step():
+        U.copy_(U_init)
+        stepper.step(U, A, TAU, NSTEPS, ws=ws)
+
+    # warm-up
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    assert kron.device_error() == 0, "device error word set during warm-up"
+
+    # timed region: per step, flush L2 (untimed), then time the step with events
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(dist)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        l2_flush.zero_()
+        U.copy_(U_init)
+        ev[i][0].record(stream)
+        stepper.step(U, A, TAU, NSTEPS, ws=ws)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ms = max_over_ranks(dist, ms, dev)
+    ms_per_step = ms / args.steps
+    value = world * FLOPS_PER_STEP / (ms_per_step * 1e-3) / 1e12
+    assert kron.device_error() == 0, "device error word set during the timed region"
+    U_split = U.clone()
+
+    # dominant kernel: one mode product of the stepper, timed alone with events
+    kern = time_mode_product(kron, torch, dev, prec, args)
+
+    # end to end: host U0 -> device, stepper, device -> host, through the public API
+    U_host_out = torch.empty_like(U0_host).pin_memory()
+    e2e_ms = []
+    for i in range(max(args.steps, 1)):
+        l2_flush.zero_()
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        U.copy_(U0_host, non_blocking=True)
+        stepper.step(U, A, TAU, NSTEPS, ws=ws)
+        U_host_out.copy_(U, non_blocking=True)
+        e.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(s.elapsed_time(e))
+    e2e = max_over_ranks(dist, sum(e2e_ms) / len(e2e_ms), dev)
+
+    # plain FP64 GPU path on the same inputs (the comparison path)
+    fp64 = StepperFP64(kron, torch, dev, A, U_init)
+    fp64_ms, U64 = fp64.run()
+    rel = float((U_split - U64).abs().max() / U64.abs().max())
+
+    if rank == 0:
+        peaks, peak_src = load_peaks()
+        out = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"3xtf32": "tf32x3/f32acc", "bf16x6": "bf16x6/f32acc",
+                                           "bf16x3": "bf16x3/f32acc"}.get(prec, prec),
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "prec": prec, "state": "f64 in/out, f32 between modes",
+                       "l2": "flushed between timed steps (512 MiB write); U is 134 MB FP64"},
+            "rel_err_vs_fp64_gpu": rel,
+            "fp64_path": {"ms_per_step": fp64_ms, "value": FLOPS_PER_STEP / (fp64_ms * 1e-3) / 1e12,
+                          "unit": "TFLOP/s", "speedup": fp64_ms / ms_per_step},
+            "roofline": roofline(kern, peaks, peak_src, prec),
+            "e2e": {"value": world * FLOPS_PER_STEP / (e2e * 1e-3) / 1e12, "unit": "TFLOP/s",
+                    "h2d_bytes_per_step": N ** D * 8, "d2h_bytes_per_step": N ** D * 8},
+            "gpu_launches": args.steps * (1 + D + NSTEPS * D),
+            "clocks": clocks.summary(),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline_sample()
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+class StepperFP64:
+    """The plain FP64 path on the same inputs: 100 steps, timed once."""
+
+    def __init__(self, kron, torch, dev, A, U_init):
+        self.kron, self.torch, self.dev, self.A, self.U_init = kron, torch, dev, A, U_init
+        self.plan = kron.StepperPlan([N] * D, torch.float64, "fp64")
+        self.ws = self.plan.workspace(dev)
+
+    def run(self):
+        torch = self.torch
+        U = self.U_init.clone()
+        self.plan.step(U, self.A, TAU, 1, ws=self.ws)  # warm-up
+        U = self.U_init.clone()
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        self.plan.step(U, self.A, TAU, NSTEPS, ws=self.ws)
+        e.record()
+        torch.cuda.synchronize()
+        return s.elapsed_time(e), U
+
+
+def time_mode_product(kron, torch, dev, prec, args):
+    """Average duration of the dominant kernel (one 256^3 mode product in
+    the form the stepper uses), timed with CUDA events on its stream, with
+    L2 flushed before each launch."""
+    mu = 1
+    X = kron.empty_colmajor([N] * D, torch.float32, dev)
+    X.normal_()
+    E = torch.randn(N, N, dtype=torch.float32, device=dev)
+    Y = kron.empty_colmajor([N] * D, torch.float32, dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        kron.mump_into(X, E, mu, Y, prec=prec)
+    ts = []
+    for _ in range(20):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        kron.mump_into(X, E, mu, Y, prec=prec)
+        e.record()
+        torch.cuda.synchronize()
+        ts.append(s.elapsed_time(e))
+    return {"ms": statistics.median(ts), "mu": mu}
+
+
+def run_kernel_only(args):
+    import torch
+    import paper_2112_11238_gb300 as kron
+    dev = torch.device("cuda", 0)
+    kern = time_mode_product(kron, torch, dev, args.prec, args)
+    print(json.dumps({"kernel": "mode product 256^3 f32", "prec": args.prec, "ms": kern["ms"]}))
+    return 0
+
+
+def roofline(kern, peaks, src, prec):
+    """Roofline of the dominant kernel (one mode product, 256^3 FP32 in/out).
+
+    Algorithmic work per launch: 2 * 256^4 flops; bytes: 256^3 * 4 in + out.
+    The split form runs `mult` tensor-core products per algorithmic product,
+    so its ceiling in algorithmic flops is the pipe's peak / mult; the pipe
+    peak for TF32 is the measured bf16 peak times the nominal TF32/BF16
+    ratio.  The kernel runs inside a long step: sustained peak."""
+    flops = 2.0 * N ** (D + 1)
+    byts = 2.0 * N ** D * 4
+    t = kern["ms"] * 1e-3
+    bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    if prec == "3xtf32":
+        pipe, mult = bf16 * NOMINAL["tf32"] / NOMINAL["bf16"], 3
+    elif prec == "bf16x6":
+        pipe, mult = bf16, 6
+    else:
+        pipe, mult = bf16, 3
+    peak = pipe / mult
+    achieved = flops / t / 1e12
+    hbm_t = byts / (peaks["hbm_gbs"] * 1e9)
+    tc_t = flops / (peak * 1e12)
+    bound = "tensor" if tc_t >= hbm_t else "hbm"
+    if bound == "hbm":
+        return {"bound": "hbm", "achieved": byts / t / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": (byts / t / 1e9) / peaks["hbm_gbs"], "traffic": None, "peak_source": src}
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "peak_source": f"{src} (sustained bf16 x nominal ratio / {mult} products)",
+            "kernel_ms": kern["ms"]}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="kron", choices=["kron", "reference"])
+    ap.add_argument("--prec", default="3xtf32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="run only the dominant kernel (256^3 mode products) a few times, for profilers")
+    args = ap.parse_args()
+    if args.kernel_only:
+        return run_kernel_only(args)
+    if args.warmup < 3 and args.impl == "kron":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
