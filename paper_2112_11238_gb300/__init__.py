@@ -190,6 +190,15 @@ def _require_cuda(*ts):
 
 # --------------------------------------------------------------- mu-mode
 
+def mump_workspace(T: torch.Tensor, L: torch.Tensor, mu: int, trans: bool = False, prec="fp64") -> torch.Tensor:
+    """A workspace large enough for mump_into with these operands."""
+    n = L.shape[1] if trans else L.shape[0]
+    need = ctypes.c_size_t(0)
+    _check(_lib.kron_mump_workspace_size(T.dim(), _i64(list(T.shape)), mu, n, _dtype_code(T), _prec(prec),
+                                         ctypes.byref(need)), "kron_mump_workspace_size")
+    return _workspace(need.value, T.device)
+
+
 def mump_into(T: torch.Tensor, L: torch.Tensor, mu: int, S: torch.Tensor, trans: bool = False,
               prec="fp64", ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """S = T x_mu op(L) (Eq. (mmp)) into a preallocated column-major S."""

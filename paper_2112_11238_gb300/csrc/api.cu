@@ -166,7 +166,7 @@ kron_status run_chain(const kron_plan_s *pl, const void *T, const void *const *L
             Contraction c = tc_mode_contraction(g, src, src64, L[mu], io64, ldL[mu], trans, dst, dst64);
             void *img = ws + pl->img_off[mu];
             e = tc_build_bimage(form, c, img, st);
-            if (e == cudaSuccess) e = tc_contract_bimage(form, c, img, st);
+            if (e == cudaSuccess) e = tcp_contract(form, c, img, st);
         } else {
             Contraction c =
                 simt_mode_contraction(g, src, src64, L[mu], io64, ldL[mu], trans, dst, dst64);
@@ -297,7 +297,7 @@ kron_status kron_mump(int d, const int64_t *m, int mu, int64_t n, const void *T,
         const int form = form_of(prec);
         Contraction c = tc_mode_contraction(g, T, io64, L, io64, ldL, transL != 0, S, io64);
         e = tc_build_bimage(form, c, ws, cs);
-        if (e == cudaSuccess) e = tc_contract_bimage(form, c, ws, cs);
+        if (e == cudaSuccess) e = tcp_contract(form, c, ws, cs);
     } else {
         Contraction c = simt_mode_contraction(g, T, io64, L, io64, ldL, transL != 0, S, io64);
         e = simt_contract(prec == KRON_PREC_FP64, c, cs);
@@ -454,7 +454,7 @@ cudaError_t adj_mode(const kron_plan_s *pl, const ModeGeom &g, const void *src, 
         Contraction c = tc_mode_contraction(g, src, src64, L, io64, ldL, trans, dst, dst64);
         cudaError_t e = tc_build_bimage(form, c, img, st);
         if (e != cudaSuccess) return e;
-        return tc_contract_bimage(form, c, img, st);
+        return tcp_contract(form, c, img, st);
     }
     Contraction c = simt_mode_contraction(g, src, src64, L, io64, ldL, trans, dst, dst64);
     return simt_contract(pl->prec == KRON_PREC_FP64, c, st);
@@ -649,7 +649,7 @@ kron_status run_steps(const kron_plan_s *pl, const double *const *E, const int64
             cudaError_t e;
             if (split) {
                 Contraction c = tc_mode_contraction(g, src, src64, E[mu], true, ldE[mu], false, dst, dst64);
-                e = tc_contract_bimage(form, c, w + lay.img[mu], cs);
+                e = tcp_contract(form, c, w + lay.img[mu], cs);
             } else {
                 Contraction c = simt_mode_contraction(g, src, src64, E[mu], true, ldE[mu], false, dst, dst64);
                 e = simt_contract(i64, c, cs);

@@ -1,30 +1,365 @@
-// batched.cu -- many independent Tucker operators in one persistent launch.
-#include "internal.h"
-#include "ptx.cuh"
+// batched.cu -- many independent Tucker operators of uneven sizes in one
+// persistent launch (Section 3.2, Eq. (tensinterp); the batched evaluation
+// of tensor-product interpolants, cf. Section 4.3).
+//
+// A plan fixes the shapes.  Every problem b becomes d jobs of the persistent
+// tensor-core kernel (tcp.cu), one per mode in the problem's cost-minimising
+// order; the job of mode step s waits for step s-1 of the same problem.  Jobs
+// are ordered in waves (step s of problem group g runs in wave g + s) so that
+// the intermediates of a group are consumed while they are still in L2.
+//
+// bind() writes the device job table (pointers of that binding) into the
+// workspace; run() is two launches -- one that splits and swizzles every L_mu
+// into its image, and the persistent kernel -- plus a memset of the job
+// counters, so a bound run can be captured in a CUDA graph.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "tc_common.cuh"
 
 namespace kron {
 cudaError_t batched_error_word(unsigned int *out, bool clear) { return read_error_word(out, clear); }
-}  // namespace kron
 
-struct kron_batched_plan_s {
-    int batch;
+namespace {
+
+constexpr size_t kAl = 256;
+inline size_t al(size_t x) { return (x + kAl - 1) / kAl * kAl; }
+
+// One L_mu to split into an image.
+struct ImgJob {
+    const void *L;
+    int64_t ld, N, K;
+    uint8_t *img;
+    int32_t BN;
+    int32_t l64;
+    int64_t items;   // (nt, kb, row, chunk) items of this image
+    int64_t begin;   // prefix sum of items
 };
 
-extern "C" {
-kron_status kron_batched_plan_create(kron_batched_plan *plan, int, int, const int64_t *, const int64_t *,
-                                     kron_dtype, kron_prec, unsigned) {
-    if (plan) *plan = nullptr;
-    return KRON_ERR_UNSUPPORTED;
+template <int F>
+__global__ void batched_bimage_kernel(const ImgJob *__restrict__ jobs, int njobs, int64_t total) {
+    using T = FT<F>;
+    constexpr int BK = kRowBytes / T::ELEM;
+    constexpr int CH = 16 / T::ELEM;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = njobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].begin <= idx) lo = mid;
+            else hi = mid - 1;
+        }
+        const ImgJob &J = jobs[lo];
+        int64_t r = idx - J.begin;
+        const int ch = (int)(r % kChunks);
+        r /= kChunks;
+        const int row = (int)(r % J.BN);
+        r /= J.BN;
+        const int64_t KB = (J.K + BK - 1) / BK;
+        const int64_t kb = r % KB;
+        const int64_t nt = r / KB;
+        const int64_t c = nt * J.BN + row;
+        const int64_t ro = c < J.N ? c : -1;  // L is n x m with ld: element (c, k) at c + ld * k
+        const IdxMap km{0, J.ld, 0};
+        uint4 out[T::PIECES];
+        if (J.l64) load_split<F, double>(static_cast<const double *>(J.L), ro, km, kb * BK + ch * CH, J.K, out);
+        else load_split<F, float>(static_cast<const float *>(J.L), ro, km, kb * BK + ch * CH, J.K, out);
+        uint8_t *base = J.img + (size_t)((nt * KB + kb) * T::PIECES) * J.BN * kRowBytes;
+        const uint32_t off = swz(row, ch);
+#pragma unroll
+        for (int q = 0; q < T::PIECES; ++q) *reinterpret_cast<uint4 *>(base + (size_t)q * J.BN * kRowBytes + off) = out[q];
+    }
 }
+
+}  // namespace
+}  // namespace kron
+
+using namespace kron;
+
+struct kron_batched_plan_s {
+    int batch = 0, d = 0;
+    kron_dtype dtype = KRON_F32;
+    kron_prec prec = KRON_PREC_3XTF32;
+    int form = 0;
+    std::vector<int64_t> m, n;          // batch * d
+    std::vector<int> order;             // batch * d
+    // job sequence: (problem, step) in launch order
+    std::vector<std::pair<int, int>> seq;
+    // workspace layout
+    std::vector<size_t> img_off;        // batch * d (per mode)
+    std::vector<size_t> buf_off;        // batch * (d - 1) intermediates
+    size_t imgjob_off = 0, imgjob_bytes = 0;
+    size_t table_off = 0, table_bytes = 0;
+    size_t done_off = 0, done_bytes = 0;
+    size_t ws_bytes = 0;
+    double flops = 0;
+    int64_t img_items = 0;
+    // bound state
+    TcpJobs jobs;
+    std::vector<ImgJob> imgjobs;
+    uint8_t *pinned = nullptr;          // staging for the uploads
+    size_t pinned_bytes = 0;
+    bool bound = false;
+    void *bound_ws = nullptr;
+};
+
+namespace {
+
+int64_t prodv(const int64_t *v, int d) {
+    int64_t p = 1;
+    for (int k = 0; k < d; ++k) p *= v[k];
+    return p;
+}
+
+void problem_order(int d, const int64_t *m, const int64_t *n, int *order) {
+    int perm[KRON_MAX_D];
+    for (int k = 0; k < d; ++k) perm[k] = order[k] = k;
+    long double best = -1;
+    do {
+        int64_t cur[KRON_MAX_D];
+        for (int k = 0; k < d; ++k) cur[k] = m[k];
+        long double fl = 0;
+        for (int s = 0; s < d; ++s) {
+            fl += 2.0L * n[perm[s]] * (long double)prodv(cur, d);
+            cur[perm[s]] = n[perm[s]];
+        }
+        if (best < 0 || fl < best * (1 - 1e-12L)) {
+            best = fl;
+            for (int k = 0; k < d; ++k) order[k] = perm[k];
+        }
+    } while (std::next_permutation(perm, perm + d));
+}
+
+int kb_of(int form) { return form == kTF32x3 ? kRowBytes / 4 : kRowBytes / 2; }
+
+}  // namespace
+
+extern "C" {
+
+kron_status kron_batched_plan_create(kron_batched_plan *plan, int batch, int d, const int64_t *m, const int64_t *n,
+                                     kron_dtype dtype, kron_prec prec, unsigned flags) {
+    if (!plan) return KRON_ERR_INVALID_ARG;
+    *plan = nullptr;
+    if (batch < 1 || batch > 65536 || d < 1 || d > KRON_MAX_D || !m || !n || flags != 0) return KRON_ERR_INVALID_ARG;
+    if (dtype != KRON_F64 && dtype != KRON_F32) return KRON_ERR_INVALID_ARG;
+    if (prec < KRON_PREC_FP64 || prec > KRON_PREC_BF16X6) return KRON_ERR_INVALID_ARG;
+    if (!is_split(prec)) return KRON_ERR_UNSUPPORTED;
+    for (int64_t i = 0; i < (int64_t)batch * d; ++i)
+        if (m[i] < 1 || n[i] < 1 || m[i] > (1 << 20) || n[i] > (1 << 20)) return KRON_ERR_INVALID_ARG;
+    auto *pl = new (std::nothrow) kron_batched_plan_s();
+    if (!pl) return KRON_ERR_INVALID_ARG;
+    pl->batch = batch;
+    pl->d = d;
+    pl->dtype = dtype;
+    pl->prec = prec;
+    pl->form = form_of(prec);
+    pl->m.assign(m, m + (size_t)batch * d);
+    pl->n.assign(n, n + (size_t)batch * d);
+    pl->order.resize((size_t)batch * d);
+    const size_t isz = 4;  // FP32 intermediates
+    size_t off = 0;
+    pl->img_off.resize((size_t)batch * d);
+    pl->buf_off.assign((size_t)batch * std::max(d - 1, 1), 0);
+    std::vector<size_t> inter_bytes(batch, 0);
+    for (int b = 0; b < batch; ++b) {
+        const int64_t *mb = &pl->m[(size_t)b * d];
+        const int64_t *nb = &pl->n[(size_t)b * d];
+        problem_order(d, mb, nb, &pl->order[(size_t)b * d]);
+        int64_t cur[KRON_MAX_D];
+        for (int k = 0; k < d; ++k) cur[k] = mb[k];
+        for (int s = 0; s < d; ++s) {
+            const int mu = pl->order[(size_t)b * d + s];
+            pl->flops += 2.0 * (double)nb[mu] * (double)prodv(cur, d);
+            cur[mu] = nb[mu];
+            if (s < d - 1) {
+                pl->buf_off[(size_t)b * (d - 1) + s] = off;
+                const size_t by = al((size_t)prodv(cur, d) * isz);
+                off += by;
+                inter_bytes[b] += by;
+            }
+        }
+        for (int k = 0; k < d; ++k) {
+            pl->img_off[(size_t)b * d + k] = off;
+            off += al(tc_bimage_bytes(pl->form, nb[k], mb[k]));
+            const int bn = tc_tile_n(pl->form, nb[k]);
+            const int64_t nt = (nb[k] + bn - 1) / bn;
+            const int64_t kb = (mb[k] + kb_of(pl->form) - 1) / kb_of(pl->form);
+            pl->img_items += nt * kb * bn * kChunks;
+        }
+    }
+    // waves: groups of problems whose intermediates take about 32 MB
+    std::vector<int> group(batch, 0);
+    int ng = 0;
+    size_t acc = 0;
+    for (int b = 0; b < batch; ++b) {
+        if (acc > 0 && acc + inter_bytes[b] > (32u << 20)) {
+            ++ng;
+            acc = 0;
+        }
+        group[b] = ng;
+        acc += inter_bytes[b];
+    }
+    ++ng;
+    for (int w = 0; w < ng + d - 1; ++w)
+        for (int s = 0; s < d; ++s) {
+            const int g = w - s;
+            if (g < 0 || g >= ng) continue;
+            for (int b = 0; b < batch; ++b)
+                if (group[b] == g) pl->seq.emplace_back(b, s);
+        }
+    const size_t njobs = pl->seq.size();
+    pl->imgjob_off = off;
+    pl->imgjob_bytes = al(sizeof(ImgJob) * (size_t)batch * d);
+    off += pl->imgjob_bytes;
+    pl->table_off = off;
+    pl->table_bytes = al(tcp_job_bytes() * njobs);
+    off += pl->table_bytes;
+    pl->done_off = off;
+    pl->done_bytes = al(sizeof(int) * njobs);
+    off += pl->done_bytes;
+    pl->ws_bytes = off;
+    pl->pinned_bytes = pl->imgjob_bytes + pl->table_bytes;
+    if (cudaMallocHost(reinterpret_cast<void **>(&pl->pinned), pl->pinned_bytes) != cudaSuccess) {
+        delete pl;
+        return KRON_ERR_CUDA;
+    }
+    *plan = pl;
+    return KRON_OK;
+}
+
 kron_status kron_batched_plan_destroy(kron_batched_plan plan) {
+    if (!plan) return KRON_OK;
+    if (plan->pinned) {
+        // the staging buffer may still feed an upload in flight
+        cudaDeviceSynchronize();
+        cudaFreeHost(plan->pinned);
+    }
     delete plan;
     return KRON_OK;
 }
-kron_status kron_batched_workspace_size(kron_batched_plan, size_t *) { return KRON_ERR_UNSUPPORTED; }
-double kron_batched_flops(kron_batched_plan) { return 0.0; }
-kron_status kron_batched_bind(kron_batched_plan, const void *const *, const void *const *, void *const *,
-                              void *, size_t, kron_stream_t) {
-    return KRON_ERR_UNSUPPORTED;
+
+kron_status kron_batched_workspace_size(kron_batched_plan plan, size_t *bytes) {
+    if (!plan || !bytes) return KRON_ERR_INVALID_ARG;
+    *bytes = plan->ws_bytes;
+    return KRON_OK;
 }
-kron_status kron_batched_run(kron_batched_plan, void *, size_t, kron_stream_t) { return KRON_ERR_UNSUPPORTED; }
+
+double kron_batched_flops(kron_batched_plan plan) { return plan ? plan->flops : 0.0; }
+
+kron_status kron_batched_bind(kron_batched_plan plan, const void *const *T, const void *const *L, void *const *S,
+                              void *ws, size_t ws_bytes, kron_stream_t stream) {
+    if (!plan || !T || !L || !S || !ws) return KRON_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(ws) % kAl) return KRON_ERR_ALIGNMENT;
+    if (ws_bytes < plan->ws_bytes) return KRON_ERR_WORKSPACE;
+    const int d = plan->d, batch = plan->batch;
+    const size_t es = plan->dtype == KRON_F64 ? 8 : 4;
+    for (int b = 0; b < batch; ++b) {
+        if (!T[b] || !S[b]) return KRON_ERR_INVALID_ARG;
+        if (reinterpret_cast<uintptr_t>(T[b]) % es || reinterpret_cast<uintptr_t>(S[b]) % es) return KRON_ERR_ALIGNMENT;
+        for (int k = 0; k < d; ++k) {
+            const void *l = L[(size_t)b * d + k];
+            if (!l) return KRON_ERR_INVALID_ARG;
+            if (reinterpret_cast<uintptr_t>(l) % es) return KRON_ERR_ALIGNMENT;
+        }
+    }
+    auto *w = static_cast<uint8_t *>(ws);
+    const bool io64 = plan->dtype == KRON_F64;
+    // image jobs
+    plan->imgjobs.assign((size_t)batch * d, ImgJob{});
+    int64_t begin = 0;
+    for (int b = 0; b < batch; ++b)
+        for (int k = 0; k < d; ++k) {
+            ImgJob &J = plan->imgjobs[(size_t)b * d + k];
+            J.L = L[(size_t)b * d + k];
+            J.N = plan->n[(size_t)b * d + k];
+            J.K = plan->m[(size_t)b * d + k];
+            J.ld = J.N;
+            J.img = w + plan->img_off[(size_t)b * d + k];
+            J.BN = tc_tile_n(plan->form, J.N);
+            J.l64 = io64;
+            const int64_t nt = (J.N + J.BN - 1) / J.BN;
+            const int64_t kb = (J.K + kb_of(plan->form) - 1) / kb_of(plan->form);
+            J.items = nt * kb * J.BN * kChunks;
+            J.begin = begin;
+            begin += J.items;
+        }
+    // tensor-core jobs in launch order; job index of (b, s) for dependencies
+    tcp_jobs_begin(plan->jobs, plan->form);
+    std::vector<int> jid((size_t)batch * d, -1);
+    for (const auto &bs : plan->seq) {
+        const int b = bs.first, s = bs.second;
+        const int64_t *mb = &plan->m[(size_t)b * d];
+        const int64_t *nb = &plan->n[(size_t)b * d];
+        const int *ord = &plan->order[(size_t)b * d];
+        int64_t cur[KRON_MAX_D];
+        for (int k = 0; k < d; ++k) cur[k] = mb[k];
+        for (int j = 0; j < s; ++j) cur[ord[j]] = nb[ord[j]];
+        const int mu = ord[s];
+        int64_t P = 1, Q = 1;
+        for (int k = 0; k < mu; ++k) P *= cur[k];
+        for (int k = mu + 1; k < d; ++k) Q *= cur[k];
+        const int64_t mm = cur[mu], nn = nb[mu];
+        const void *src = (s == 0) ? T[b] : (const void *)(w + plan->buf_off[(size_t)b * (d - 1) + s - 1]);
+        const bool src64 = (s == 0) ? io64 : false;
+        void *dst = (s == d - 1) ? S[b] : (void *)(w + plan->buf_off[(size_t)b * (d - 1) + s]);
+        const bool dst64 = (s == d - 1) ? io64 : false;
+        Contraction c;
+        c.M = P * Q;
+        c.N = nn;
+        c.K = mm;
+        c.A = src;
+        c.A_f64 = src64;
+        if (P == 1) {
+            c.rowA = IdxMap{0, mm, 0};
+            c.rowC = IdxMap{0, nn, 0};
+        } else {
+            c.rowA = IdxMap{P, 1, P * mm};
+            c.rowC = IdxMap{P, 1, P * nn};
+        }
+        c.kA = IdxMap{0, P, 0};
+        c.C = dst;
+        c.C_f64 = dst64;
+        c.colC = IdxMap{0, P, 0};
+        const int dep = (s == 0) ? -1 : jid[(size_t)b * d + s - 1];
+        jid[(size_t)b * d + s] = tcp_jobs_add(plan->jobs, c, w + plan->img_off[(size_t)b * d + mu], dep);
+    }
+    // upload both tables (one copy from the pinned staging buffer)
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(cs) != cudaSuccess) return KRON_ERR_CUDA;  // staging buffer reuse
+    std::memcpy(plan->pinned, plan->imgjobs.data(), sizeof(ImgJob) * plan->imgjobs.size());
+    std::memcpy(plan->pinned + plan->imgjob_bytes, plan->jobs.host.data(), plan->jobs.host.size());
+    if (cudaMemcpyAsync(w + plan->imgjob_off, plan->pinned, plan->imgjob_bytes + plan->table_bytes,
+                        cudaMemcpyHostToDevice, cs) != cudaSuccess)
+        return KRON_ERR_CUDA;
+    plan->bound = true;
+    plan->bound_ws = ws;
+    return KRON_OK;
 }
+
+kron_status kron_batched_run(kron_batched_plan plan, void *ws, size_t ws_bytes, kron_stream_t stream) {
+    if (!plan || !ws) return KRON_ERR_INVALID_ARG;
+    if (!plan->bound || ws != plan->bound_ws) return KRON_ERR_INVALID_ARG;
+    if (ws_bytes < plan->ws_bytes) return KRON_ERR_WORKSPACE;
+    auto *w = static_cast<uint8_t *>(ws);
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t total = plan->img_items;
+    const int threads = 256;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + threads - 1) / threads, 152 * 32));
+    const auto *ij = reinterpret_cast<const ImgJob *>(w + plan->imgjob_off);
+    const int nij = (int)plan->imgjobs.size();
+    switch (plan->form) {
+        case kTF32x3: batched_bimage_kernel<kTF32x3><<<blocks, threads, 0, cs>>>(ij, nij, total); break;
+        case kBF16x3: batched_bimage_kernel<kBF16x3><<<blocks, threads, 0, cs>>>(ij, nij, total); break;
+        case kBF16x6: batched_bimage_kernel<kBF16x6><<<blocks, threads, 0, cs>>>(ij, nij, total); break;
+        default: return KRON_ERR_UNSUPPORTED;
+    }
+    if (cudaGetLastError() != cudaSuccess) return KRON_ERR_CUDA;
+    if (tcp_jobs_run(plan->jobs, w + plan->table_off, reinterpret_cast<int *>(w + plan->done_off), cs) != cudaSuccess)
+        return KRON_ERR_CUDA;
+    return KRON_OK;
+}
+
+}  // extern "C"

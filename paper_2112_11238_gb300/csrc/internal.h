@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "../../include/kron.h"
 
 namespace kron {
@@ -66,6 +68,26 @@ cudaError_t tc_contract_bimage(int form, const Contraction &c, const void *img, 
 // fixed order into C.  Returns the number of splits used via *splits.
 size_t tc_splitk_partial_bytes(int64_t M, int64_t N, int64_t K);
 cudaError_t tc_contract_splitk(int form, const Contraction &c, float *partial, cudaStream_t st);
+
+// ---- persistent tensor-core path (tcp.cu) ----
+// One contraction (B from an image made by tc_build_bimage).
+cudaError_t tcp_contract(int form, const Contraction &c, const void *img, cudaStream_t st);
+// A table of contractions run by one persistent launch; a job may wait for
+// an earlier one (dep = its index) whose output it reads.
+struct TcpJobs {
+    int form = 0;
+    std::vector<uint8_t> host;  // packed device job records
+    int total_tiles = 0;
+    int bn_max = 16;
+    int nkb_max = 1;
+};
+size_t tcp_job_bytes();
+void tcp_jobs_begin(TcpJobs &jobs, int form);
+int tcp_jobs_add(TcpJobs &jobs, const Contraction &c, const void *img, int dep);
+size_t tcp_jobs_table_bytes(const TcpJobs &jobs);
+// `table`: device copy of jobs.host (needed above 8 jobs); `done`: one int per
+// job of device scratch (zeroed by the call).
+cudaError_t tcp_jobs_run(const TcpJobs &jobs, const void *table, int *done, cudaStream_t st);
 
 // ---- CUDA-core path (simt.cu) ----
 // FP64 (f64 = true) or FP32 fused multiply-add.

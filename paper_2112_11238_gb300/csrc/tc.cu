@@ -9,7 +9,7 @@
 //   major tensor through a 2-level index map (no permute; the slab view of
 //   the mu-unfolding is an index map, cf. the remark on permutations in
 //   Section 2).  Converter warps load a 128 x BK tile, split every value into
-//   TF32 or BF16 pieces and write each piece K-major with the 128-byte
+//   TF32 or BF16 pieces and write each piece K-major with the 64-byte
 //   swizzle into shared memory.
 // * B (the small matrix op(L_mu)) is split and swizzled once per call into a
 //   global "image" laid out exactly like its shared-memory tiles, and one
@@ -22,50 +22,14 @@
 //
 // Pipelining: `stages` shared-memory stages guarded by full/empty mbarriers;
 // every wait is bounded (ptx.cuh) so a fault never hangs the GPU.
-#include <cuda_bf16.h>
-
 #include <algorithm>
 #include <mutex>
 
-#include "internal.h"
-#include "ptx.cuh"
+#include "tc_common.cuh"
 
 namespace kron {
 
-template <int F>
-struct FT;
-template <>
-struct FT<kTF32x3> {
-    static constexpr int KIND = 0, PIECES = 2, ELEM = 4, NPROD = 3, FMT = 2, MMA_K = 8;
-};
-template <>
-struct FT<kBF16x3> {
-    static constexpr int KIND = 1, PIECES = 2, ELEM = 2, NPROD = 3, FMT = 1, MMA_K = 16;
-};
-template <>
-struct FT<kBF16x6> {
-    static constexpr int KIND = 1, PIECES = 3, ELEM = 2, NPROD = 6, FMT = 1, MMA_K = 16;
-};
-
-// Products (piece of A, piece of B), smallest magnitude first.
-template <int F>
-__device__ __forceinline__ void prod_pieces(int i, int &pa, int &pb) {
-    if constexpr (FT<F>::PIECES == 2) {
-        // lo*hi, hi*lo, hi*hi
-        pa = (i == 0) ? 1 : 0;
-        pb = (i == 1) ? 1 : 0;
-    } else {
-        // (2,0) (1,1) (0,2) (1,0) (0,1) (0,0)
-        const int ta[6] = {2, 1, 0, 1, 0, 0};
-        const int tb[6] = {0, 1, 2, 0, 1, 0};
-        pa = ta[i];
-        pb = tb[i];
-    }
-}
-
-constexpr int kRowBytes = 128;      // bytes of one K-major row per K-block
-constexpr int kBM = 128;            // rows per tile (MMA M)
-constexpr int kConvWarps = 8;       // converter warps
+constexpr int kConvWarps = 16;      // converter warps
 constexpr int kThreads = 64 + 32 * kConvWarps;
 
 struct TcDev {
@@ -86,80 +50,8 @@ struct TcDev {
     int stages;
     int nacc;          // accumulators in tensor memory (K-blocks round-robin)
     int a64, b64, c64, acc;
+    int avec;          // A rows are contiguous along k and 16-byte aligned chunks
 };
-
-__device__ __forceinline__ int64_t imap(const IdxMap &m, int64_t x) {
-    if (m.R0 == 0) return x * m.s0;
-    return (x % m.R0) * m.s0 + (x / m.R0) * m.s1;
-}
-
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ void to_hl(float x, float &h, float &l) {
-    h = x;
-    l = 0.f;
-}
-__device__ __forceinline__ void to_hl(double x, float &h, float &l) {
-    h = __double2float_rn(x);
-    l = __double2float_rn(x - (double)h);
-}
-
-// Loads CH consecutive-k values of one row (zero outside the tensor), splits
-// them into the form's pieces and packs each piece as one 16-byte chunk.
-template <int F, typename Tin>
-__device__ __forceinline__ void load_split(const Tin *__restrict__ src, int64_t ro, const IdxMap &km,
-                                           int64_t k0, int64_t K, uint4 (&out)[FT<F>::PIECES]) {
-    constexpr int CH = 16 / FT<F>::ELEM;
-    float h[CH], l[CH];
-#pragma unroll
-    for (int e = 0; e < CH; ++e) {
-        const int64_t k = k0 + e;
-        if (ro >= 0 && k < K) {
-            const Tin x = __ldg(src + ro + imap(km, k));
-            to_hl(x, h[e], l[e]);
-        } else {
-            h[e] = 0.f;
-            l[e] = 0.f;
-        }
-    }
-    if constexpr (F == kTF32x3) {
-        uint32_t a0[4], a1[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            a0[e] = to_tf32(h[e]);
-            const float r = (h[e] - __uint_as_float(a0[e])) + l[e];
-            a1[e] = to_tf32(r);
-        }
-        out[0] = make_uint4(a0[0], a0[1], a0[2], a0[3]);
-        out[1] = make_uint4(a1[0], a1[1], a1[2], a1[3]);
-    } else {
-        uint32_t w[FT<F>::PIECES][8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const __nv_bfloat16 b0 = __float2bfloat16_rn(h[e]);
-            const float r = (h[e] - __bfloat162float(b0)) + l[e];
-            const __nv_bfloat16 b1 = __float2bfloat16_rn(r);
-            w[0][e] = __bfloat16_as_ushort(b0);
-            w[1][e] = __bfloat16_as_ushort(b1);
-            if constexpr (FT<F>::PIECES == 3) {
-                const __nv_bfloat16 b2 = __float2bfloat16_rn(r - __bfloat162float(b1));
-                w[2][e] = __bfloat16_as_ushort(b2);
-            }
-        }
-#pragma unroll
-        for (int p = 0; p < FT<F>::PIECES; ++p)
-            out[p] = make_uint4(w[p][0] | (w[p][1] << 16), w[p][2] | (w[p][3] << 16),
-                                w[p][4] | (w[p][5] << 16), w[p][6] | (w[p][7] << 16));
-    }
-}
-
-__device__ __forceinline__ uint32_t swz128(int row, int ch) {
-    return (uint32_t)row * kRowBytes + ((uint32_t)(ch ^ (row & 7)) << 4);
-}
 
 // Converts one R-row tile (rows given by precomputed offsets, -1 = padding)
 // for the K-block starting at kbase into `dst` (piece tiles `piece_bytes`
@@ -171,22 +63,101 @@ __device__ __forceinline__ void conv_tile(const Tin *__restrict__ src, const int
                                           const IdxMap &km, int64_t kbase, int64_t K, uint8_t *dst,
                                           uint32_t piece_bytes, int t) {
     constexpr int CH = 16 / FT<F>::ELEM;
-    const int items = R * 8;
+    const int items = R * kChunks;
     for (int it = t; it < items; it += 32 * kConvWarps) {
         int row, ch;
         if constexpr (KC) {
-            ch = it & 7;
-            row = it >> 3;
+            ch = it % kChunks;
+            row = it / kChunks;
         } else {
             row = it % R;
             ch = it / R;
         }
         uint4 out[FT<F>::PIECES];
         load_split<F, Tin>(src, rowoff[row], km, kbase + ch * CH, K, out);
-        const uint32_t off = swz128(row, ch);
+        const uint32_t off = swz(row, ch);
 #pragma unroll
         for (int p = 0; p < FT<F>::PIECES; ++p)
             *reinterpret_cast<uint4 *>(dst + p * piece_bytes + off) = out[p];
+    }
+}
+
+// Items (row, 16-byte chunk) of the 128-row A tile owned by converter thread t.
+constexpr int kItemsA = kBM * kChunks / (32 * kConvWarps);
+
+template <bool KC>
+__device__ __forceinline__ void item_of(int it, int R, int &row, int &ch) {
+    if constexpr (KC) {
+        ch = it % kChunks;
+        row = it / kChunks;
+    } else {
+        row = it % R;
+        ch = it / R;
+    }
+}
+
+template <int F, typename Tin, bool KC>
+__device__ __forceinline__ void load_a(const Tin *__restrict__ src, const int64_t *rowoff, const IdxMap &km,
+                                       int64_t kbase, int64_t K, bool vec, int t,
+                                       Tin (&v)[kItemsA][16 / FT<F>::ELEM]) {
+    constexpr int CH = 16 / FT<F>::ELEM;
+#pragma unroll
+    for (int i = 0; i < kItemsA; ++i) {
+        int row, ch;
+        item_of<KC>(t + i * 32 * kConvWarps, kBM, row, ch);
+        load_chunk<F, Tin>(src, rowoff[row], km, kbase + ch * CH, K, vec, v[i]);
+    }
+}
+
+template <int F, typename Tin, bool KC>
+__device__ __forceinline__ void store_a(const Tin (&v)[kItemsA][16 / FT<F>::ELEM], uint8_t *dst, int t) {
+#pragma unroll
+    for (int i = 0; i < kItemsA; ++i) {
+        int row, ch;
+        item_of<KC>(t + i * 32 * kConvWarps, kBM, row, ch);
+        uint4 out[FT<F>::PIECES];
+        split_pack<F, Tin>(v[i], out);
+        const uint32_t off = swz(row, ch);
+#pragma unroll
+        for (int q = 0; q < FT<F>::PIECES; ++q)
+            *reinterpret_cast<uint4 *>(dst + q * (kBM * kRowBytes) + off) = out[q];
+    }
+}
+
+// The converter warps' main loop for one source type: the loads of K-block
+// kb+1 are issued right after K-block kb is handed to the MMA warp, so they
+// are in flight while the warp waits for the next free stage.
+template <int F, typename Tin, bool AKC, bool BIMG, bool BKC>
+__device__ __forceinline__ void converter_loop(const TcDev &p, const Tin *__restrict__ A, const int64_t *rowA,
+                                               const int64_t *rowB, uint8_t *sA, uint8_t *sB, uint64_t *full,
+                                               uint64_t *empty, int64_t kb0, int64_t nkb, int S, uint32_t A_ST,
+                                               uint32_t B_ST, uint32_t PIECE_B, int BN, int lane, int t) {
+    constexpr int BK = kRowBytes / FT<F>::ELEM;
+    Tin v[kItemsA][16 / FT<F>::ELEM];
+    const bool vec = p.avec != 0;
+    if (nkb > 0) load_a<F, Tin, AKC>(A, rowA, p.kA, kb0 * BK, p.K, vec, t, v);
+    for (int64_t kb = 0; kb < nkb; ++kb) {
+        const int s = (int)(kb % S);
+        const uint32_t ph = (uint32_t)((kb / S) & 1);
+        // lane 0 waits, the warp follows (keeps the warp converged)
+        int ok = (lane == 0) ? (int)mbar_wait(smem_u32(&empty[s]), ph ^ 1u) : 1;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+        const int64_t kbase = (kb0 + kb) * BK;
+        store_a<F, Tin, AKC>(v, sA + (size_t)s * A_ST, t);
+        if constexpr (!BIMG) {
+            uint8_t *dB = sB + (size_t)s * B_ST;
+            if (p.b64)
+                conv_tile<F, double, BKC>(static_cast<const double *>(p.B), rowB, BN, p.kB, kbase, p.K, dB,
+                                          PIECE_B, t);
+            else
+                conv_tile<F, float, BKC>(static_cast<const float *>(p.B), rowB, BN, p.kB, kbase, p.K, dB,
+                                         PIECE_B, t);
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&full[s]));
+        if (kb + 1 < nkb) load_a<F, Tin, AKC>(A, rowA, p.kA, kbase + BK, p.K, vec, t, v);
     }
 }
 
@@ -310,34 +281,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const TcDev p) {
         __syncwarp();
     } else {
         const int t = threadIdx.x - 64;
-        for (int64_t kb = 0; kb < nkb; ++kb) {
-            const int s = (int)(kb % S);
-            const uint32_t ph = (uint32_t)((kb / S) & 1);
-            // lane 0 waits, the warp follows (keeps the warp converged)
-            int ok = (lane == 0) ? (int)mbar_wait(smem_u32(&empty[s]), ph ^ 1u) : 1;
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) break;
-            const int64_t kbase = (kb0 + kb) * BK;
-            uint8_t *dA = sA + (size_t)s * A_ST;
-            if (p.a64)
-                conv_tile<F, double, AKC>(static_cast<const double *>(p.A), rowA, kBM, p.kA, kbase,
-                                          p.K, dA, PIECE_A, t);
-            else
-                conv_tile<F, float, AKC>(static_cast<const float *>(p.A), rowA, kBM, p.kA, kbase,
-                                         p.K, dA, PIECE_A, t);
-            if constexpr (!BIMG) {
-                uint8_t *dB = sB + (size_t)s * B_ST;
-                if (p.b64)
-                    conv_tile<F, double, BKC>(static_cast<const double *>(p.B), rowB, BN, p.kB,
-                                              kbase, p.K, dB, PIECE_B, t);
-                else
-                    conv_tile<F, float, BKC>(static_cast<const float *>(p.B), rowB, BN, p.kB, kbase,
-                                             p.K, dB, PIECE_B, t);
-            }
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&full[s]));
-        }
+        if (p.a64)
+            converter_loop<F, double, AKC, BIMG, BKC>(p, static_cast<const double *>(p.A), rowA, rowB, sA, sB, full,
+                                                      empty, kb0, nkb, S, A_ST, B_ST, PIECE_B, BN, lane, t);
+        else
+            converter_loop<F, float, AKC, BIMG, BKC>(p, static_cast<const float *>(p.A), rowA, rowB, sA, sB, full,
+                                                     empty, kb0, nkb, S, A_ST, B_ST, PIECE_B, BN, lane, t);
         // Epilogue: warps 2..5 cover the four 32-lane quarters of the accumulator.
         if (warp < 6) {
             int ok = (lane == 0) ? (int)mbar_wait(smem_u32(accf), 0) : 1;
@@ -366,21 +315,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const TcDev p) {
                         }
                     }
                     if (ro >= 0) {
-#pragma unroll
-                        for (int e = 0; e < 16; ++e) {
-                            const int64_t cg = n0 + c0 + e;
-                            if (cg < p.N) {
-                                const int64_t off = zoff + ro + imap(p.colC, cg);
-                                const float val = sum[e];
-                                if (p.c64) {
-                                    double *c = static_cast<double *>(p.C) + off;
-                                    *c = p.acc ? *c + (double)val : (double)val;
-                                } else {
-                                    float *c = static_cast<float *>(p.C) + off;
-                                    *c = p.acc ? *c + val : val;
-                                }
-                            }
-                        }
+                        const int cmax = (int)max((int64_t)0, min((int64_t)16, p.N - n0 - c0));
+                        if (p.c64) store_row16<double>(static_cast<double *>(p.C) + zoff, ro, p.colC, n0 + c0, cmax, sum, p.acc != 0);
+                        else store_row16<float>(static_cast<float *>(p.C) + zoff, ro, p.colC, n0 + c0, cmax, sum, p.acc != 0);
                     }
                 }
             }
@@ -395,18 +332,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const TcDev p) {
 }
 
 // Builds the pre-split, pre-swizzled global image of B:
-//   image[nt][kb][piece][BN rows x 128 bytes]   (row = output column c).
+//   image[nt][kb][piece][BN rows x 64 bytes]   (row = output column c).
 template <int F, typename Tin>
 __global__ void bimage_kernel(const Tin *__restrict__ B, IdxMap colB, IdxMap kB, int64_t N, int64_t K,
                               int BN, int64_t KB, int64_t NT, uint8_t *img) {
     using T = FT<F>;
     constexpr int BK = kRowBytes / T::ELEM;
     constexpr int CH = 16 / T::ELEM;
-    const int64_t total = NT * KB * BN * 8;
+    const int64_t total = NT * KB * BN * kChunks;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        const int ch = (int)(idx & 7);
-        int64_t rest = idx >> 3;
+        const int ch = (int)(idx % kChunks);
+        int64_t rest = idx / kChunks;
         const int row = (int)(rest % BN);
         rest /= BN;
         const int64_t kb = rest % KB;
@@ -416,7 +353,7 @@ __global__ void bimage_kernel(const Tin *__restrict__ B, IdxMap colB, IdxMap kB,
         uint4 out[T::PIECES];
         load_split<F, Tin>(B, ro, kB, kb * BK + ch * CH, K, out);
         uint8_t *base = img + (size_t)((nt * KB + kb) * T::PIECES) * BN * kRowBytes;
-        const uint32_t off = swz128(row, ch);
+        const uint32_t off = swz(row, ch);
 #pragma unroll
         for (int q = 0; q < T::PIECES; ++q)
             *reinterpret_cast<uint4 *>(base + (size_t)q * BN * kRowBytes + off) = out[q];
@@ -448,8 +385,8 @@ __global__ void splitk_reduce_kernel(const float *__restrict__ P, int64_t splits
 cudaError_t tc_error_word(unsigned int *out, bool clear) { return read_error_word(out, clear); }
 
 static int pieces_of(int form) { return form == kBF16x6 ? 3 : 2; }
-static int bk_of(int form) { return form == kTF32x3 ? 32 : 64; }
-static int max_bn(int form) { return form == kBF16x6 ? 128 : 256; }
+static int bk_of(int form) { return form == kTF32x3 ? kRowBytes / 4 : kRowBytes / 2; }
+static int max_bn(int form) { return form == kBF16x6 ? 64 : 128; }
 
 int tc_tile_n(int form, int64_t N) {
     const int64_t mx = max_bn(form);
@@ -544,7 +481,7 @@ cudaError_t tc_build_bimage(int form, const Contraction &c, void *img, cudaStrea
     const int bn = tc_tile_n(form, c.N);
     const int64_t nt = (c.N + bn - 1) / bn;
     const int64_t kb = (c.K + bk_of(form) - 1) / bk_of(form);
-    const int64_t total = nt * kb * bn * 8;
+    const int64_t total = nt * kb * bn * kChunks;
     const int threads = 256;
     const int64_t blocks = std::min<int64_t>((total + threads - 1) / threads, 152 * 16);
     auto *out = static_cast<uint8_t *>(img);
@@ -586,6 +523,13 @@ static TcDev make_dev(int form, const Contraction &c, int bn) {
     d.b64 = c.B_f64;
     d.c64 = c.C_f64;
     d.acc = c.accumulate;
+    {
+        const int64_t v = c.A_f64 ? 2 : 4;  // elements per 16 bytes
+        const bool unit_k = c.kA.R0 == 0 && c.kA.s0 == 1;
+        const bool rows_ok = (c.rowA.s0 % v == 0) && (c.rowA.R0 == 0 || c.rowA.s1 % v == 0);
+        const bool base_ok = (reinterpret_cast<uintptr_t>(c.A) % 16) == 0;
+        d.avec = (unit_k && rows_ok && base_ok) ? 1 : 0;
+    }
     d.czstride = 0;
     return d;
 }

@@ -1,0 +1,193 @@
+// tc_common.cuh -- pieces shared by the tensor-core kernels: the split forms,
+// index maps, loading and splitting of operand chunks, and the
+// swizzled (64-byte) K-major shared-memory layout the tcgen05 descriptors
+// describe.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace kron {
+
+template <int F>
+struct FT;
+template <>
+struct FT<kTF32x3> {
+    static constexpr int KIND = 0, PIECES = 2, ELEM = 4, NPROD = 3, FMT = 2, MMA_K = 8;
+};
+template <>
+struct FT<kBF16x3> {
+    static constexpr int KIND = 1, PIECES = 2, ELEM = 2, NPROD = 3, FMT = 1, MMA_K = 16;
+};
+template <>
+struct FT<kBF16x6> {
+    static constexpr int KIND = 1, PIECES = 3, ELEM = 2, NPROD = 6, FMT = 1, MMA_K = 16;
+};
+
+// Products (piece of A, piece of B), smallest magnitude first.
+template <int F>
+__device__ __forceinline__ void prod_pieces(int i, int &pa, int &pb) {
+    if constexpr (FT<F>::PIECES == 2) {
+        // lo*hi, hi*lo, hi*hi
+        pa = (i == 0) ? 1 : 0;
+        pb = (i == 1) ? 1 : 0;
+    } else {
+        // (2,0) (1,1) (0,2) (1,0) (0,1) (0,0)
+        const int ta[6] = {2, 1, 0, 1, 0, 0};
+        const int tb[6] = {0, 1, 2, 0, 1, 0};
+        pa = ta[i];
+        pb = tb[i];
+    }
+}
+
+constexpr int kRowBytes = 64;       // bytes of one K-major row per K-block (64-byte swizzle)
+constexpr int kChunks = kRowBytes / 16;  // 16-byte chunks per row
+constexpr int kBM = 128;            // rows per tile (MMA M)
+
+__device__ __forceinline__ int64_t imap(const IdxMap &m, int64_t x) {
+    if (m.R0 == 0) return x * m.s0;
+    return (x % m.R0) * m.s0 + (x / m.R0) * m.s1;
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void to_hl(float x, float &h, float &l) {
+    h = x;
+    l = 0.f;
+}
+__device__ __forceinline__ void to_hl(double x, float &h, float &l) {
+    h = __double2float_rn(x);
+    l = __double2float_rn(x - (double)h);
+}
+
+// Loads CH consecutive-k values of one row (zero outside the tensor).  VEC:
+// the CH values are contiguous and 16-byte aligned whenever fully in range.
+// COH: coherent L2 loads (ld.global.cg) for data written earlier in the same
+// launch by other CTAs; otherwise read-only loads (ld.global.nc).
+template <bool COH, typename T>
+__device__ __forceinline__ T ldx(const T *p) {
+    if constexpr (COH) return __ldcg(p);
+    else return __ldg(p);
+}
+
+template <int F, typename Tin, bool COH = false>
+__device__ __forceinline__ void load_chunk(const Tin *__restrict__ src, int64_t ro, const IdxMap &km,
+                                           int64_t k0, int64_t K, bool vec, Tin (&v)[16 / FT<F>::ELEM]) {
+    constexpr int CH = 16 / FT<F>::ELEM;
+    if (vec && ro >= 0 && k0 + CH <= K) {
+        const uint4 *q = reinterpret_cast<const uint4 *>(src + ro + k0);
+        constexpr int NV = CH * (int)sizeof(Tin) / 16;
+        uint4 w[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) w[i] = ldx<COH>(q + i);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) *reinterpret_cast<uint4 *>(&v[i * (16 / sizeof(Tin))]) = w[i];
+        return;
+    }
+#pragma unroll
+    for (int e = 0; e < CH; ++e) {
+        const int64_t k = k0 + e;
+        v[e] = (ro >= 0 && k < K) ? ldx<COH>(src + ro + imap(km, k)) : Tin(0);
+    }
+}
+
+// Splits CH values into the form's pieces, one 16-byte chunk per piece.
+template <int F, typename Tin>
+__device__ __forceinline__ void split_pack(const Tin (&v)[16 / FT<F>::ELEM], uint4 (&out)[FT<F>::PIECES]) {
+    constexpr int CH = 16 / FT<F>::ELEM;
+    float h[CH], l[CH];
+#pragma unroll
+    for (int e = 0; e < CH; ++e) to_hl(v[e], h[e], l[e]);
+    if constexpr (F == kTF32x3) {
+        uint32_t a0[4], a1[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            a0[e] = to_tf32(h[e]);
+            const float r = (h[e] - __uint_as_float(a0[e])) + l[e];
+            a1[e] = to_tf32(r);
+        }
+        out[0] = make_uint4(a0[0], a0[1], a0[2], a0[3]);
+        out[1] = make_uint4(a1[0], a1[1], a1[2], a1[3]);
+    } else {
+        uint32_t w[FT<F>::PIECES][8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const __nv_bfloat16 b0 = __float2bfloat16_rn(h[e]);
+            const float r = (h[e] - __bfloat162float(b0)) + l[e];
+            const __nv_bfloat16 b1 = __float2bfloat16_rn(r);
+            w[0][e] = __bfloat16_as_ushort(b0);
+            w[1][e] = __bfloat16_as_ushort(b1);
+            if constexpr (FT<F>::PIECES == 3) {
+                const __nv_bfloat16 b2 = __float2bfloat16_rn(r - __bfloat162float(b1));
+                w[2][e] = __bfloat16_as_ushort(b2);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < FT<F>::PIECES; ++p)
+            out[p] = make_uint4(w[p][0] | (w[p][1] << 16), w[p][2] | (w[p][3] << 16),
+                                w[p][4] | (w[p][5] << 16), w[p][6] | (w[p][7] << 16));
+    }
+}
+
+template <int F, typename Tin>
+__device__ __forceinline__ void load_split(const Tin *__restrict__ src, int64_t ro, const IdxMap &km,
+                                           int64_t k0, int64_t K, uint4 (&out)[FT<F>::PIECES]) {
+    Tin v[16 / FT<F>::ELEM];
+    load_chunk<F, Tin>(src, ro, km, k0, K, false, v);
+    split_pack<F, Tin>(v, out);
+}
+
+// Byte offset of 16-byte chunk `ch` of row `row` in a K-major tile with the
+// 64-byte swizzle: rows 64 bytes apart, chunk index XOR-ed with bits 1..2 of
+// the row (address bits 4..5 ^= bits 7..8), tile base 1024-byte aligned.
+__device__ __forceinline__ uint32_t swz(int row, int ch) {
+    return (uint32_t)row * kRowBytes + ((uint32_t)(ch ^ ((row >> 1) & 3)) << 4);
+}
+
+// Stores 16 consecutive output columns of one row: C[ro + colC(c0 + e)],
+// e < cmax.  The accumulate flag is tested once (no speculative loads of C
+// when it is off); unit-stride aligned rows use 16-byte stores.
+template <typename To>
+__device__ __forceinline__ void store_row16(void *C, int64_t ro, const IdxMap &colC, int64_t c0, int cmax,
+                                            const float (&v)[16], bool acc) {
+    To *base = static_cast<To *>(C) + ro;
+    if (colC.R0 != 0) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+            if (e < cmax) {
+                To *d = base + imap(colC, c0 + e);
+                *d = acc ? (To)(*d + (To)v[e]) : (To)v[e];
+            }
+        return;
+    }
+    const int64_t cs = colC.s0;
+    To *cp = base + c0 * cs;
+    if (acc) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+            if (e < cmax) cp[e * cs] += (To)v[e];
+        return;
+    }
+    if (cs == 1 && cmax == 16 && (reinterpret_cast<uintptr_t>(cp) & 15) == 0) {
+        if constexpr (sizeof(To) == 4) {
+#pragma unroll
+            for (int e = 0; e < 16; e += 4)
+                *reinterpret_cast<float4 *>(cp + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 16; e += 2)
+                *reinterpret_cast<double2 *>(cp + e) = make_double2((double)v[e], (double)v[e + 1]);
+        }
+        return;
+    }
+#pragma unroll
+    for (int e = 0; e < 16; ++e)
+        if (e < cmax) cp[e * cs] = (To)v[e];
+}
+
+}  // namespace kron

@@ -1,0 +1,700 @@
+// tcp.cu -- persistent, warp-specialised tensor-core kernel for mu-mode
+// products (Eq. (mmp)), used by the Tucker chain, the stepper and the batched
+// Tucker operators.
+//
+// One launch runs a table of "jobs"; each job is one contraction
+//     C[r, c] = sum_k A[r, k] * op(L)[c, k]
+// with A the tensor read through its index maps and converted/split on the
+// fly, and op(L) read from its pre-split, pre-swizzled image.  A job may wait
+// for another job of the same launch (the next mode of the same tensor), so a
+// whole batch of Tucker operators runs in one launch.
+//
+// Roles (one CTA per SM, looping over tiles t = blockIdx.x + i * gridDim.x):
+//   warp 0        bulk-copies the image tile of op(L) for every K-block
+//   warp 1        issues tcgen05.mma (single thread) into tensor memory
+//   warps 2..5    epilogue: tensor memory -> registers -> C, one row per thread
+//   warps 6..13   converters: A tile (128 rows x one K-block) -> split pieces
+//                 in 64-byte-swizzled K-major shared memory
+// Stages are guarded by full/empty mbarriers, accumulators by acc_full /
+// acc_empty mbarriers; with two accumulator buffers the epilogue of tile i
+// overlaps the main loop of tile i+1.  Every wait is bounded.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "tc_common.cuh"
+
+namespace kron {
+
+namespace {
+
+constexpr int kConv = 8;                            // converter warps
+constexpr int kEpi = 4;                             // epilogue warps
+constexpr int kConv0 = 2 + kEpi;                      // first converter warp
+constexpr int kPThreads = 32 * (kConv0 + kConv);     // 448 threads
+constexpr int kItems = kBM * kChunks / (32 * kConv);  // (row, chunk) items per converter thread
+constexpr int kMaxInline = 8;
+
+struct TcJob {
+    const void *A;
+    IdxMap rowA, kA;
+    int64_t M;
+    const uint8_t *bimg;
+    int64_t kb_img;    // K-blocks per N-tile in the image
+    void *C;
+    IdxMap rowC, colC;
+    int64_t N, K;
+    int32_t kb0, nkb;  // K-block range of the job
+    int32_t BN;        // N-tile width (image layout)
+    int32_t tiles_m, tiles_n, tile_begin;
+    int32_t dep, dep_tiles;
+    int32_t a64, c64, acc, avec, akc;
+    int32_t publish;   // some later job waits for this one
+    int32_t cp16;      // FP32 source: 16-byte asynchronous copies are legal
+};
+
+// Raw (unsplit FP32) A tiles staged by cp.async ahead of the converters.
+template <int F>
+struct RawCfg {
+    static constexpr int BK = kRowBytes / FT<F>::ELEM;
+    static constexpr int BYTES = kBM * BK * 4;                 // one K-block of FP32 rows
+    static constexpr int UNITS = BYTES / 16 / (32 * kConv);    // 16-byte units per converter thread
+    static constexpr int STAGES = 4;
+};
+
+struct TcLaunch {
+    const TcJob *jobs;      // device table (when njobs > kMaxInline)
+    TcJob inl[kMaxInline];  // small tables travel with the launch
+    int njobs, total_tiles;
+    int *done;              // finished tiles per job (zeroed before the launch)
+    int stages, nacc, nbuf, acc_cols, bn_max;
+};
+
+__device__ __forceinline__ const TcJob &job_at(const TcLaunch &L, int j) {
+    return (L.njobs <= kMaxInline) ? L.inl[j] : L.jobs[j];
+}
+
+__device__ __forceinline__ int find_job(const TcLaunch &L, int t) {
+    int lo = 0, hi = L.njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (job_at(L, mid).tile_begin <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void named_bar(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// Item i of converter thread ct: (row, 16-byte chunk) of the 128-row tile.
+__device__ __forceinline__ void item_rc(int i, int ct, bool kc, int &row, int &ch) {
+    const int it = ct + i * 32 * kConv;
+    if (kc) {
+        ch = it % kChunks;
+        row = it / kChunks;
+    } else {
+        row = it % kBM;
+        ch = it / kBM;
+    }
+}
+
+template <int F, typename Tin>
+__device__ __forceinline__ void conv_load(const TcJob &J, const int64_t (&ro)[kItems], int64_t kbase, int ct,
+                                          Tin (&v)[kItems][16 / FT<F>::ELEM]) {
+    constexpr int CH = 16 / FT<F>::ELEM;
+    const Tin *src = static_cast<const Tin *>(J.A);
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        int row, ch;
+        item_rc(i, ct, J.akc != 0, row, ch);
+        load_chunk<F, Tin, true>(src, ro[i], J.kA, kbase + ch * CH, J.K, J.avec != 0, v[i]);
+    }
+}
+
+template <int F, typename Tin>
+__device__ __forceinline__ void conv_store(const TcJob &J, const Tin (&v)[kItems][16 / FT<F>::ELEM], uint8_t *dst,
+                                           int ct) {
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        int row, ch;
+        item_rc(i, ct, J.akc != 0, row, ch);
+        uint4 out[FT<F>::PIECES];
+        split_pack<F, Tin>(v[i], out);
+        const uint32_t off = swz(row, ch);
+#pragma unroll
+        for (int q = 0; q < FT<F>::PIECES; ++q)
+            *reinterpret_cast<uint4 *>(dst + q * (kBM * kRowBytes) + off) = out[q];
+    }
+}
+
+// Converter warps: one tile's K-blocks; the loads of K-block kb+1 are issued
+// right after K-block kb has been handed over.
+template <int F, typename Tin>
+__device__ __forceinline__ bool conv_tile_loop(const TcJob &J, int mt, uint8_t *sA, uint32_t A_ST, uint64_t *full,
+                                               uint64_t *empty, int S, uint32_t &g, int lane, int ct) {
+    constexpr int BK = kRowBytes / FT<F>::ELEM;
+    int64_t ro[kItems];
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        int row, ch;
+        item_rc(i, ct, J.akc != 0, row, ch);
+        const int64_t rg = (int64_t)mt * kBM + row;
+        ro[i] = rg < J.M ? imap(J.rowA, rg) : -1;
+    }
+    Tin v[kItems][16 / FT<F>::ELEM];
+    conv_load<F, Tin>(J, ro, (int64_t)J.kb0 * BK, ct, v);
+    for (int kb = 0; kb < J.nkb; ++kb, ++g) {
+        const int s = (int)(g % (uint32_t)S);
+        const uint32_t ph = (g / (uint32_t)S) & 1u;
+        int ok = (lane == 0) ? (int)mbar_wait(smem_u32(&empty[s]), ph ^ 1u) : 1;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) return false;
+        conv_store<F, Tin>(J, v, sA + (size_t)s * A_ST, ct);
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&full[s]));
+        if (kb + 1 < J.nkb) conv_load<F, Tin>(J, ro, (int64_t)(J.kb0 + kb + 1) * BK, ct, v);
+    }
+    return true;
+}
+
+// Unit u of converter thread ct (16 bytes of the raw FP32 tile): KC tiles are
+// stored [row][k], the others [k][row].
+template <int F>
+__device__ __forceinline__ void raw_unit(int i, int ct, bool kc, int &row, int &k, uint32_t &dst_off) {
+    using R = RawCfg<F>;
+    const int u = ct + i * 32 * kConv;
+    if (kc) {
+        const int per_row = R::BK / 4;
+        row = u / per_row;
+        k = (u % per_row) * 4;
+        dst_off = (uint32_t)(row * R::BK + k) * 4u;
+    } else {
+        k = u / (kBM / 4);
+        row = (u % (kBM / 4)) * 4;
+        dst_off = (uint32_t)(k * kBM + row) * 4u;
+    }
+}
+
+// Issues the cp.async copies of one K-block of the raw FP32 A tile.
+template <int F>
+__device__ __forceinline__ void raw_issue(const TcJob &J, const int64_t (&base)[RawCfg<F>::UNITS],
+                                          const int (&nrow)[RawCfg<F>::UNITS], int64_t row0, int64_t kbase,
+                                          uint32_t raw_s, int ct) {
+    using R = RawCfg<F>;
+    const float *src = static_cast<const float *>(J.A);
+    const bool kc = J.akc != 0;
+#pragma unroll
+    for (int i = 0; i < R::UNITS; ++i) {
+        int row, k;
+        uint32_t off;
+        raw_unit<F>(i, ct, kc, row, k, off);
+        const int64_t kg = kbase + k;
+        const uint32_t dst = raw_s + off;
+        if (kc) {
+            // 4 consecutive k of one row
+            const int nk = (int)max((int64_t)0, min((int64_t)4, J.K - kg));
+            if (J.cp16) {
+                const float *p = src + (base[i] >= 0 ? base[i] + kg : 0);
+                cp_async16(dst, p, (base[i] >= 0) ? (uint32_t)(nk * 4) : 0u);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const bool ok = base[i] >= 0 && e < nk;
+                    cp_async4(dst + 4 * e, src + (ok ? base[i] + imap(J.kA, kg + e) : 0), ok ? 4u : 0u);
+                }
+            }
+        } else {
+            // 4 consecutive rows at one k
+            const bool kok = kg < J.K;
+            const int nr = kok ? nrow[i] : 0;
+            if (J.cp16) {
+                const float *p = src + (nr > 0 ? base[i] + imap(J.kA, kg) : 0);
+                cp_async16(dst, p, (uint32_t)(nr * 4));
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int64_t rg = row0 + row + e;
+                    const bool ok = kok && rg < J.M;
+                    const int64_t o = ok ? imap(J.rowA, rg) + imap(J.kA, kg) : 0;
+                    cp_async4(dst + 4 * e, src + o, ok ? 4u : 0u);
+                }
+            }
+        }
+    }
+}
+
+// Float sources: raw tiles arrive through cp.async several K-blocks ahead;
+// the converters split them from shared memory.
+template <int F>
+__device__ __forceinline__ bool conv_tile_loop_raw(const TcJob &J, int mt, uint8_t *sA, uint32_t A_ST, uint8_t *sRaw,
+                                                   uint64_t *full, uint64_t *empty, int S, uint32_t &g, int lane,
+                                                   int ct) {
+    using R = RawCfg<F>;
+    constexpr int BK = R::BK;
+    constexpr int CH = 16 / FT<F>::ELEM;
+    const bool kc = J.akc != 0;
+    // per-unit source offsets (rows fixed over the tile)
+    const int64_t row0 = (int64_t)mt * kBM;
+    int64_t base[R::UNITS];
+    int nrow[R::UNITS];
+#pragma unroll
+    for (int i = 0; i < R::UNITS; ++i) {
+        int row, k;
+        uint32_t off;
+        raw_unit<F>(i, ct, kc, row, k, off);
+        const int64_t rg = (int64_t)mt * kBM + row;
+        base[i] = rg < J.M ? imap(J.rowA, rg) : -1;
+        nrow[i] = (int)max((int64_t)0, min((int64_t)4, J.M - rg));
+    }
+    named_bar(2, 32 * kConv);  // the raw ring is free (previous tile consumed)
+    const uint32_t raw0 = smem_u32(sRaw);
+#pragma unroll
+    for (int j = 0; j < R::STAGES - 1; ++j) {
+        if (j < J.nkb) raw_issue<F>(J, base, nrow, row0, (int64_t)(J.kb0 + j) * BK, raw0 + j * R::BYTES, ct);
+        cp_async_commit();
+    }
+    // conversion items of this thread
+    int irow[kItems], ich[kItems];
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) item_rc(i, ct, kc, irow[i], ich[i]);
+    for (int kb = 0; kb < J.nkb; ++kb, ++g) {
+        cp_async_wait<R::STAGES - 2>();
+        named_bar(2, 32 * kConv);
+        const int rs = kb % R::STAGES;
+        {
+            const int kn = kb + R::STAGES - 1;
+            if (kn < J.nkb)
+                raw_issue<F>(J, base, nrow, row0, (int64_t)(J.kb0 + kn) * BK, raw0 + (kn % R::STAGES) * R::BYTES, ct);
+            cp_async_commit();
+        }
+        const int s = (int)(g % (uint32_t)S);
+        const uint32_t ph = (g / (uint32_t)S) & 1u;
+        int ok = (lane == 0) ? (int)mbar_wait(smem_u32(&empty[s]), ph ^ 1u) : 1;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+            cp_async_wait<0>();
+            return false;
+        }
+        const float *raw = reinterpret_cast<const float *>(sRaw + rs * R::BYTES);
+        uint8_t *dst = sA + (size_t)s * A_ST;
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            float v[CH];
+            if (kc) {
+                const float *q = raw + irow[i] * BK + ich[i] * CH;
+#pragma unroll
+                for (int e = 0; e < CH; e += 4) *reinterpret_cast<float4 *>(&v[e]) = *reinterpret_cast<const float4 *>(q + e);
+            } else {
+#pragma unroll
+                for (int e = 0; e < CH; ++e) v[e] = raw[(ich[i] * CH + e) * kBM + irow[i]];
+            }
+            uint4 out[FT<F>::PIECES];
+            split_pack<F, float>(v, out);
+            const uint32_t off = swz(irow[i], ich[i]);
+#pragma unroll
+            for (int q = 0; q < FT<F>::PIECES; ++q)
+                *reinterpret_cast<uint4 *>(dst + q * (kBM * kRowBytes) + off) = out[q];
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&full[s]));
+    }
+    cp_async_wait<0>();
+    return true;
+}
+
+template <int F>
+__global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const TcLaunch L) {
+    using T = FT<F>;
+    constexpr int BK = kRowBytes / T::ELEM;
+    constexpr uint32_t PIECE_A = kBM * kRowBytes;
+    constexpr uint32_t A_ST = T::PIECES * PIECE_A;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int S = L.stages, NACC = L.nacc, NBUF = L.nbuf;
+    const uint32_t ACOLS = (uint32_t)L.acc_cols;
+    const uint32_t B_ST = (uint32_t)T::PIECES * (uint32_t)L.bn_max * kRowBytes;
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + (size_t)S * A_ST;
+    uint8_t *sRaw = sB + (size_t)S * B_ST;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sRaw + (size_t)RawCfg<F>::STAGES * RawCfg<F>::BYTES);
+    uint64_t *full = bars, *empty = bars + S, *accf = bars + 2 * S, *acce = bars + 2 * S + NBUF;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * S + 2 * NBUF);
+    const uint32_t ncols = ACOLS * 2u * (uint32_t)NACC * (uint32_t)NBUF;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(smem_u32(&full[s]), kConv + 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int b = 0; b < NBUF; ++b) {
+            mbar_init(smem_u32(&accf[b]), 1);
+            mbar_init(smem_u32(&acce[b]), kEpi);
+        }
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(tslot), ncols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0) {
+        // ---------------------------------------------- op(L) image producer
+        if (lane == 0) {
+            uint32_t g = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < L.total_tiles && ok; t += gridDim.x) {
+                const TcJob J = job_at(L, find_job(L, t));
+                const int lt = t - J.tile_begin;
+                const int nt = lt % J.tiles_n;
+                const uint32_t bytes = (uint32_t)T::PIECES * (uint32_t)J.BN * kRowBytes;
+                const uint8_t *img = J.bimg + ((size_t)nt * J.kb_img + J.kb0) * bytes;
+                for (int kb = 0; kb < J.nkb; ++kb, ++g) {
+                    const int s = (int)(g % (uint32_t)S);
+                    const uint32_t ph = (g / (uint32_t)S) & 1u;
+                    if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(smem_u32(&full[s]), bytes);
+                    bulk_g2s(smem_u32(sB + (size_t)s * B_ST), img + (size_t)kb * bytes, bytes, smem_u32(&full[s]));
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // -------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            uint32_t g = 0;
+            int it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < L.total_tiles && ok; t += gridDim.x, ++it) {
+                const TcJob J = job_at(L, find_job(L, t));
+                const int buf = it % NBUF;
+                const uint32_t use = (uint32_t)(it / NBUF);
+                if (!mbar_wait(smem_u32(&acce[buf]), (use & 1u) ^ 1u)) break;
+                tc_fence_after();
+                const uint32_t idesc = make_idesc(T::FMT, kBM, (uint32_t)J.BN);
+                const uint32_t PIECE_B = (uint32_t)J.BN * kRowBytes;
+                const uint32_t dbase = tmem + (uint32_t)(buf * NACC) * 2u * ACOLS;
+                for (int kb = 0; kb < J.nkb; ++kb, ++g) {
+                    const int s = (int)(g % (uint32_t)S);
+                    const uint32_t ph = (g / (uint32_t)S) & 1u;
+                    if (!mbar_wait(smem_u32(&full[s]), ph)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const int64_t kval = min((int64_t)BK, J.K - (int64_t)(J.kb0 + kb) * BK);
+                    const int ksteps = (int)((kval + T::MMA_K - 1) / T::MMA_K);
+                    const uint32_t a_base = smem_u32(sA + (size_t)s * A_ST);
+                    const uint32_t b_base = smem_u32(sB + (size_t)s * B_ST);
+                    const uint32_t dhi = dbase + (uint32_t)(kb % NACC) * 2u * ACOLS;
+                    const uint32_t dlo = dhi + ACOLS;
+                    const bool fresh = kb < NACC;
+                    for (int ks = 0; ks < ksteps; ++ks) {
+#pragma unroll
+                        for (int pr = 0; pr < T::NPROD; ++pr) {
+                            int pa, pb;
+                            prod_pieces<F>(pr, pa, pb);
+                            const uint64_t ad = smem_desc_kmajor(a_base + pa * PIECE_A + ks * 32, kRowBytes);
+                            const uint64_t bd = smem_desc_kmajor(b_base + pb * PIECE_B + ks * 32, kRowBytes);
+                            const bool is_hi = (pr == T::NPROD - 1);
+                            const bool first = fresh && ks == 0 && (is_hi || pr == 0);
+                            tc_mma<T::KIND>(is_hi ? dhi : dlo, ad, bd, idesc, first ? 0u : 1u);
+                        }
+                    }
+                    tc_commit(smem_u32(&empty[s]));
+                }
+                if (!ok) break;
+                tc_commit(smem_u32(&accf[buf]));
+            }
+        }
+        __syncwarp();
+    } else if (warp < kConv0) {
+        // ---------------------------------------------------------- epilogue
+        const int q = warp & 3;                // TMEM lane quarter this warp may access
+        int it = 0;
+        for (int t = blockIdx.x; t < L.total_tiles; t += gridDim.x, ++it) {
+            const int j = find_job(L, t);
+            const TcJob J = job_at(L, j);
+            const int lt = t - J.tile_begin;
+            const int nt = lt % J.tiles_n, mt = lt / J.tiles_n;
+            const int buf = it % NBUF;
+            const uint32_t use = (uint32_t)(it / NBUF);
+            int ok = (lane == 0) ? (int)mbar_wait(smem_u32(&accf[buf]), use & 1u) : 1;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            tc_fence_after();
+            const int64_t rg = (int64_t)mt * kBM + q * 32 + lane;
+            const int64_t ro = rg < J.M ? imap(J.rowC, rg) : -1;
+            const int64_t n0 = (int64_t)nt * J.BN;
+            const int used = min(NACC, J.nkb);
+            const uint32_t lane_base =
+                tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * NACC) * 2u * ACOLS;
+            for (int c0 = 0; c0 < J.BN; c0 += 32) {
+                // accumulator 0: hi + cross in FP32; further accumulators are
+                // added in order
+                uint32_t h[32], l[32];
+                tmem_ld32(lane_base + (uint32_t)c0, h);
+                tmem_ld32(lane_base + ACOLS + (uint32_t)c0, l);
+                tmem_ld_wait();
+#pragma unroll
+                for (int e = 0; e < 32; ++e) h[e] = __float_as_uint(__uint_as_float(l[e]) + __uint_as_float(h[e]));
+                for (int a = 1; a < used; ++a) {
+                    uint32_t x[32];
+                    tmem_ld32(lane_base + (uint32_t)(2 * a) * ACOLS + (uint32_t)c0, l);
+                    tmem_ld32(lane_base + (uint32_t)(2 * a + 1) * ACOLS + (uint32_t)c0, x);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int e = 0; e < 32; ++e)
+                        h[e] = __float_as_uint(__uint_as_float(h[e]) + (__uint_as_float(x[e]) + __uint_as_float(l[e])));
+                }
+                if (ro >= 0) {
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        // columns of this tile only: the 32-column block may run past BN
+                        const int64_t lim = min(J.N - n0, (int64_t)J.BN);
+                        const int cmax = (int)max((int64_t)0, min((int64_t)16, lim - c0 - 16 * hh));
+                        float s16[16];
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) s16[e] = __uint_as_float(h[16 * hh + e]);
+                        if (J.c64) store_row16<double>(J.C, ro, J.colC, n0 + c0 + 16 * hh, cmax, s16, J.acc != 0);
+                        else store_row16<float>(J.C, ro, J.colC, n0 + c0 + 16 * hh, cmax, s16, J.acc != 0);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&acce[buf]));
+            // publish the finished tile for jobs that wait on this one
+            if (J.publish) {
+                named_bar(1, 32 * kEpi);
+                if (warp == 2 && lane == 0) {
+                    __threadfence();
+                    atomicAdd(&L.done[j], 1);
+                }
+            }
+        }
+    } else {
+        // -------------------------------------------------------- converters
+        const int ct = threadIdx.x - kConv0 * 32;
+        uint32_t g = 0;
+        for (int t = blockIdx.x; t < L.total_tiles; t += gridDim.x) {
+            const TcJob J = job_at(L, find_job(L, t));
+            const int lt = t - J.tile_begin;
+            const int mt = lt / J.tiles_n;
+            if (J.dep >= 0) {
+                // wait until every tile of the job this one reads is stored
+                if (ct == 0) {
+                    volatile int *dn = L.done + J.dep;
+                    const unsigned long long t0 = globaltimer_ns();
+                    while (*dn < J.dep_tiles) {
+                        const unsigned long long dt = globaltimer_ns() - t0;
+                        if ((dt > 1000000ull && device_error_set()) || dt > kWaitLimitNs) {
+                            latch_error(kErrTimeout);
+                            break;
+                        }
+                    }
+                    __threadfence();
+                }
+                named_bar(2, 32 * kConv);
+            }
+            bool ok = J.a64 ? conv_tile_loop<F, double>(J, mt, sA, A_ST, full, empty, S, g, lane, ct)
+                            : conv_tile_loop_raw<F>(J, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct);
+            if (!ok) break;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, ncols);
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+
+static int pieces_of_f(int form) { return form == kBF16x6 ? 3 : 2; }
+static int bk_of_f(int form) { return form == kTF32x3 ? kRowBytes / 4 : kRowBytes / 2; }
+
+size_t tcp_job_bytes() { return sizeof(TcJob); }
+
+// Fills a job for contraction c (B side from `img`, built with tcp_tile_n).
+static TcJob make_job(int form, const Contraction &c, const void *img) {
+    TcJob J{};
+    J.A = c.A;
+    J.rowA = c.rowA;
+    J.kA = c.kA;
+    J.M = c.M;
+    J.bimg = static_cast<const uint8_t *>(img);
+    J.C = c.C;
+    J.rowC = c.rowC;
+    J.colC = c.colC;
+    J.N = c.N;
+    J.K = c.K;
+    const int bk = bk_of_f(form);
+    J.kb_img = (c.K + bk - 1) / bk;
+    J.kb0 = 0;
+    J.nkb = (int32_t)J.kb_img;
+    J.BN = tc_tile_n(form, c.N);
+    J.tiles_m = (int32_t)((c.M + kBM - 1) / kBM);
+    J.tiles_n = (int32_t)((c.N + J.BN - 1) / J.BN);
+    J.dep = -1;
+    J.dep_tiles = 0;
+    J.a64 = c.A_f64;
+    J.c64 = c.C_f64;
+    J.acc = c.accumulate;
+    J.akc = (c.kA.s0 == 1 && c.kA.R0 != 1) ? 1 : 0;
+    const int64_t v = c.A_f64 ? 2 : 4;
+    const bool unit_k = c.kA.R0 == 0 && c.kA.s0 == 1;
+    const bool rows_ok = (c.rowA.s0 % v == 0) && (c.rowA.R0 == 0 || c.rowA.s1 % v == 0);
+    const bool base_ok = (reinterpret_cast<uintptr_t>(c.A) % 16) == 0;
+    J.avec = (unit_k && rows_ok && base_ok) ? 1 : 0;
+    // 16-byte cp.async of FP32 sources: k-contiguous rows need m % 4 == 0;
+    // fibre-contiguous tiles need groups of 4 rows contiguous and aligned
+    if (!c.A_f64 && base_ok) {
+        if (J.akc)
+            J.cp16 = (unit_k && c.rowA.s0 % 4 == 0 && (c.rowA.R0 == 0 || c.rowA.s1 % 4 == 0)) ? 1 : 0;
+        else
+            J.cp16 = (c.rowA.s0 == 1 && (c.rowA.R0 == 0 || (c.rowA.R0 % 4 == 0 && c.rowA.s1 % 4 == 0)) &&
+                      c.kA.R0 == 0 && c.kA.s0 % 4 == 0) ? 1 : 0;
+    }
+    return J;
+}
+
+static constexpr size_t kSmemMax = 227 * 1024;
+
+static void pick_config(int form, int bn_max, int nkb_max, int &stages, int &nacc, int &nbuf, int &acc_cols,
+                        size_t &smem) {
+    acc_cols = bn_max <= 32 ? 32 : (bn_max <= 64 ? 64 : 128);
+    // two accumulator buffers (epilogue overlapped) when the K loop is short,
+    // more accumulators per tile (accuracy) when it is long
+    const int budget = 512 / (2 * acc_cols);  // NACC * NBUF
+    nbuf = std::min(2, budget);
+    nacc = std::max(1, std::min(4, budget / nbuf));
+    if (nkb_max < 2) nacc = 1;
+    const size_t a_st = (size_t)pieces_of_f(form) * kBM * kRowBytes;
+    const size_t b_st = (size_t)pieces_of_f(form) * bn_max * kRowBytes;
+    const size_t extra = 1024 + (size_t)(2 * 8 + 2 * 4 + 2) * 8;
+    size_t raw = 0;
+    switch (form) {
+        case kTF32x3: raw = (size_t)RawCfg<kTF32x3>::STAGES * RawCfg<kTF32x3>::BYTES; break;
+        case kBF16x3: raw = (size_t)RawCfg<kBF16x3>::STAGES * RawCfg<kBF16x3>::BYTES; break;
+        default: raw = (size_t)RawCfg<kBF16x6>::STAGES * RawCfg<kBF16x6>::BYTES; break;
+    }
+    stages = 1;
+    while (stages < 8 && (size_t)(stages + 1) * (a_st + b_st) + raw + extra <= kSmemMax) ++stages;
+    smem = (size_t)stages * (a_st + b_st) + raw + extra;
+}
+
+template <int F>
+static cudaError_t launch_f(const TcLaunch &L, int grid, size_t smem, cudaStream_t st) {
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [&] {
+        attr = cudaFuncSetAttribute(tcp_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+    });
+    if (attr != cudaSuccess) return attr;
+    tcp_kernel<F><<<grid, kPThreads, smem, st>>>(L);
+    return cudaGetLastError();
+}
+
+static int num_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+// Runs the jobs (tile_begin / dep fields filled by the caller).  `table` is a
+// device copy of the jobs when there are more than kMaxInline of them;
+// `done` holds one int per job, zeroed here.
+static cudaError_t tcp_launch(int form, const TcJob *jobs, int njobs, int total_tiles, int bn_max, int nkb_max,
+                              const void *table, int *done, cudaStream_t st) {
+    if (total_tiles <= 0) return cudaSuccess;
+    TcLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    L.njobs = njobs;
+    L.total_tiles = total_tiles;
+    L.done = done;
+    if (njobs <= kMaxInline)
+        for (int j = 0; j < njobs; ++j) L.inl[j] = jobs[j];
+    else
+        L.jobs = static_cast<const TcJob *>(table);
+    size_t smem;
+    pick_config(form, bn_max, nkb_max, L.stages, L.nacc, L.nbuf, L.acc_cols, smem);
+    L.bn_max = bn_max;
+    if (done != nullptr) {
+        cudaError_t e = cudaMemsetAsync(done, 0, sizeof(int) * (size_t)njobs, st);
+        if (e != cudaSuccess) return e;
+    }
+    const int grid = std::min(total_tiles, num_sms());
+    switch (form) {
+        case kTF32x3: return launch_f<kTF32x3>(L, grid, smem, st);
+        case kBF16x3: return launch_f<kBF16x3>(L, grid, smem, st);
+        case kBF16x6: return launch_f<kBF16x6>(L, grid, smem, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// One contraction with the B side from an image built by tc_build_bimage.
+cudaError_t tcp_contract(int form, const Contraction &c, const void *img, cudaStream_t st) {
+    if (c.M == 0 || c.N == 0) return cudaSuccess;
+    TcJob J = make_job(form, c, img);
+    J.tile_begin = 0;
+    const int tiles = J.tiles_m * J.tiles_n;
+    return tcp_launch(form, &J, 1, tiles, J.BN, J.nkb, nullptr, nullptr, st);
+}
+
+// ---------------------------------------------------------- job tables
+
+void tcp_jobs_begin(TcpJobs &jobs, int form) {
+    jobs.form = form;
+    jobs.host.clear();
+    jobs.total_tiles = 0;
+    jobs.bn_max = 16;
+    jobs.nkb_max = 1;
+}
+
+int tcp_jobs_add(TcpJobs &jobs, const Contraction &c, const void *img, int dep) {
+    TcJob J = make_job(jobs.form, c, img);
+    J.tile_begin = jobs.total_tiles;
+    J.dep = dep;
+    if (dep >= 0) {
+        TcJob *D = reinterpret_cast<TcJob *>(jobs.host.data()) + dep;
+        J.dep_tiles = D->tiles_m * D->tiles_n;
+        D->publish = 1;
+    }
+    jobs.total_tiles += J.tiles_m * J.tiles_n;
+    jobs.bn_max = std::max(jobs.bn_max, (int)J.BN);
+    jobs.nkb_max = std::max(jobs.nkb_max, (int)J.nkb);
+    const size_t off = jobs.host.size();
+    jobs.host.resize(off + sizeof(TcJob));
+    std::memcpy(jobs.host.data() + off, &J, sizeof(TcJob));
+    return (int)(off / sizeof(TcJob));
+}
+
+size_t tcp_jobs_table_bytes(const TcpJobs &jobs) { return jobs.host.size(); }
+
+cudaError_t tcp_jobs_run(const TcpJobs &jobs, const void *table, int *done, cudaStream_t st) {
+    const int njobs = (int)(jobs.host.size() / sizeof(TcJob));
+    return tcp_launch(jobs.form, reinterpret_cast<const TcJob *>(jobs.host.data()), njobs, jobs.total_tiles,
+                      jobs.bn_max, jobs.nkb_max, table, done, st);
+}
+
+}  // namespace kron

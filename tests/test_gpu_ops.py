@@ -30,6 +30,8 @@ MUMP_CASES = [
     ((7,), 0, 5), ((37, 3), 0, 19), ((3, 37), 1, 40), ((130, 5, 3), 0, 7),
     ((9, 33, 17), 1, 33), ((5, 6, 300), 2, 12), ((129, 2, 2), 1, 257), ((20, 20, 20, 3), 2, 20),
     ((1, 1, 5), 2, 1), ((64, 64), 1, 64), ((17, 70), 0, 33),
+    # several N-tiles whose width is not a power of two
+    ((14, 54, 8), 0, 81), ((14, 54, 8), 1, 65), ((30, 33, 20), 2, 129), ((9, 40, 7), 1, 200),
 ]
 
 
