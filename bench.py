@@ -324,6 +324,8 @@ def time_mode_product(kron, torch, dev, prec, args):
     X.normal_()
     E = torch.randn(N, N, dtype=torch.float32, device=dev)
     Y = kron.empty_colmajor([N] * D, torch.float32, dev)
+    if prec == "fx32":
+        return {"ms": time_fx_mode_product(kron, torch, dev, X, E, Y, mu), "mu": mu}
     # the 1 GiB flush keeps the GPU busy while the host enqueues the events
     # and the launch, so no host latency lands between the two events
     flush = torch.empty(1024 * 1024 * 1024, dtype=torch.uint8, device=dev)
@@ -340,6 +342,33 @@ def time_mode_product(kron, torch, dev, prec, args):
         torch.cuda.synchronize()
         ts.append(s.elapsed_time(e))
     return {"ms": statistics.median(ts), "mu": mu}
+
+
+def time_fx_mode_product(kron, torch, dev, X, E, Y, mu):
+    """The fixed-point form's mode product on a 256^3 fixed-point state, as
+    the stepper runs it (state and output 32-bit fixed point)."""
+    plan = kron.StepperPlan([N] * D, torch.float32, "fx32")
+    ws = plan.workspace(dev)
+    U = kron.empty_colmajor([N] * D, torch.float32, dev)
+    U.copy_(X)
+    Es = [E.double()] * D
+    flush = torch.empty(1024 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    # one stepper call = conversion + images + nsteps * D products; difference
+    # of two call lengths isolates the per-product time
+    def run(nsteps):
+        ts = []
+        for _ in range(5):
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            plan.apply(U, Es, nsteps, ws=ws)
+            e.record()
+            torch.cuda.synchronize()
+            ts.append(s.elapsed_time(e))
+        return statistics.median(ts)
+    run(1)
+    t1, t5 = run(1), run(5)
+    return (t5 - t1) / (4 * D)
 
 
 def run_kernel_only(args):

@@ -75,6 +75,19 @@ typedef enum kron_dtype { KRON_F64 = 0, KRON_F32 = 1 } kron_dtype;
  *                     bf16 pieces per operand, three products, FP32 accumulate.
  *  KRON_PREC_BF16X6 : three bf16 pieces per operand, the six products with
  *                     piece-index sum <= 2, FP32 accumulate.
+ *  KRON_PREC_FX32   : error-free slicing in the manner of Ozaki et al. (Numer.
+ *                     Algorithms 59, 2012): the tensor is held as 32-bit fixed
+ *                     point with one power-of-two scale per tensor, every row
+ *                     of L as 32-bit fixed point with its own scale; both are
+ *                     cut into four balanced base-256 digits stored exactly as
+ *                     bf16 (so the products left out average to zero), and
+ *                     the ten slice products down to 2^-24 are accumulated in
+ *                     three tensor-memory accumulators, the two leading ones
+ *                     exactly (integer-valued sums below 2^24), then combined
+ *                     in 64-bit integer arithmetic.  About 31 significant bits
+ *                     per stored value and per product, for contraction
+ *                     lengths up to 256; intermediates are 32-bit fixed point.
+ *                     Supported by kron_mump, kron_tucker and the stepper.
  * Split forms keep intermediates in FP32.  Inputs stored as double are split
  * from their double value.
  */
@@ -83,7 +96,8 @@ typedef enum kron_prec {
     KRON_PREC_FP32 = 1,
     KRON_PREC_3XTF32 = 2,
     KRON_PREC_BF16X3 = 3,
-    KRON_PREC_BF16X6 = 4
+    KRON_PREC_BF16X6 = 4,
+    KRON_PREC_FX32 = 5
 } kron_prec;
 
 /* Plan flags. */

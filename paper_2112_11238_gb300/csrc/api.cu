@@ -20,7 +20,7 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 kron_status cuda_status(cudaError_t e) { return e == cudaSuccess ? KRON_OK : KRON_ERR_CUDA; }
 
 bool valid_dtype(kron_dtype t) { return t == KRON_F64 || t == KRON_F32; }
-bool valid_prec(kron_prec p) { return p >= KRON_PREC_FP64 && p <= KRON_PREC_BF16X6; }
+bool valid_prec(kron_prec p) { return p >= KRON_PREC_FP64 && p <= KRON_PREC_FX32; }
 size_t esize(kron_dtype t) { return t == KRON_F64 ? 8 : 4; }
 
 // Element size of the intermediates of a precision.
@@ -136,6 +136,9 @@ struct kron_plan_s {
     // workspace layout of kron_tucker
     size_t img_off[KRON_MAX_D], img_bytes[KRON_MAX_D];
     size_t buf_off[2], buf_bytes;
+    // fixed-point form: row exponents and row-sum bounds of every image, the
+    // fixed-point copy of T, three scale words and a scratch word
+    size_t fxf_off[KRON_MAX_D], fxg_off[KRON_MAX_D], fxin_off, fxsc_off;
     size_t ws_bytes;
 };
 
@@ -144,8 +147,42 @@ namespace {
 // Applies the chain of the plan in its order.  src (dtype of the plan) ->
 // dst (dtype); intermediates in ws buffers.  Images of the split L live in
 // ws at the plan's offsets.
+kron_status run_chain_fx(const kron_plan_s *pl, const void *T, const void *const *L, const int64_t *ldL,
+                         void *S, uint8_t *ws, cudaStream_t st, bool trans) {
+    const int d = pl->d;
+    const bool io64 = pl->dtype == KRON_F64;
+    FxScale *sc = reinterpret_cast<FxScale *>(ws + pl->fxsc_off);  // [0] input, [1], [2] buffers
+    auto *scratch = reinterpret_cast<unsigned long long *>(sc + 3);
+    auto *xin = reinterpret_cast<int32_t *>(ws + pl->fxin_off);
+    if (fx_from_float(T, io64, prod(pl->m, 0, d), xin, &sc[0], scratch, st) != cudaSuccess) return KRON_ERR_CUDA;
+    int64_t cur[KRON_MAX_D];
+    for (int k = 0; k < d; ++k) cur[k] = pl->m[k];
+    const void *src = xin;
+    const FxScale *ssrc = &sc[0];
+    for (int s = 0; s < d; ++s) {
+        const int mu = pl->order[s];
+        const ModeGeom g = mode_geom(d, cur, mu, pl->n[mu]);
+        const bool last = (s == d - 1);
+        void *dst = last ? S : (void *)(ws + pl->buf_off[s & 1]);
+        FxScale *sdst = last ? nullptr : &sc[1 + (s & 1)];
+        Contraction c = tc_mode_contraction(g, src, false, L[mu], io64, ldL[mu], trans, dst, last ? io64 : false);
+        void *img = ws + pl->img_off[mu];
+        int *f = reinterpret_cast<int *>(ws + pl->fxf_off[mu]);
+        auto *gb = reinterpret_cast<unsigned long long *>(ws + pl->fxg_off[mu]);
+        cudaError_t e = fx_build_bimage(c, img, f, gb, st);
+        if (e == cudaSuccess && sdst) e = fx_reset(sdst, st);
+        if (e == cudaSuccess) e = tcp_contract_fx(c, img, ssrc, f, gb, sdst, st);
+        if (e != cudaSuccess) return KRON_ERR_CUDA;
+        cur[mu] = pl->n[mu];
+        src = dst;
+        ssrc = sdst;
+    }
+    return KRON_OK;
+}
+
 kron_status run_chain(const kron_plan_s *pl, const void *T, const void *const *L, const int64_t *ldL,
                       void *S, uint8_t *ws, cudaStream_t st, bool trans) {
+    if (is_fx(pl->prec)) return run_chain_fx(pl, T, L, ldL, S, ws, st, trans);
     const int d = pl->d;
     const bool io64 = pl->dtype == KRON_F64;
     const bool split = is_split(pl->prec);
@@ -201,6 +238,18 @@ void plan_layout(kron_plan_s *pl) {
     pl->buf_off[0] = off;
     pl->buf_off[1] = off + pl->buf_bytes;
     off += 2 * pl->buf_bytes;
+    if (is_fx(pl->prec)) {
+        for (int k = 0; k < d; ++k) {
+            pl->fxf_off[k] = off;
+            off += align_up((size_t)pl->n[k] * sizeof(int));
+            pl->fxg_off[k] = off;
+            off += kAlign;
+        }
+        pl->fxin_off = off;
+        off += align_up((size_t)prod(pl->m, 0, d) * sizeof(int32_t));
+        pl->fxsc_off = off;
+        off += kAlign;
+    }
     pl->ws_bytes = std::max<size_t>(off, kAlign);
 }
 
@@ -270,6 +319,8 @@ kron_status kron_mump_workspace_size(int d, const int64_t *m, int mu, int64_t n,
         if (m[k] < 1) return KRON_ERR_INVALID_ARG;
     const int form = form_of(prec);
     *bytes = align_up(form >= 0 ? tc_bimage_bytes(form, n, m[mu]) : 0);
+    if (is_fx(prec))  // + row exponents, row-sum bound, fixed-point T, scales
+        *bytes += align_up((size_t)n * sizeof(int)) + kAlign + align_up((size_t)prod(m, 0, d) * 4) + kAlign;
     if (*bytes == 0) *bytes = kAlign;
     return KRON_OK;
 }
@@ -284,7 +335,7 @@ kron_status kron_mump(int d, const int64_t *m, int mu, int64_t n, const void *T,
     if (transL ? ldL < m[mu] : ldL < n) return KRON_ERR_INVALID_ARG;
     const size_t es = esize(dtype);
     if (!aligned(T, es) || !aligned(L, es) || !aligned(S, es)) return KRON_ERR_ALIGNMENT;
-    if (is_split(prec)) {
+    if (is_split(prec) || is_fx(prec)) {
         if (!ws) return KRON_ERR_INVALID_ARG;
         if (!aligned(ws, kAlign)) return KRON_ERR_ALIGNMENT;
         if (ws_bytes < need) return KRON_ERR_WORKSPACE;
@@ -293,7 +344,22 @@ kron_status kron_mump(int d, const int64_t *m, int mu, int64_t n, const void *T,
     const bool io64 = dtype == KRON_F64;
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e;
-    if (is_split(prec)) {
+    if (is_fx(prec)) {
+        auto *w = static_cast<uint8_t *>(ws);
+        size_t off = align_up(tc_bimage_bytes(kFX32, n, m[mu]));
+        int *f = reinterpret_cast<int *>(w + off);
+        off += align_up((size_t)n * sizeof(int));
+        auto *gb = reinterpret_cast<unsigned long long *>(w + off);
+        off += kAlign;
+        auto *X = reinterpret_cast<int32_t *>(w + off);
+        off += align_up((size_t)prod(m, 0, d) * 4);
+        auto *sc = reinterpret_cast<FxScale *>(w + off);
+        auto *scratch = reinterpret_cast<unsigned long long *>(sc + 1);
+        Contraction c = tc_mode_contraction(g, X, false, L, io64, ldL, transL != 0, S, io64);
+        e = fx_from_float(T, io64, prod(m, 0, d), X, sc, scratch, cs);
+        if (e == cudaSuccess) e = fx_build_bimage(c, w, f, gb, cs);
+        if (e == cudaSuccess) e = tcp_contract_fx(c, w, sc, f, gb, nullptr, cs);
+    } else if (is_split(prec)) {
         const int form = form_of(prec);
         Contraction c = tc_mode_contraction(g, T, io64, L, io64, ldL, transL != 0, S, io64);
         e = tc_build_bimage(form, c, ws, cs);
@@ -472,6 +538,7 @@ kron_status kron_tucker_adjoint(kron_plan plan, const void *T, const void *const
                                 kron_stream_t stream) {
     if (!plan || !dS) return KRON_ERR_INVALID_ARG;
     if (plan->flags & KRON_PLAN_TRANS_L) return KRON_ERR_UNSUPPORTED;
+    if (is_fx(plan->prec)) return KRON_ERR_UNSUPPORTED;
     kron_status st = check_L(plan, L, ldL, false);
     if (st != KRON_OK) return st;
     const int d = plan->d;
@@ -582,6 +649,7 @@ kron_status kron_expm(int64_t n, const double *A, int64_t ldA, double tau, doubl
 namespace {
 struct StepLayout {
     size_t expm, E[KRON_MAX_D], img[KRON_MAX_D], st[2], stbytes, total;
+    size_t fxf[KRON_MAX_D], fxg[KRON_MAX_D], fxsc;  // fixed-point form
 };
 
 StepLayout step_layout(const kron_plan_s *pl) {
@@ -605,8 +673,60 @@ StepLayout step_layout(const kron_plan_s *pl) {
     off += s.stbytes;
     s.st[1] = off;
     off += s.stbytes;
+    if (is_fx(pl->prec)) {
+        for (int k = 0; k < pl->d; ++k) {
+            s.fxf[k] = off;
+            off += align_up((size_t)pl->n[k] * sizeof(int));
+            s.fxg[k] = off;
+            off += kAlign;
+        }
+        s.fxsc = off;
+        off += kAlign;
+    }
     s.total = off;
     return s;
+}
+
+// Fixed-point stepper: U (float) -> fixed point once, then every mode
+// product fixed point -> fixed point (state ping-pong), the last one back to
+// the storage type.
+kron_status run_steps_fx(const kron_plan_s *pl, const double *const *E, const int64_t *ldE, int nsteps, void *U,
+                         uint8_t *w, const StepLayout &lay, cudaStream_t cs) {
+    const int d = pl->d;
+    const bool io64 = pl->dtype == KRON_F64;
+    const int total = nsteps * d;
+    if (total == 0) return KRON_OK;
+    FxScale *sc = reinterpret_cast<FxScale *>(w + lay.fxsc);  // [0], [1]: state buffers
+    auto *scratch = reinterpret_cast<unsigned long long *>(sc + 2);
+    for (int k = 0; k < d; ++k) {
+        const ModeGeom g{1, 1, pl->n[k], pl->n[k]};
+        Contraction c = tc_mode_contraction(g, nullptr, false, E[k], true, ldE[k], false, nullptr, false);
+        if (fx_build_bimage(c, w + lay.img[k], reinterpret_cast<int *>(w + lay.fxf[k]),
+                            reinterpret_cast<unsigned long long *>(w + lay.fxg[k]), cs) != cudaSuccess)
+            return KRON_ERR_CUDA;
+    }
+    const int64_t N = prod(pl->n, 0, d);
+    if (fx_from_float(U, io64, N, reinterpret_cast<int32_t *>(w + lay.st[0]), &sc[0], scratch, cs) != cudaSuccess)
+        return KRON_ERR_CUDA;
+    int cur = 0, idx = 0;
+    for (int s = 0; s < nsteps; ++s) {
+        for (int j = 0; j < d; ++j, ++idx) {
+            const int mu = pl->order[j];
+            const ModeGeom g = mode_geom(d, pl->n, mu, pl->n[mu]);
+            const bool last = (idx == total - 1);
+            void *dst = last ? U : (void *)(w + lay.st[cur ^ 1]);
+            FxScale *sdst = last ? nullptr : &sc[cur ^ 1];
+            Contraction c = tc_mode_contraction(g, w + lay.st[cur], false, E[mu], true, ldE[mu], false, dst,
+                                                last ? io64 : false);
+            cudaError_t e = sdst ? fx_reset(sdst, cs) : cudaSuccess;
+            if (e == cudaSuccess)
+                e = tcp_contract_fx(c, w + lay.img[mu], &sc[cur], reinterpret_cast<const int *>(w + lay.fxf[mu]),
+                                    reinterpret_cast<const unsigned long long *>(w + lay.fxg[mu]), sdst, cs);
+            if (e != cudaSuccess) return KRON_ERR_CUDA;
+            cur ^= 1;
+        }
+    }
+    return KRON_OK;
 }
 
 kron_status check_step_plan(const kron_plan_s *pl) {
@@ -618,6 +738,7 @@ kron_status check_step_plan(const kron_plan_s *pl) {
 
 kron_status run_steps(const kron_plan_s *pl, const double *const *E, const int64_t *ldE, int nsteps, void *U,
                       uint8_t *w, const StepLayout &lay, cudaStream_t cs) {
+    if (is_fx(pl->prec)) return run_steps_fx(pl, E, ldE, nsteps, U, w, lay, cs);
     const int d = pl->d;
     const bool io64 = pl->dtype == KRON_F64;
     const bool split = is_split(pl->prec);

@@ -1,0 +1,163 @@
+// fx.cu -- helpers of the 32-bit fixed-point form (KRON_PREC_FX32): the
+// sliced image of op(L) with one power-of-two scale per row, and the
+// conversion of a floating-point tensor into fixed point with one scale.
+//
+// Fixed point: a tensor X with scale e holds the values X * 2^(e - 31),
+// |X| <= 2^31 - 1, so |value| < 2^e.  A row c of op(L) is held as
+// Y = round(L[c, :] * 2^(31 - f_c)) with 2^(f_c - 1) <= max_k |L[c, k]| < 2^f_c.
+// Both are cut into four 8-bit slices (fx_pack, tc_common.cuh).
+#include <algorithm>
+
+#include "tc_common.cuh"
+
+namespace kron {
+
+namespace {
+
+// Exponent f with |x| < 2^f for the largest |x| of a set (0 for an all-zero set).
+__device__ __forceinline__ int exp_bound(double mx) {
+    int f = 0;
+    if (mx > 0.0) frexp(mx, &f);
+    return f;
+}
+
+__device__ __forceinline__ int32_t to_fixed(double v, int f) {
+    double y = rint(ldexp(v, 31 - f));
+    y = fmax(-2147483647.0, fmin(2147483647.0, y));
+    return (int32_t)y;
+}
+
+// One warp per row of op(L): row exponent and |row| sum (bound on the output
+// growth).  The largest row sum goes to *g through an atomic maximum on the
+// bits of a non-negative double.
+template <typename T>
+__global__ void fx_rows_kernel(const T *__restrict__ B, IdxMap colB, IdxMap kB, int64_t N, int64_t K, int *f,
+                               unsigned long long *g) {
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (row >= N) return;
+    const int64_t ro = imap(colB, row);
+    double mx = 0.0, sum = 0.0;
+    for (int64_t k = lane; k < K; k += 32) {
+        const double v = fabs((double)B[ro + imap(kB, k)]);
+        mx = fmax(mx, v);
+        sum += v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    }
+    if (lane == 0) {
+        f[row] = exp_bound(mx);
+        atomicMax(g, (unsigned long long)__double_as_longlong(sum));
+    }
+}
+
+// Image items (nt, kb, row, chunk): eight consecutive k of one row of op(L),
+// fixed point with the row's exponent, cut into the four slices.
+template <typename T>
+__global__ void fx_image_kernel(const T *__restrict__ B, IdxMap colB, IdxMap kB, int64_t N, int64_t K, int BN,
+                                int64_t KB, int64_t NT, const int *__restrict__ f, uint8_t *img) {
+    constexpr int BK = kRowBytes / 2;
+    const int64_t total = NT * KB * BN * kChunks;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int ch = (int)(idx % kChunks);
+        int64_t rest = idx / kChunks;
+        const int row = (int)(rest % BN);
+        rest /= BN;
+        const int64_t kb = rest % KB;
+        const int64_t nt = rest / KB;
+        const int64_t c = nt * BN + row;
+        int32_t x[8];
+        const int fc = c < N ? f[c] : 0;
+        const int64_t ro = c < N ? imap(colB, c) : 0;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int64_t k = kb * BK + ch * 8 + e;
+            x[e] = (c < N && k < K) ? to_fixed((double)B[ro + imap(kB, k)], fc) : 0;
+        }
+        uint4 out[4];
+        fx_pack(x, out);
+        uint8_t *base = img + (size_t)((nt * KB + kb) * 4) * BN * kRowBytes;
+        const uint32_t off = swz(row, ch);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4 *>(base + (size_t)q * BN * kRowBytes + off) = out[q];
+    }
+}
+
+template <typename T>
+__global__ void fx_maxabs_kernel(const T *__restrict__ src, int64_t n, unsigned long long *mx) {
+    double m = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs((double)src[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(mx, (unsigned long long)__double_as_longlong(m));
+}
+
+template <typename T>
+__global__ void fx_convert_kernel(const T *__restrict__ src, int64_t n, const unsigned long long *mx, int32_t *X,
+                                  FxScale *s) {
+    const int e = exp_bound(__longlong_as_double((long long)*mx));
+    unsigned m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t x = to_fixed((double)src[i], e);
+        X[i] = x;
+        m = max(m, (unsigned)(x < 0 ? -x : x));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(&s->maxabs, m);
+    if (blockIdx.x == 0 && threadIdx.x == 0) s->e = e;
+}
+
+}  // namespace
+
+cudaError_t fx_reset(FxScale *s, cudaStream_t st) {
+    return cudaMemsetAsync(&s->maxabs, 0, sizeof(unsigned), st);
+}
+
+cudaError_t fx_build_bimage(const Contraction &c, void *img, int *f, unsigned long long *g, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(g, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    const unsigned rows_blocks = (unsigned)((c.N + 7) / 8);
+    if (c.B_f64)
+        fx_rows_kernel<double><<<rows_blocks, 256, 0, st>>>(static_cast<const double *>(c.B), c.colB, c.kB, c.N, c.K, f, g);
+    else
+        fx_rows_kernel<float><<<rows_blocks, 256, 0, st>>>(static_cast<const float *>(c.B), c.colB, c.kB, c.N, c.K, f, g);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int bn = tc_tile_n(kFX32, c.N);
+    const int64_t nt = (c.N + bn - 1) / bn;
+    const int64_t kb = (c.K + kRowBytes / 2 - 1) / (kRowBytes / 2);
+    const int64_t total = nt * kb * bn * kChunks;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 16));
+    auto *out = static_cast<uint8_t *>(img);
+    if (c.B_f64)
+        fx_image_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double *>(c.B), c.colB, c.kB, c.N, c.K, bn,
+                                                        kb, nt, f, out);
+    else
+        fx_image_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float *>(c.B), c.colB, c.kB, c.N, c.K, bn, kb,
+                                                       nt, f, out);
+    return cudaGetLastError();
+}
+
+cudaError_t fx_from_float(const void *src, bool src64, int64_t count, int32_t *X, FxScale *s,
+                          unsigned long long *scratch, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = fx_reset(s, st);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, 152 * 8));
+    if (src64) {
+        fx_maxabs_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double *>(src), count, scratch);
+        fx_convert_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double *>(src), count, scratch, X, s);
+    } else {
+        fx_maxabs_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float *>(src), count, scratch);
+        fx_convert_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float *>(src), count, scratch, X, s);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace kron

@@ -41,17 +41,26 @@ struct Contraction {
 };
 
 // The split-precision forms of the tensor-core path.
-enum TcForm { kTF32x3 = 0, kBF16x3 = 1, kBF16x6 = 2 };
+enum TcForm { kTF32x3 = 0, kBF16x3 = 1, kBF16x6 = 2, kFX32 = 3 };
 
 inline int form_of(kron_prec p) {
     switch (p) {
         case KRON_PREC_3XTF32: return kTF32x3;
         case KRON_PREC_BF16X3: return kBF16x3;
         case KRON_PREC_BF16X6: return kBF16x6;
+        case KRON_PREC_FX32: return kFX32;
         default: return -1;
     }
 }
-inline bool is_split(kron_prec p) { return form_of(p) >= 0; }
+inline bool is_split(kron_prec p) { return form_of(p) >= 0 && p != KRON_PREC_FX32; }
+inline bool is_fx(kron_prec p) { return p == KRON_PREC_FX32; }
+
+// Scale word of a 32-bit fixed-point tensor: value = X * 2^(e - 31), and the
+// largest |X| stored (maintained with atomicMax by the kernel that writes X).
+struct FxScale {
+    int e;
+    unsigned maxabs;
+};
 
 // ---- tensor-core path (tc.cu) ----
 // Bytes of the pre-split, pre-swizzled image of an (N x K) B operand.
@@ -72,6 +81,22 @@ cudaError_t tc_contract_splitk(int form, const Contraction &c, float *partial, c
 // ---- persistent tensor-core path (tcp.cu) ----
 // One contraction (B from an image made by tc_build_bimage).
 cudaError_t tcp_contract(int form, const Contraction &c, const void *img, cudaStream_t st);
+// One fixed-point contraction (FX32): A 32-bit fixed point (scale fxA), B
+// from an image made by fx_build_bimage (row exponents fxF, row-sum bound
+// fxG); C 32-bit fixed point with scale fxC, or values when fxC is null.
+cudaError_t tcp_contract_fx(const Contraction &c, const void *img, const FxScale *fxA, const int *fxF,
+                            const unsigned long long *fxG, FxScale *fxC, cudaStream_t st);
+
+// ---- fixed-point helpers (fx.cu) ----
+// Image of op(L) for the FX32 form (same layout as tc_build_bimage, four
+// slices), per-row exponents f[N] and the row-sum bound *g (zeroed here).
+cudaError_t fx_build_bimage(const Contraction &c, void *img, int *f, unsigned long long *g, cudaStream_t st);
+// Dense FP64/FP32 tensor of `count` elements -> 32-bit fixed point X with
+// one scale (written to *s); `scratch` is 8 bytes of device memory.
+cudaError_t fx_from_float(const void *src, bool src64, int64_t count, int32_t *X, FxScale *s,
+                          unsigned long long *scratch, cudaStream_t st);
+// Zeroes the running maximum of a scale word before a kernel fills it.
+cudaError_t fx_reset(FxScale *s, cudaStream_t st);
 // A table of contractions run by one persistent launch; a job may wait for
 // an earlier one (dep = its index) whose output it reads.
 struct TcpJobs {

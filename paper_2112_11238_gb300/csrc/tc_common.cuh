@@ -25,10 +25,29 @@ struct FT<kBF16x6> {
     static constexpr int KIND = 1, PIECES = 3, ELEM = 2, NPROD = 6, FMT = 1, MMA_K = 16;
 };
 
+template <>
+struct FT<kFX32> {
+    static constexpr int KIND = 1, PIECES = 4, ELEM = 2, NPROD = 10, FMT = 1, MMA_K = 16;
+};
+
+// Tensor-memory accumulator regions per accumulator set: the split forms keep
+// hi*hi (region 0) apart from the cross products (region 1); the fixed-point
+// form keeps level 0, level 1 and the rest (levels 2 and 3) apart.
+template <int F>
+struct Regions {
+    static constexpr int N = (F == kFX32) ? 3 : 2;
+};
+
 // Products (piece of A, piece of B), smallest magnitude first.
 template <int F>
 __device__ __forceinline__ void prod_pieces(int i, int &pa, int &pb) {
-    if constexpr (FT<F>::PIECES == 2) {
+    if constexpr (F == kFX32) {
+        // levels 3 and 2, then level 1, then level 0
+        const int ta[10] = {3, 2, 1, 0, 2, 1, 0, 1, 0, 0};
+        const int tb[10] = {0, 1, 2, 3, 0, 1, 2, 0, 1, 0};
+        pa = ta[i];
+        pb = tb[i];
+    } else if constexpr (FT<F>::PIECES == 2) {
         // lo*hi, hi*lo, hi*hi
         pa = (i == 0) ? 1 : 0;
         pb = (i == 1) ? 1 : 0;
@@ -39,6 +58,18 @@ __device__ __forceinline__ void prod_pieces(int i, int &pa, int &pb) {
         pa = ta[i];
         pb = tb[i];
     }
+}
+
+// Region of product i and whether it is the first product written there.
+template <int F>
+__device__ __forceinline__ int region_of(int i) {
+    if constexpr (F == kFX32) return i < 7 ? 2 : (i < 9 ? 1 : 0);
+    else return (i == FT<F>::NPROD - 1) ? 0 : 1;
+}
+template <int F>
+__device__ __forceinline__ bool first_in_region(int i) {
+    if constexpr (F == kFX32) return i == 0 || i == 7 || i == 9;
+    else return i == 0 || i == FT<F>::NPROD - 1;
 }
 
 constexpr int kRowBytes = 64;       // bytes of one K-major row per K-block (64-byte swizzle)
@@ -132,6 +163,47 @@ __device__ __forceinline__ void split_pack(const Tin (&v)[16 / FT<F>::ELEM], uin
             out[p] = make_uint4(w[p][0] | (w[p][1] << 16), w[p][2] | (w[p][3] << 16),
                                 w[p][4] | (w[p][5] << 16), w[p][6] | (w[p][7] << 16));
     }
+}
+
+// 32-bit fixed-point value -> four balanced base-256 digits,
+// x = d0 2^24 + d1 2^16 + d2 2^8 + d3 with d1..d3 in [-128, 127] and
+// d0 in [-128, 128]; slice t = d_t * 2^(-8t), exact in bf16.  Balanced
+// digits make the slice products left out (levels 4 and up) average to zero
+// instead of always pulling the same way.  Returns the bf16 bit patterns.
+__device__ __forceinline__ void fx_slices(int32_t x, uint32_t (&b)[4]) {
+    int d[4];
+    int r = x;
+#pragma unroll
+    for (int t = 3; t >= 1; --t) {
+        const int lo = ((r & 0xFF) ^ 0x80) - 0x80;
+        d[t] = lo;
+        r = (r - lo) >> 8;
+    }
+    d[0] = r;
+    const float scale[4] = {1.0f, 0.00390625f, 1.52587890625e-05f, 5.9604644775390625e-08f};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const uint32_t a = (uint32_t)(d[t] < 0 ? -d[t] : d[t]);
+        // exact small-integer to float: (2^23 + a) - 2^23
+        const float f = (__uint_as_float(0x4B000000u | a) - 8388608.0f) * scale[t];
+        b[t] = (a == 0) ? 0u : ((__float_as_uint(f) >> 16) | (d[t] < 0 ? 0x8000u : 0u));
+    }
+}
+
+// Eight fixed-point values -> one 16-byte chunk per slice.
+__device__ __forceinline__ void fx_pack(const int32_t (&v)[8], uint4 (&out)[4]) {
+    uint32_t w[4][8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        uint32_t b[4];
+        fx_slices(v[e], b);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) w[t][e] = b[t];
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+        out[t] = make_uint4(w[t][0] | (w[t][1] << 16), w[t][2] | (w[t][3] << 16), w[t][4] | (w[t][5] << 16),
+                            w[t][6] | (w[t][7] << 16));
 }
 
 template <int F, typename Tin>

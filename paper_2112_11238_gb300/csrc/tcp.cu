@@ -50,7 +50,14 @@ struct TcJob {
     int32_t dep, dep_tiles;
     int32_t a64, c64, acc, avec, akc;
     int32_t publish;   // some later job waits for this one
-    int32_t cp16;      // FP32 source: 16-byte asynchronous copies are legal
+    int32_t cp16;      // 4-byte source: 16-byte asynchronous copies are legal
+    // fixed-point form: scale of A, scale of C (when C is fixed point),
+    // row exponents of op(L) and the bound of its row sums
+    const FxScale *fxA;
+    FxScale *fxC;
+    const int *fxF;
+    const unsigned long long *fxG;
+    int32_t cfix;      // C is 32-bit fixed point
 };
 
 // Raw (unsplit FP32) A tiles staged by cp.async ahead of the converters.
@@ -59,7 +66,7 @@ struct RawCfg {
     static constexpr int BK = kRowBytes / FT<F>::ELEM;
     static constexpr int BYTES = kBM * BK * 4;                 // one K-block of FP32 rows
     static constexpr int UNITS = BYTES / 16 / (32 * kConv);    // 16-byte units per converter thread
-    static constexpr int STAGES = 4;
+    static constexpr int STAGES = (F == kFX32) ? 2 : 4;
 };
 
 struct TcLaunch {
@@ -292,7 +299,14 @@ __device__ __forceinline__ bool conv_tile_loop_raw(const TcJob &J, int mt, uint8
                 for (int e = 0; e < CH; ++e) v[e] = raw[(ich[i] * CH + e) * kBM + irow[i]];
             }
             uint4 out[FT<F>::PIECES];
-            split_pack<F, float>(v, out);
+            if constexpr (F == kFX32) {
+                int32_t x[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) x[e] = __float_as_int(v[e]);
+                fx_pack(x, out);
+            } else {
+                split_pack<F, float>(v, out);
+            }
             const uint32_t off = swz(irow[i], ich[i]);
 #pragma unroll
             for (int q = 0; q < FT<F>::PIECES; ++q)
@@ -304,6 +318,70 @@ __device__ __forceinline__ bool conv_tile_loop_raw(const TcJob &J, int mt, uint8
     }
     cp_async_wait<0>();
     return true;
+}
+
+// Fixed-point form epilogue for one tile row: the three accumulator regions
+// (level 0 and level 1 exact, the rest small) are combined in 64-bit
+// integers, T = 2^16 (a0 + a1 + a2), then written either as 32-bit fixed
+// point with the output scale (tracking the largest magnitude) or as the
+// value T * 2^(eA + f_c - 30).
+__device__ __forceinline__ void fx_epilogue(const TcJob &J, uint32_t lane_base, uint32_t ACOLS, int64_t ro,
+                                            int64_t n0, int warp, int lane) {
+    const int eA = J.fxA->e;
+    const unsigned mA = J.fxA->maxabs;
+    const int eAact = eA - 31 + (mA ? 32 - __clz((int)mA) : 0);
+    int g = 0;
+    {
+        const double rs = __longlong_as_double((long long)*J.fxG);
+        if (rs > 0.0) frexp(rs, &g);
+    }
+    const int eC = eAact + g;
+    if (J.cfix && warp == 2 && lane == 0) J.fxC->e = eC;
+    const int64_t lim = min(J.N - n0, (int64_t)J.BN);
+    unsigned mx = 0;
+    for (int c0 = 0; c0 < J.BN; c0 += 16) {
+        uint32_t r0[16], r1[16], r2[16];
+        tmem_ld16(lane_base + (uint32_t)c0, r0);
+        tmem_ld16(lane_base + ACOLS + (uint32_t)c0, r1);
+        tmem_ld16(lane_base + 2u * ACOLS + (uint32_t)c0, r2);
+        tmem_ld_wait();
+        if (ro < 0) continue;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            if (c0 + e >= lim) continue;
+            const int64_t c = n0 + c0 + e;
+            const long long I0 = __float2ll_rz(__uint_as_float(r0[e]));
+            const long long I1 = __float2ll_rn(__uint_as_float(r1[e]) * 256.0f);
+            const long long I2 = __float2ll_rn(__uint_as_float(r2[e]) * 65536.0f);
+            const long long Tq = I0 * 65536 + I1 * 256 + I2;
+            const int f = J.fxF[c];
+            const int64_t off = ro + imap(J.colC, c);
+            if (J.cfix) {
+                const int sh = eA + f + 1 - eC;
+                long long X;
+                if (sh >= 0) X = (sh < 40) ? (Tq << sh) : (Tq > 0 ? (1ll << 40) : (Tq < 0 ? -(1ll << 40) : 0));
+                else if (sh > -63) X = (Tq + (1ll << (-sh - 1))) >> (-sh);
+                else X = 0;
+                X = max(-2147483647ll, min(2147483647ll, X));
+                static_cast<int32_t *>(J.C)[off] = (int32_t)X;
+                mx = max(mx, (unsigned)(X < 0 ? -X : X));
+            } else {
+                const double v = ldexp((double)Tq, eA + f - 30);
+                if (J.c64) {
+                    double *d = static_cast<double *>(J.C) + off;
+                    *d = J.acc ? *d + v : v;
+                } else {
+                    float *d = static_cast<float *>(J.C) + off;
+                    *d = J.acc ? (float)((double)*d + v) : (float)v;
+                }
+            }
+        }
+    }
+    if (J.cfix) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0 && mx) atomicMax(&J.fxC->maxabs, mx);
+    }
 }
 
 template <int F>
@@ -324,7 +402,9 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const TcLaunch L) {
     uint64_t *bars = reinterpret_cast<uint64_t *>(sRaw + (size_t)RawCfg<F>::STAGES * RawCfg<F>::BYTES);
     uint64_t *full = bars, *empty = bars + S, *accf = bars + 2 * S, *acce = bars + 2 * S + NBUF;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * S + 2 * NBUF);
-    const uint32_t ncols = ACOLS * 2u * (uint32_t)NACC * (uint32_t)NBUF;
+    constexpr int RG = Regions<F>::N;
+    uint32_t ncols = ACOLS * (uint32_t)RG * (uint32_t)NACC * (uint32_t)NBUF;
+    ncols = ncols <= 32 ? 32u : (ncols <= 64 ? 64u : (ncols <= 128 ? 128u : (ncols <= 256 ? 256u : 512u)));
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -384,7 +464,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const TcLaunch L) {
                 tc_fence_after();
                 const uint32_t idesc = make_idesc(T::FMT, kBM, (uint32_t)J.BN);
                 const uint32_t PIECE_B = (uint32_t)J.BN * kRowBytes;
-                const uint32_t dbase = tmem + (uint32_t)(buf * NACC) * 2u * ACOLS;
+                const uint32_t dbase = tmem + (uint32_t)(buf * NACC * RG) * ACOLS;
                 for (int kb = 0; kb < J.nkb; ++kb, ++g) {
                     const int s = (int)(g % (uint32_t)S);
                     const uint32_t ph = (g / (uint32_t)S) & 1u;
@@ -397,8 +477,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const TcLaunch L) {
                     const int ksteps = (int)((kval + T::MMA_K - 1) / T::MMA_K);
                     const uint32_t a_base = smem_u32(sA + (size_t)s * A_ST);
                     const uint32_t b_base = smem_u32(sB + (size_t)s * B_ST);
-                    const uint32_t dhi = dbase + (uint32_t)(kb % NACC) * 2u * ACOLS;
-                    const uint32_t dlo = dhi + ACOLS;
+                    const uint32_t dset = dbase + (uint32_t)(kb % NACC) * (uint32_t)RG * ACOLS;
                     const bool fresh = kb < NACC;
                     for (int ks = 0; ks < ksteps; ++ks) {
 #pragma unroll
@@ -407,9 +486,8 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const TcLaunch L) {
                             prod_pieces<F>(pr, pa, pb);
                             const uint64_t ad = smem_desc_kmajor(a_base + pa * PIECE_A + ks * 32, kRowBytes);
                             const uint64_t bd = smem_desc_kmajor(b_base + pb * PIECE_B + ks * 32, kRowBytes);
-                            const bool is_hi = (pr == T::NPROD - 1);
-                            const bool first = fresh && ks == 0 && (is_hi || pr == 0);
-                            tc_mma<T::KIND>(is_hi ? dhi : dlo, ad, bd, idesc, first ? 0u : 1u);
+                            const bool first = fresh && ks == 0 && first_in_region<F>(pr);
+                            tc_mma<T::KIND>(dset + (uint32_t)region_of<F>(pr) * ACOLS, ad, bd, idesc, first ? 0u : 1u);
                         }
                     }
                     tc_commit(smem_u32(&empty[s]));
@@ -439,7 +517,10 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const TcLaunch L) {
             const int64_t n0 = (int64_t)nt * J.BN;
             const int used = min(NACC, J.nkb);
             const uint32_t lane_base =
-                tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * NACC) * 2u * ACOLS;
+                tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * NACC * RG) * ACOLS;
+            if constexpr (F == kFX32) {
+                fx_epilogue(J, lane_base, ACOLS, ro, n0, warp, lane);
+            } else
             for (int c0 = 0; c0 < J.BN; c0 += 32) {
                 // accumulator 0: hi + cross in FP32; further accumulators are
                 // added in order
@@ -451,8 +532,8 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const TcLaunch L) {
                 for (int e = 0; e < 32; ++e) h[e] = __float_as_uint(__uint_as_float(l[e]) + __uint_as_float(h[e]));
                 for (int a = 1; a < used; ++a) {
                     uint32_t x[32];
-                    tmem_ld32(lane_base + (uint32_t)(2 * a) * ACOLS + (uint32_t)c0, l);
-                    tmem_ld32(lane_base + (uint32_t)(2 * a + 1) * ACOLS + (uint32_t)c0, x);
+                    tmem_ld32(lane_base + (uint32_t)(RG * a) * ACOLS + (uint32_t)c0, l);
+                    tmem_ld32(lane_base + (uint32_t)(RG * a + 1) * ACOLS + (uint32_t)c0, x);
                     tmem_ld_wait();
 #pragma unroll
                     for (int e = 0; e < 32; ++e)
@@ -525,7 +606,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const TcLaunch L) {
 
 // ---------------------------------------------------------------- host side
 
-static int pieces_of_f(int form) { return form == kBF16x6 ? 3 : 2; }
+static int pieces_of_f(int form) { return form == kFX32 ? 4 : (form == kBF16x6 ? 3 : 2); }
 static int bk_of_f(int form) { return form == kTF32x3 ? kRowBytes / 4 : kRowBytes / 2; }
 
 size_t tcp_job_bytes() { return sizeof(TcJob); }
@@ -578,12 +659,14 @@ static constexpr size_t kSmemMax = 227 * 1024;
 static void pick_config(int form, int bn_max, int nkb_max, int &stages, int &nacc, int &nbuf, int &acc_cols,
                         size_t &smem) {
     acc_cols = bn_max <= 32 ? 32 : (bn_max <= 64 ? 64 : 128);
-    // two accumulator buffers (epilogue overlapped) when the K loop is short,
-    // more accumulators per tile (accuracy) when it is long
-    const int budget = 512 / (2 * acc_cols);  // NACC * NBUF
+    // two accumulator buffers (epilogue overlapped) when tensor memory
+    // allows, then more accumulator sets per tile (accuracy)
+    const int rg = (form == kFX32) ? 3 : 2;
+    const int budget = std::max(1, 512 / (rg * acc_cols));  // NACC * NBUF
     nbuf = std::min(2, budget);
     nacc = std::max(1, std::min(4, budget / nbuf));
-    if (nkb_max < 2) nacc = 1;
+    // the fixed-point form keeps one exact accumulator set per tile
+    if (nkb_max < 2 || form == kFX32) nacc = 1;
     const size_t a_st = (size_t)pieces_of_f(form) * kBM * kRowBytes;
     const size_t b_st = (size_t)pieces_of_f(form) * bn_max * kRowBytes;
     const size_t extra = 1024 + (size_t)(2 * 8 + 2 * 4 + 2) * 8;
@@ -591,6 +674,7 @@ static void pick_config(int form, int bn_max, int nkb_max, int &stages, int &nac
     switch (form) {
         case kTF32x3: raw = (size_t)RawCfg<kTF32x3>::STAGES * RawCfg<kTF32x3>::BYTES; break;
         case kBF16x3: raw = (size_t)RawCfg<kBF16x3>::STAGES * RawCfg<kBF16x3>::BYTES; break;
+        case kFX32: raw = (size_t)RawCfg<kFX32>::STAGES * RawCfg<kFX32>::BYTES; break;
         default: raw = (size_t)RawCfg<kBF16x6>::STAGES * RawCfg<kBF16x6>::BYTES; break;
     }
     stages = 1;
@@ -648,8 +732,27 @@ static cudaError_t tcp_launch(int form, const TcJob *jobs, int njobs, int total_
         case kTF32x3: return launch_f<kTF32x3>(L, grid, smem, st);
         case kBF16x3: return launch_f<kBF16x3>(L, grid, smem, st);
         case kBF16x6: return launch_f<kBF16x6>(L, grid, smem, st);
+        case kFX32: return launch_f<kFX32>(L, grid, smem, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// One fixed-point contraction: A is 32-bit fixed point with scale fxA, the
+// image of op(L) comes with its row exponents and row-sum bound; C is fixed
+// point with scale fxC (cfix) or a value tensor.
+cudaError_t tcp_contract_fx(const Contraction &c, const void *img, const FxScale *fxA, const int *fxF,
+                            const unsigned long long *fxG, FxScale *fxC, cudaStream_t st) {
+    if (c.M == 0 || c.N == 0) return cudaSuccess;
+    TcJob J = make_job(kFX32, c, img);
+    J.fxA = fxA;
+    J.fxF = fxF;
+    J.fxG = fxG;
+    J.fxC = fxC;
+    J.cfix = fxC != nullptr;
+    J.a64 = 0;
+    J.tile_begin = 0;
+    const int tiles = J.tiles_m * J.tiles_n;
+    return tcp_launch(kFX32, &J, 1, tiles, J.BN, J.nkb, nullptr, nullptr, st);
 }
 
 // One contraction with the B side from an image built by tc_build_bimage.

@@ -35,7 +35,7 @@ def cfg_d3():
     return c, oracle.tucker(c.T, c.L)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "3xtf32", "bf16x3", "bf16x6"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "3xtf32", "bf16x3", "bf16x6", "fx32"])
 def test_tucker_d3_n100(kron, cfg_d3, prec):
     c, ref = cfg_d3
     S = kron.tucker(to_dev(c.T), [to_dev(L) for L in c.L], prec=prec)
@@ -53,11 +53,11 @@ def cfg_d6():
     return c, idx, ref
 
 
-@pytest.mark.parametrize("prec", ["fp64", "3xtf32", "bf16x3", "bf16x6", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "3xtf32", "bf16x3", "bf16x6", "fp32", "fx32"])
 def test_tucker_d6_n20_sampled(kron, cfg_d6, prec):
     import torch
     c, idx, ref = cfg_d6
-    dtype = torch.float64 if prec == "fp64" else torch.float32
+    dtype = torch.float64 if prec in ("fp64", "fx32") else torch.float32
     S = kron.tucker(to_dev(c.T, dtype), [to_dev(L, dtype) for L in c.L], prec=prec)
     ix = [torch.as_tensor(i, device=S.device) for i in idx]
     sub = S
@@ -82,6 +82,17 @@ def test_stepper_fp64_100_steps(kron, cfg_stepper):
     err = rel_err(to_host(U), ref)
     print(f"stepper fp64 100 steps: {err:.3e}")
     assert err <= 1e-12
+    assert kron.device_error() == 0
+
+
+def test_stepper_fx32_100_steps(kron, cfg_stepper):
+    """The fixed-point form keeps about 31 bits per value and per product, so
+    the 300 chained mode products of the 100 steps stay within 2e-6."""
+    c, ref = cfg_stepper
+    U = kron.expkronsum_step(to_dev(c.U0), [to_dev(A) for A in c.A], c.tau, c.nsteps, prec="fx32")
+    err = rel_err(to_host(U), ref)
+    print(f"stepper fx32 100 steps: {err:.3e}")
+    assert err <= 2e-6
     assert kron.device_error() == 0
 
 

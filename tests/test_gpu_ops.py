@@ -10,7 +10,7 @@ from gpu_util import TOL, rel_err, to_dev, to_host, tol
 pytestmark = pytest.mark.gpu
 
 RNG = np.random.default_rng(2024)
-PRECS = ["fp64", "fp32", "3xtf32", "bf16x3", "bf16x6"]
+PRECS = ["fp64", "fp32", "3xtf32", "bf16x3", "bf16x6", "fx32"]
 
 
 def rnd(*s):
