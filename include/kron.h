@@ -82,9 +82,9 @@ typedef enum kron_dtype { KRON_F64 = 0, KRON_F32 = 1 } kron_dtype;
  *                     cut into four balanced base-256 digits stored exactly as
  *                     bf16 (so the products left out average to zero), and
  *                     the ten slice products down to 2^-24 are accumulated in
- *                     three tensor-memory accumulators, the two leading ones
- *                     exactly (integer-valued sums below 2^24), then combined
- *                     in 64-bit integer arithmetic.  About 31 significant bits
+ *                     two tensor-memory accumulators, the leading one exactly
+ *                     (integer-valued sums below 2^24), then combined in
+ *                     64-bit integer arithmetic.  About 31 significant bits
  *                     per stored value and per product, for contraction
  *                     lengths up to 256; intermediates are 32-bit fixed point.
  *                     Supported by kron_mump, kron_tucker and the stepper.

@@ -7,6 +7,7 @@
 // Y = round(L[c, :] * 2^(31 - f_c)) with 2^(f_c - 1) <= max_k |L[c, k]| < 2^f_c.
 // Both are cut into four 8-bit slices (fx_pack, tc_common.cuh).
 #include <algorithm>
+#include <climits>
 
 #include "tc_common.cuh"
 
@@ -87,23 +88,58 @@ __global__ void fx_image_kernel(const T *__restrict__ B, IdxMap colB, IdxMap kB,
     }
 }
 
-template <typename T>
-__global__ void fx_maxabs_kernel(const T *__restrict__ src, int64_t n, unsigned long long *mx) {
-    double m = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        m = fmax(m, fabs((double)src[i]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(mx, (unsigned long long)__double_as_longlong(m));
+// Smallest e with |v| < 2^e for a normal nonzero v (INT_MIN for zero and
+// subnormal values, which the fixed point rounds to zero anyway); integer
+// operations only.
+__device__ __forceinline__ int ebound(double v) {
+    const int E = (int)((__double_as_longlong(v) >> 52) & 0x7FF);
+    return E ? E - 1022 : INT_MIN;
+}
+__device__ __forceinline__ int ebound(float v) {
+    const int E = (int)((__float_as_uint(v) >> 23) & 0xFF);
+    return E ? E - 126 : INT_MIN;
+}
+
+// round(v * 2^(31 - e)) from the bits of v, for |v| < 2^e (integer only).
+__device__ __forceinline__ int32_t fixed_bits(double v, int e) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int E = (int)((b >> 52) & 0x7FF);
+    if (E == 0) return 0;
+    const unsigned long long mant = (1ull << 52) | (b & ((1ull << 52) - 1));
+    const int r = e + 1044 - E;  // right shift, >= 22 when |v| < 2^e
+    unsigned long long x = 0;
+    if (r < 64) x = r > 0 ? (mant + (1ull << (r - 1))) >> r : mant << (-r);
+    if (x > 2147483647ull) x = 2147483647ull;
+    return (b >> 63) ? -(int32_t)x : (int32_t)x;
+}
+__device__ __forceinline__ int32_t fixed_bits(float v, int e) {
+    const uint32_t b = __float_as_uint(v);
+    const int E = (int)((b >> 23) & 0xFF);
+    if (E == 0) return 0;
+    const unsigned long long mant = (1u << 23) | (b & ((1u << 23) - 1));
+    const int r = e + 119 - E;
+    unsigned long long x = 0;
+    if (r < 64) x = r > 0 ? (mant + (1ull << (r - 1))) >> r : mant << (-r);
+    if (x > 2147483647ull) x = 2147483647ull;
+    return (b >> 31) ? -(int32_t)x : (int32_t)x;
 }
 
 template <typename T>
-__global__ void fx_convert_kernel(const T *__restrict__ src, int64_t n, const unsigned long long *mx, int32_t *X,
-                                  FxScale *s) {
-    const int e = exp_bound(__longlong_as_double((long long)*mx));
+__global__ void fx_maxabs_kernel(const T *__restrict__ src, int64_t n, int *emax) {
+    int m = INT_MIN;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, ebound(src[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m != INT_MIN) atomicMax(emax, m);
+}
+
+template <typename T>
+__global__ void fx_convert_kernel(const T *__restrict__ src, int64_t n, const int *emax, int32_t *X, FxScale *s) {
+    const int e = (*emax < -100000) ? 0 : *emax;  // all-zero tensor: any scale
     unsigned m = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t x = to_fixed((double)src[i], e);
+        const int32_t x = fixed_bits(src[i], e);
         X[i] = x;
         m = max(m, (unsigned)(x < 0 ? -x : x));
     }
@@ -146,16 +182,17 @@ cudaError_t fx_build_bimage(const Contraction &c, void *img, int *f, unsigned lo
 
 cudaError_t fx_from_float(const void *src, bool src64, int64_t count, int32_t *X, FxScale *s,
                           unsigned long long *scratch, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), st);
+    int *emax = reinterpret_cast<int *>(scratch);
+    cudaError_t e = cudaMemsetAsync(emax, 0x80, sizeof(int), st);  // 0x80808080: below every bound
     if (e == cudaSuccess) e = fx_reset(s, st);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, 152 * 8));
     if (src64) {
-        fx_maxabs_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double *>(src), count, scratch);
-        fx_convert_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double *>(src), count, scratch, X, s);
+        fx_maxabs_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double *>(src), count, emax);
+        fx_convert_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double *>(src), count, emax, X, s);
     } else {
-        fx_maxabs_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float *>(src), count, scratch);
-        fx_convert_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float *>(src), count, scratch, X, s);
+        fx_maxabs_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float *>(src), count, emax);
+        fx_convert_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float *>(src), count, emax, X, s);
     }
     return cudaGetLastError();
 }

@@ -32,10 +32,13 @@ struct FT<kFX32> {
 
 // Tensor-memory accumulator regions per accumulator set: the split forms keep
 // hi*hi (region 0) apart from the cross products (region 1); the fixed-point
-// form keeps level 0, level 1 and the rest (levels 2 and 3) apart.
+// form keeps level 0 (exact: integer-valued sums below 2^24) apart from
+// levels 1..3 (region 1; with balanced digits its partial sums have no
+// preferred sign, so the truncation of the FP32 accumulation does not
+// accumulate a bias).
 template <int F>
 struct Regions {
-    static constexpr int N = (F == kFX32) ? 3 : 2;
+    static constexpr int N = 2;
 };
 
 // Products (piece of A, piece of B), smallest magnitude first.
@@ -63,13 +66,11 @@ __device__ __forceinline__ void prod_pieces(int i, int &pa, int &pb) {
 // Region of product i and whether it is the first product written there.
 template <int F>
 __device__ __forceinline__ int region_of(int i) {
-    if constexpr (F == kFX32) return i < 7 ? 2 : (i < 9 ? 1 : 0);
-    else return (i == FT<F>::NPROD - 1) ? 0 : 1;
+    return (i == FT<F>::NPROD - 1) ? 0 : 1;
 }
 template <int F>
 __device__ __forceinline__ bool first_in_region(int i) {
-    if constexpr (F == kFX32) return i == 0 || i == 7 || i == 9;
-    else return i == 0 || i == FT<F>::NPROD - 1;
+    return i == 0 || i == FT<F>::NPROD - 1;
 }
 
 constexpr int kRowBytes = 64;       // bytes of one K-major row per K-block (64-byte swizzle)
@@ -165,45 +166,36 @@ __device__ __forceinline__ void split_pack(const Tin (&v)[16 / FT<F>::ELEM], uin
     }
 }
 
-// 32-bit fixed-point value -> four balanced base-256 digits,
+// 32-bit fixed-point values -> four balanced base-256 digits each,
 // x = d0 2^24 + d1 2^16 + d2 2^8 + d3 with d1..d3 in [-128, 127] and
 // d0 in [-128, 128]; slice t = d_t * 2^(-8t), exact in bf16.  Balanced
 // digits make the slice products left out (levels 4 and up) average to zero
-// instead of always pulling the same way.  Returns the bf16 bit patterns.
-__device__ __forceinline__ void fx_slices(int32_t x, uint32_t (&b)[4]) {
-    int d[4];
-    int r = x;
-#pragma unroll
-    for (int t = 3; t >= 1; --t) {
-        const int lo = ((r & 0xFF) ^ 0x80) - 0x80;
-        d[t] = lo;
-        r = (r - lo) >> 8;
-    }
-    d[0] = r;
-    const float scale[4] = {1.0f, 0.00390625f, 1.52587890625e-05f, 5.9604644775390625e-08f};
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        const uint32_t a = (uint32_t)(d[t] < 0 ? -d[t] : d[t]);
-        // exact small-integer to float: (2^23 + a) - 2^23
-        const float f = (__uint_as_float(0x4B000000u | a) - 8388608.0f) * scale[t];
-        b[t] = (a == 0) ? 0u : ((__float_as_uint(f) >> 16) | (d[t] < 0 ? 0x8000u : 0u));
-    }
-}
-
-// Eight fixed-point values -> one 16-byte chunk per slice.
+// instead of always pulling the same way.
+// Digits without a carry chain: y = x + 0x808080 has the unsigned bytes
+// d1 + 128, d2 + 128, d3 + 128 and y >> 24 = d0.  Each digit becomes a float
+// exactly through the 2^23 exponent trick (one OR, one FMA), and the high
+// halves of two floats are packed into one bf16x2 word with a byte permute.
 __device__ __forceinline__ void fx_pack(const int32_t (&v)[8], uint4 (&out)[4]) {
-    uint32_t w[4][8];
+    uint32_t w[4][4];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        uint32_t b[4];
-        fx_slices(v[e], b);
+    for (int e = 0; e < 8; e += 2) {
+        float f[4][2];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) w[t][e] = b[t];
+        for (int h = 0; h < 2; ++h) {
+            const long long y64 = (long long)v[e + h] + 0x808080ll;
+            const uint32_t y = (uint32_t)y64;
+            const int d0 = (int)(y64 >> 24);
+            f[0][h] = __int_as_float(0x4B400000 + d0) - 12582912.0f;
+            f[1][h] = fmaf(__uint_as_float(0x4B000000u | ((y >> 16) & 0xFFu)), 0.00390625f, -32768.5f);
+            f[2][h] = fmaf(__uint_as_float(0x4B000000u | ((y >> 8) & 0xFFu)), 1.52587890625e-05f, -128.001953125f);
+            f[3][h] = fmaf(__uint_as_float(0x4B000000u | (y & 0xFFu)), 5.9604644775390625e-08f, -0.50000762939453125f);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            w[t][e / 2] = __byte_perm(__float_as_uint(f[t][0]), __float_as_uint(f[t][1]), 0x7632);
     }
 #pragma unroll
-    for (int t = 0; t < 4; ++t)
-        out[t] = make_uint4(w[t][0] | (w[t][1] << 16), w[t][2] | (w[t][3] << 16), w[t][4] | (w[t][5] << 16),
-                            w[t][6] | (w[t][7] << 16));
+    for (int t = 0; t < 4; ++t) out[t] = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
 }
 
 template <int F, typename Tin>

@@ -320,11 +320,11 @@ __device__ __forceinline__ bool conv_tile_loop_raw(const TcJob &J, int mt, uint8
     return true;
 }
 
-// Fixed-point form epilogue for one tile row: the three accumulator regions
-// (level 0 and level 1 exact, the rest small) are combined in 64-bit
-// integers, T = 2^16 (a0 + a1 + a2), then written either as 32-bit fixed
-// point with the output scale (tracking the largest magnitude) or as the
-// value T * 2^(eA + f_c - 30).
+// Fixed-point form epilogue for one tile row: the two accumulator regions
+// (level 0 exact, levels 1..3 small) are combined in 64-bit integers,
+// T = 2^16 (a0 + a1), then written either as 32-bit fixed point with the
+// output scale (tracking the largest magnitude) or as the value
+// T * 2^(eA + f_c - 30).
 __device__ __forceinline__ void fx_epilogue(const TcJob &J, uint32_t lane_base, uint32_t ACOLS, int64_t ro,
                                             int64_t n0, int warp, int lane) {
     const int eA = J.fxA->e;
@@ -340,10 +340,9 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, uint32_t lane_base, 
     const int64_t lim = min(J.N - n0, (int64_t)J.BN);
     unsigned mx = 0;
     for (int c0 = 0; c0 < J.BN; c0 += 16) {
-        uint32_t r0[16], r1[16], r2[16];
+        uint32_t r0[16], r1[16];
         tmem_ld16(lane_base + (uint32_t)c0, r0);
         tmem_ld16(lane_base + ACOLS + (uint32_t)c0, r1);
-        tmem_ld16(lane_base + 2u * ACOLS + (uint32_t)c0, r2);
         tmem_ld_wait();
         if (ro < 0) continue;
 #pragma unroll
@@ -351,9 +350,8 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, uint32_t lane_base, 
             if (c0 + e >= lim) continue;
             const int64_t c = n0 + c0 + e;
             const long long I0 = __float2ll_rz(__uint_as_float(r0[e]));
-            const long long I1 = __float2ll_rn(__uint_as_float(r1[e]) * 256.0f);
-            const long long I2 = __float2ll_rn(__uint_as_float(r2[e]) * 65536.0f);
-            const long long Tq = I0 * 65536 + I1 * 256 + I2;
+            const long long I1 = __float2ll_rn(__uint_as_float(r1[e]) * 65536.0f);
+            const long long Tq = I0 * 65536 + I1;
             const int f = J.fxF[c];
             const int64_t off = ro + imap(J.colC, c);
             if (J.cfix) {
@@ -589,8 +587,13 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const TcLaunch L) {
                 }
                 named_bar(2, 32 * kConv);
             }
-            bool ok = J.a64 ? conv_tile_loop<F, double>(J, mt, sA, A_ST, full, empty, S, g, lane, ct)
-                            : conv_tile_loop_raw<F>(J, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct);
+            bool ok;
+            if constexpr (F == kFX32) {  // always 32-bit fixed point
+                ok = conv_tile_loop_raw<F>(J, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct);
+            } else {
+                ok = J.a64 ? conv_tile_loop<F, double>(J, mt, sA, A_ST, full, empty, S, g, lane, ct)
+                           : conv_tile_loop_raw<F>(J, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct);
+            }
             if (!ok) break;
         }
     }
@@ -661,7 +664,7 @@ static void pick_config(int form, int bn_max, int nkb_max, int &stages, int &nac
     acc_cols = bn_max <= 32 ? 32 : (bn_max <= 64 ? 64 : 128);
     // two accumulator buffers (epilogue overlapped) when tensor memory
     // allows, then more accumulator sets per tile (accuracy)
-    const int rg = (form == kFX32) ? 3 : 2;
+    const int rg = 2;
     const int budget = std::max(1, 512 / (rg * acc_cols));  // NACC * NBUF
     nbuf = std::min(2, budget);
     nacc = std::max(1, std::min(4, budget / nbuf));

@@ -41,7 +41,8 @@ def test_tucker_d3_n100(kron, cfg_d3, prec):
     S = kron.tucker(to_dev(c.T), [to_dev(L) for L in c.L], prec=prec)
     err = rel_err(to_host(S), ref)
     print(f"tucker d=3 n=100 {prec}: max-norm rel err {err:.3e}")
-    assert err <= TOL[prec], err
+    # the workload budget for every split form, the fixed-point one included
+    assert err <= (2e-6 if prec == "fx32" else TOL[prec]), err
 
 
 @pytest.fixture(scope="module")
