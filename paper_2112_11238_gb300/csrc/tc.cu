@@ -386,7 +386,7 @@ cudaError_t tc_error_word(unsigned int *out, bool clear) { return read_error_wor
 
 static int pieces_of(int form) { return form == kFX32 ? 4 : (form == kBF16x6 ? 3 : 2); }
 static int bk_of(int form) { return form == kTF32x3 ? kRowBytes / 4 : kRowBytes / 2; }
-static int max_bn(int form) { return form == kBF16x6 ? 64 : 128; }
+static int max_bn(int form) { return form == kBF16x6 ? 64 : (form == kFX32 ? 256 : 128); }
 
 int tc_tile_n(int form, int64_t N) {
     const int64_t mx = max_bn(form);

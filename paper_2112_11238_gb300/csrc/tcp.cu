@@ -320,11 +320,14 @@ __device__ __forceinline__ bool conv_tile_loop_raw(const TcJob &J, int mt, uint8
     return true;
 }
 
-// Fixed-point form epilogue for one tile row: the two accumulator regions
-// (level 0 exact, levels 1..3 small) are combined in 64-bit integers,
-// T = 2^16 (a0 + a1), then written either as 32-bit fixed point with the
-// output scale (tracking the largest magnitude) or as the value
-// T * 2^(eA + f_c - 30).
+// Fixed-point form epilogue for one tile row.  The two accumulator regions
+// hold a0 (level 0, an exact integer below 2^24) and a1 (levels 1..3, small)
+// in units of 2^(eA + f_c - 14).  Fixed-point output with scale eC:
+//     X = a0 * 2^s + round(a1 * 2^s),  s = eA + f_c + 17 - eC,
+// where s >= 17 - log2(K) > 0 because the row-sum bound g makes eC at most
+// eA + f_c + log2(K): the level-0 part is an exact shift and a1 * 2^s an exact
+// scaling followed by one rounding.  Value output (last mode): the sum
+// 2^16 (a0 + a1) is formed in 64-bit integers and scaled by 2^(eA + f_c - 30).
 __device__ __forceinline__ void fx_epilogue(const TcJob &J, uint32_t lane_base, uint32_t ACOLS, int64_t ro,
                                             int64_t n0, int warp, int lane) {
     const int eA = J.fxA->e;
@@ -337,34 +340,51 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, uint32_t lane_base, 
     }
     const int eC = eAact + g;
     if (J.cfix && warp == 2 && lane == 0) J.fxC->e = eC;
-    const int64_t lim = min(J.N - n0, (int64_t)J.BN);
+    const int lim = (int)min(J.N - n0, (int64_t)J.BN);
+    const bool unit = (J.colC.R0 == 0 && J.colC.s0 == 1);
+    const int64_t cs = J.colC.s0;
     unsigned mx = 0;
     for (int c0 = 0; c0 < J.BN; c0 += 16) {
         uint32_t r0[16], r1[16];
         tmem_ld16(lane_base + (uint32_t)c0, r0);
         tmem_ld16(lane_base + ACOLS + (uint32_t)c0, r1);
+        // row exponents of the 16 columns: one per lane, shared by shuffles
+        const int fl = (c0 + (lane & 15) < lim) ? J.fxF[n0 + c0 + (lane & 15)] : 0;
         tmem_ld_wait();
-        if (ro < 0) continue;
+        if (J.cfix) {
+            int32_t xv[16];
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            if (c0 + e >= lim) continue;
-            const int64_t c = n0 + c0 + e;
-            const long long I0 = __float2ll_rz(__uint_as_float(r0[e]));
-            const long long I1 = __float2ll_rn(__uint_as_float(r1[e]) * 65536.0f);
-            const long long Tq = I0 * 65536 + I1;
-            const int f = J.fxF[c];
-            const int64_t off = ro + imap(J.colC, c);
-            if (J.cfix) {
-                const int sh = eA + f + 1 - eC;
-                long long X;
-                if (sh >= 0) X = (sh < 40) ? (Tq << sh) : (Tq > 0 ? (1ll << 40) : (Tq < 0 ? -(1ll << 40) : 0));
-                else if (sh > -63) X = (Tq + (1ll << (-sh - 1))) >> (-sh);
-                else X = 0;
+            for (int e = 0; e < 16; ++e) {
+                const int f = __shfl_sync(0xffffffffu, fl, e);
+                const int sft = min(62, max(0, eA + f + 17 - eC));  // > 0, see above
+                const int a0 = __float2int_rz(__uint_as_float(r0[e]));
+                const int a1 = __float2int_rn(__uint_as_float(r1[e]) * __int_as_float((127 + sft) << 23));
+                long long X = ((long long)a0 << sft) + a1;
                 X = max(-2147483647ll, min(2147483647ll, X));
-                static_cast<int32_t *>(J.C)[off] = (int32_t)X;
+                xv[e] = (int32_t)X;
                 mx = max(mx, (unsigned)(X < 0 ? -X : X));
-            } else {
-                const double v = ldexp((double)Tq, eA + f - 30);
+            }
+            if (ro >= 0) {
+                int32_t *cp = static_cast<int32_t *>(J.C) + ro + (n0 + c0) * cs;
+                if (unit && c0 + 16 <= lim && (reinterpret_cast<uintptr_t>(cp) & 15) == 0) {
+#pragma unroll
+                    for (int e = 0; e < 16; e += 4)
+                        *reinterpret_cast<int4 *>(cp + e) = make_int4(xv[e], xv[e + 1], xv[e + 2], xv[e + 3]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e)
+                        if (c0 + e < lim) cp[e * cs] = xv[e];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int f = __shfl_sync(0xffffffffu, fl, e);
+                if (ro < 0 || c0 + e >= lim) continue;
+                const long long I0 = __float2ll_rz(__uint_as_float(r0[e]));
+                const long long I1 = __float2ll_rn(__uint_as_float(r1[e]) * 65536.0f);
+                const double v = ldexp((double)(I0 * 65536 + I1), eA + f - 30);
+                const int64_t off = ro + (n0 + c0 + e) * cs;
                 if (J.c64) {
                     double *d = static_cast<double *>(J.C) + off;
                     *d = J.acc ? *d + v : v;
@@ -661,7 +681,7 @@ static constexpr size_t kSmemMax = 227 * 1024;
 
 static void pick_config(int form, int bn_max, int nkb_max, int &stages, int &nacc, int &nbuf, int &acc_cols,
                         size_t &smem) {
-    acc_cols = bn_max <= 32 ? 32 : (bn_max <= 64 ? 64 : 128);
+    acc_cols = bn_max <= 32 ? 32 : (bn_max <= 64 ? 64 : (bn_max <= 128 ? 128 : 256));
     // two accumulator buffers (epilogue overlapped) when tensor memory
     // allows, then more accumulator sets per tile (accuracy)
     const int rg = 2;
