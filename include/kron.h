@@ -136,6 +136,26 @@ KRON_API kron_status kron_mump(int d, const int64_t *m, int mu, int64_t n, const
                       kron_dtype dtype, kron_prec prec, void *ws, size_t ws_bytes,
                       kron_stream_t stream);
 
+/*
+ * The same product as kron_mump for the split forms (3XTF32, BF16X3, BF16X6),
+ * for callers that cannot provide device memory: a host application whose
+ * own pool holds all of the device memory, or a latency-critical loop that
+ * must not call cudaMalloc (an allocation can synchronise the device).  The
+ * paper has no counterpart; this is a deployment variant of kron_mump.
+ * No workspace is passed and nothing is allocated: the scratch (the split
+ * image of op(L)) lives in a 1 MiB array compiled into the library, which
+ * every GPU that loads the library holds until the process exits.  Sizes whose
+ * image exceeds 1 MiB return KRON_ERR_WORKSPACE (n and m_mu up to 256 always
+ * fit).  The first call on a device looks up the array's device address, so
+ * make that first call outside any stream capture.  All calls on a device
+ * share the array: calls whose execution overlaps on the GPU (other streams,
+ * other host threads) race and give wrong results; calls ordered on one
+ * stream are safe.  Other precisions return KRON_ERR_UNSUPPORTED.
+ */
+KRON_API kron_status kron_mump_noalloc(int d, const int64_t *m, int mu, int64_t n, const void *T,
+                                       const void *L, int64_t ldL, int transL, void *S,
+                                       kron_dtype dtype, kron_prec prec, kron_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Tucker operator: Definition "Tucker operator", Eq. (tuckerop)             */
 /* ------------------------------------------------------------------------ */

@@ -59,6 +59,7 @@ _sig("kron_version", [], _ci)
 _sig("kron_get_device_error", [ctypes.POINTER(_ci), _ci])
 _sig("kron_mump_workspace_size", [_ci, _i64p, _ci, ctypes.c_int64, _ci, _ci, ctypes.POINTER(_sz)])
 _sig("kron_mump", [_ci, _i64p, _ci, ctypes.c_int64, _vp, _vp, ctypes.c_int64, _ci, _vp, _ci, _ci, _vp, _sz, _vp])
+_sig("kron_mump_noalloc", [_ci, _i64p, _ci, ctypes.c_int64, _vp, _vp, ctypes.c_int64, _ci, _vp, _ci, _ci, _vp])
 _sig("kron_plan_create", [ctypes.POINTER(_vp), _ci, _i64p, _i64p, _ci, _ci, ctypes.c_uint])
 _sig("kron_plan_destroy", [_vp])
 _sig("kron_plan_workspace_size", [_vp, ctypes.POINTER(_sz)])
@@ -81,7 +82,7 @@ _sig("kron_batched_run", [_vp, _vp, _sz, _vp])
 
 EXPORTS = [
     "kron_status_string", "kron_version", "kron_get_device_error", "kron_mump_workspace_size",
-    "kron_mump", "kron_plan_create", "kron_plan_destroy", "kron_plan_workspace_size",
+    "kron_mump", "kron_mump_noalloc", "kron_plan_create", "kron_plan_destroy", "kron_plan_workspace_size",
     "kron_plan_order", "kron_plan_flops", "kron_tucker", "kron_adjoint_workspace_size",
     "kron_tucker_adjoint", "kron_expm_workspace_size", "kron_expm",
     "kron_expkronsum_workspace_size", "kron_expkronsum_step", "kron_expkronsum_apply",
