@@ -235,10 +235,10 @@ __device__ __forceinline__ void raw_issue(const TcJob &J, const int64_t (&base)[
 
 // Float sources: raw tiles arrive through cp.async several K-blocks ahead;
 // the converters split them from shared memory.
-template <int F>
+template <int F, typename Join>
 __device__ __forceinline__ bool conv_tile_loop_raw(const TcJob &J, int mt, uint8_t *sA, uint32_t A_ST, uint8_t *sRaw,
                                                    uint64_t *full, uint64_t *empty, int S, uint32_t &g, int lane,
-                                                   int ct) {
+                                                   int ct, Join &&join) {
     using R = RawCfg<F>;
     constexpr int BK = R::BK;
     constexpr int CH = 16 / FT<F>::ELEM;
@@ -315,54 +315,117 @@ __device__ __forceinline__ bool conv_tile_loop_raw(const TcJob &J, int mt, uint8
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&full[s]));
+        // every stage holds this tile: the accumulators of the previous tile
+        // are complete, and its epilogue is what the MMA waits for
+        if (kb == S - 1 && !join()) {
+            cp_async_wait<0>();
+            return false;
+        }
     }
     cp_async_wait<0>();
     return true;
 }
 
-// Fixed-point form epilogue for one tile row.  The two accumulator regions
-// hold a0 (level 0, an exact integer below 2^24) and a1 (levels 1..3, small)
-// in units of 2^(eA + f_c - 14).  Fixed-point output with scale eC:
-//     X = a0 * 2^s + round(a1 * 2^s),  s = eA + f_c + 17 - eC,
-// where s >= 17 - log2(K) > 0 because the row-sum bound g makes eC at most
-// eA + f_c + log2(K): the level-0 part is an exact shift and a1 * 2^s an exact
-// scaling followed by one rounding.  Value output (last mode): the sum
-// 2^16 (a0 + a1) is formed in 64-bit integers and scaled by 2^(eA + f_c - 30).
-__device__ __forceinline__ void fx_epilogue(const TcJob &J, uint32_t lane_base, uint32_t ACOLS, int64_t ro,
-                                            int64_t n0, int warp, int lane) {
-    const int eA = J.fxA->e;
+// x * 2^e as a double for |x| < 2^53, from integer operations only (the
+// FP64 pipe is narrow); exponents outside the normal range take ldexp.
+__device__ __forceinline__ double i64_scaled(long long x, int e) {
+    if (x == 0) return 0.0;
+    const unsigned long long a = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
+    const int sh = __clzll((long long)a) - 11;  // leading one to bit 52
+    const int E = 1075 + e - sh;
+    if (sh < 0 || E <= 0 || E >= 2047) return ldexp((double)x, e);
+    const unsigned long long bits = ((unsigned long long)(x < 0) << 63) | ((unsigned long long)E << 52) |
+                                    ((a << sh) & ((1ull << 52) - 1));
+    return __longlong_as_double((long long)bits);
+}
+
+// round(v) as a 64-bit integer (ties away from zero) for |v| < 2^62, from
+// the bits of v.
+__device__ __forceinline__ long long f32_round_i64(float v) {
+    const uint32_t b = __float_as_uint(v);
+    const int E = (int)((b >> 23) & 0xFFu);
+    const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
+    const int sh = E - 150;  // v = m * 2^sh
+    unsigned long long r = 0;
+    if (E == 0) r = 0;
+    else if (sh >= 0) r = m << sh;
+    else if (sh > -26) r = (m + (1ull << (-sh - 1))) >> (-sh);
+    return (b >> 31) ? -(long long)r : (long long)r;
+}
+
+__device__ __forceinline__ int add_sat(int a, int b) {
+    int r;
+    asm("add.sat.s32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+
+// Scales of one fixed-point job, the same for all of its tiles: A's scale
+// eA and the output scale eC = eA_actual + g, where |A| < 2^eA_actual (from
+// A's largest magnitude) and every row sum of |op(L)| is below 2^g, so that
+// every output is below 2^31 in magnitude up to rounding (the conversion
+// saturates there).
+struct FxConsts {
+    int j = -1;
+    int eA = 0, eC = 0;
+};
+
+__device__ __forceinline__ void fx_consts(const TcJob &J, int j, FxConsts &k) {
+    if (k.j == j) return;
+    k.j = j;
+    k.eA = J.fxA->e;
     const unsigned mA = J.fxA->maxabs;
-    const int eAact = eA - 31 + (mA ? 32 - __clz((int)mA) : 0);
-    int g = 0;
-    {
-        const double rs = __longlong_as_double((long long)*J.fxG);
-        if (rs > 0.0) frexp(rs, &g);
-    }
-    const int eC = eAact + g;
-    if (J.cfix && warp == 2 && lane == 0) J.fxC->e = eC;
+    const int eAact = k.eA - 31 + (mA ? 32 - __clz((int)mA) : 0);
+    const unsigned long long gb = *J.fxG;  // bits of the largest row sum (non-negative)
+    const int g = gb ? (int)((gb >> 52) & 0x7FF) - 1022 : 0;
+    k.eC = eAact + g;
+}
+
+// Fixed-point form epilogue for one tile row.  The two accumulator regions
+// hold a0 (level 0, an exact integer below 2^24) and a1 (levels 1..3) in
+// units of 2^(eA + f_c - 14).  Fixed-point output with scale eC:
+//     X = round((a0 + a1) * 2^s),  s = eA + f_c + 17 - eC,
+// formed exactly as the float pair (h, l) = TwoSum(a0 * 2^s, a1 * 2^s) (both
+// products are exact power-of-two scalings; TwoSum is Knuth's error-free
+// sum), then X = rint(h) + rint(l), within one unit of the rounded sum and
+// saturated to +-(2^31 - 1).
+// Value output (last mode): the sum 2^16 (a0 + a1) is formed in 64-bit
+// integers and scaled by 2^(eA + f_c - 30).
+// The 16-column chunks of the tile are shared by `nparts` warps of the same
+// tensor-memory lane quarter; this one takes chunks part, part + nparts, ...
+__device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, uint32_t lane_base, uint32_t ACOLS,
+                                            int64_t ro, int64_t n0, int lane, int part, int nparts) {
+    const int eA = k.eA, eC = k.eC;
     const int lim = (int)min(J.N - n0, (int64_t)J.BN);
     const bool unit = (J.colC.R0 == 0 && J.colC.s0 == 1);
     const int64_t cs = J.colC.s0;
+    const int step = 16 * nparts;
+    const int base = eA + 17 - eC;
     unsigned mx = 0;
-    for (int c0 = 0; c0 < J.BN; c0 += 16) {
+    int c0 = 16 * part;
+    // row exponent of this lane's column of the chunk (prefetched one chunk ahead)
+    int fl = (c0 + (lane & 15) < lim) ? __ldg(J.fxF + n0 + c0 + (lane & 15)) : 0;
+    for (; c0 < J.BN; c0 += step) {
         uint32_t r0[16], r1[16];
         tmem_ld16(lane_base + (uint32_t)c0, r0);
         tmem_ld16(lane_base + ACOLS + (uint32_t)c0, r1);
-        // row exponents of the 16 columns: one per lane, shared by shuffles
-        const int fl = (c0 + (lane & 15) < lim) ? J.fxF[n0 + c0 + (lane & 15)] : 0;
+        const int cn = c0 + step;
+        const int fnext = (cn + (lane & 15) < lim) ? __ldg(J.fxF + n0 + cn + (lane & 15)) : 0;
+        // 2^s of this lane's column (s below -126 leaves only values that round to 0)
+        const float scl = __int_as_float((127 + min(100, max(-126, base + fl))) << 23);
         tmem_ld_wait();
         if (J.cfix) {
             int32_t xv[16];
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
-                const int f = __shfl_sync(0xffffffffu, fl, e);
-                const int sft = min(62, max(0, eA + f + 17 - eC));  // > 0, see above
-                const int a0 = __float2int_rz(__uint_as_float(r0[e]));
-                const int a1 = __float2int_rn(__uint_as_float(r1[e]) * __int_as_float((127 + sft) << 23));
-                long long X = ((long long)a0 << sft) + a1;
-                X = max(-2147483647ll, min(2147483647ll, X));
-                xv[e] = (int32_t)X;
-                mx = max(mx, (unsigned)(X < 0 ? -X : X));
+                const float sc = __shfl_sync(0xffffffffu, scl, e);
+                const float h = __uint_as_float(r0[e]) * sc;
+                const float l = __uint_as_float(r1[e]) * sc;
+                const float sum = h + l;
+                const float bl = sum - h;
+                const float err = (h - (sum - bl)) + (l - bl);
+                const int x = max(-2147483647, add_sat(__float2int_rn(sum), __float2int_rn(err)));
+                xv[e] = x;
+                mx = max(mx, (unsigned)abs(x));
             }
             if (ro >= 0) {
                 int32_t *cp = static_cast<int32_t *>(J.C) + ro + (n0 + c0) * cs;
@@ -377,29 +440,82 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, uint32_t lane_base, 
                 }
             }
         } else {
+            double v[16];
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
                 const int f = __shfl_sync(0xffffffffu, fl, e);
-                if (ro < 0 || c0 + e >= lim) continue;
-                const long long I0 = __float2ll_rz(__uint_as_float(r0[e]));
-                const long long I1 = __float2ll_rn(__uint_as_float(r1[e]) * 65536.0f);
-                const double v = ldexp((double)(I0 * 65536 + I1), eA + f - 30);
-                const int64_t off = ro + (n0 + c0 + e) * cs;
-                if (J.c64) {
-                    double *d = static_cast<double *>(J.C) + off;
-                    *d = J.acc ? *d + v : v;
+                const long long I0 = (long long)__float2int_rz(__uint_as_float(r0[e]));
+                const long long I1 = f32_round_i64(__uint_as_float(r1[e]) * 65536.0f);
+                v[e] = i64_scaled(I0 * 65536 + I1, eA + f - 30);
+            }
+            // the accumulate flag is tested outside the stores: no loads of C otherwise
+            if (ro < 0) {
+            } else if (J.c64) {
+                double *d = static_cast<double *>(J.C) + ro + (n0 + c0) * cs;
+                if (J.acc) {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e)
+                        if (c0 + e < lim) d[e * cs] += v[e];
                 } else {
-                    float *d = static_cast<float *>(J.C) + off;
-                    *d = J.acc ? (float)((double)*d + v) : (float)v;
+#pragma unroll
+                    for (int e = 0; e < 16; ++e)
+                        if (c0 + e < lim) d[e * cs] = v[e];
+                }
+            } else {
+                float *d = static_cast<float *>(J.C) + ro + (n0 + c0) * cs;
+                if (J.acc) {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e)
+                        if (c0 + e < lim) d[e * cs] = (float)((double)d[e * cs] + v[e]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e)
+                        if (c0 + e < lim) d[e * cs] = (float)v[e];
                 }
             }
         }
+        fl = fnext;
     }
     if (J.cfix) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (lane == 0 && mx) atomicMax(&J.fxC->maxabs, mx);
     }
+}
+
+// Epilogue share of one fixed-point tile (tile t, it-th tile of this CTA):
+// waits for its accumulators, drains this warp's column share, releases the
+// accumulators and publishes the tile.  `nbar` threads take part.
+__device__ __forceinline__ bool fx_epi_tile(const TcLaunch &L, int t, int it, uint32_t tmem, uint32_t ACOLS, int NBUF,
+                                            uint64_t *accf, uint64_t *acce, FxConsts &k, int q, int lane, bool lead,
+                                            int part, int nparts, int nbar) {
+    const int j = find_job(L, t);
+    const TcJob J = job_at(L, j);
+    const int lt = t - J.tile_begin;
+    const int nt = lt % J.tiles_n, mt = lt / J.tiles_n;
+    const int buf = it % NBUF;
+    const uint32_t use = (uint32_t)(it / NBUF);
+    int ok = (lane == 0) ? (int)mbar_wait(smem_u32(&accf[buf]), use & 1u) : 1;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) return false;
+    tc_fence_after();
+    const int64_t rg = (int64_t)mt * kBM + q * 32 + lane;
+    const int64_t ro = rg < J.M ? imap(J.rowC, rg) : -1;
+    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * Regions<kFX32>::N) * ACOLS;
+    fx_consts(J, j, k);
+    if (J.cfix && lead && lane == 0) J.fxC->e = k.eC;
+    fx_epilogue(J, k, lane_base, ACOLS, ro, (int64_t)nt * J.BN, lane, part, nparts);
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(smem_u32(&acce[buf]));
+    if (J.publish) {
+        named_bar(1, nbar);
+        if (lead && lane == 0) {
+            __threadfence();
+            atomicAdd(&L.done[j], 1);
+        }
+    }
+    return true;
 }
 
 template <int F>
@@ -424,6 +540,10 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const TcLaunch L) {
     uint32_t ncols = ACOLS * (uint32_t)RG * (uint32_t)NACC * (uint32_t)NBUF;
     ncols = ncols <= 32 ? 32u : (ncols <= 64 ? 64u : (ncols <= 128 ? 128u : (ncols <= 256 ? 256u : 512u)));
 
+    // one accumulator buffer (fixed point, 256-column tiles): the converter
+    // warps, idle while the MMA waits for the epilogue, take two thirds of it
+    const bool join = (F == kFX32) && NBUF == 1;
+    const int n_epi = kEpi + (join ? kConv : 0);
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(smem_u32(&full[s]), kConv + 1);
@@ -431,7 +551,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const TcLaunch L) {
         }
         for (int b = 0; b < NBUF; ++b) {
             mbar_init(smem_u32(&accf[b]), 1);
-            mbar_init(smem_u32(&acce[b]), kEpi);
+            mbar_init(smem_u32(&acce[b]), (uint32_t)n_epi);
         }
         fence_mbar_init();
     }
@@ -519,6 +639,13 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const TcLaunch L) {
         // ---------------------------------------------------------- epilogue
         const int q = warp & 3;                // TMEM lane quarter this warp may access
         int it = 0;
+        if constexpr (F == kFX32) {
+            FxConsts k;
+            for (int t = blockIdx.x; t < L.total_tiles; t += gridDim.x, ++it)
+                if (!fx_epi_tile(L, t, it, tmem, ACOLS, NBUF, accf, acce, k, q, lane, warp == 2, 0, join ? 3 : 1,
+                                 32 * n_epi))
+                    break;
+        } else
         for (int t = blockIdx.x; t < L.total_tiles; t += gridDim.x, ++it) {
             const int j = find_job(L, t);
             const TcJob J = job_at(L, j);
@@ -536,9 +663,6 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const TcLaunch L) {
             const int used = min(NACC, J.nkb);
             const uint32_t lane_base =
                 tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * NACC * RG) * ACOLS;
-            if constexpr (F == kFX32) {
-                fx_epilogue(J, lane_base, ACOLS, ro, n0, warp, lane);
-            } else
             for (int c0 = 0; c0 < J.BN; c0 += 32) {
                 // accumulator 0: hi + cross in FP32; further accumulators are
                 // added in order
@@ -587,11 +711,30 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const TcLaunch L) {
         // -------------------------------------------------------- converters
         const int ct = threadIdx.x - kConv0 * 32;
         uint32_t g = 0;
-        for (int t = blockIdx.x; t < L.total_tiles; t += gridDim.x) {
+        // epilogue share of the previous tile, still due (join mode)
+        int pend = -1, pend_it = 0;
+        const int part = 1 + (warp - kConv0) / 4;
+        FxConsts k;
+        auto epi_prev = [&]() -> bool {
+            if constexpr (F != kFX32) {
+                return true;
+            } else {
+                if (pend < 0) return true;
+                const int t = pend;
+                pend = -1;
+                return fx_epi_tile(L, t, pend_it, tmem, ACOLS, NBUF, accf, acce, k, warp & 3, lane, false, part, 3,
+                                   32 * n_epi);
+            }
+        };
+        int it = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < L.total_tiles && ok; t += gridDim.x, ++it) {
             const TcJob J = job_at(L, find_job(L, t));
             const int lt = t - J.tile_begin;
             const int mt = lt / J.tiles_n;
             if (J.dep >= 0) {
+                // the tile waited for may be the previous tile of this CTA
+                if (!epi_prev()) break;
                 // wait until every tile of the job this one reads is stored
                 if (ct == 0) {
                     volatile int *dn = L.done + J.dep;
@@ -607,15 +750,20 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const TcLaunch L) {
                 }
                 named_bar(2, 32 * kConv);
             }
-            bool ok;
             if constexpr (F == kFX32) {  // always 32-bit fixed point
-                ok = conv_tile_loop_raw<F>(J, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct);
+                ok = conv_tile_loop_raw<F>(J, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct, epi_prev) &&
+                     epi_prev();  // tiles of fewer than S K-blocks
+                if (join) {
+                    pend = t;
+                    pend_it = it;
+                }
             } else {
+                auto none = []() { return true; };
                 ok = J.a64 ? conv_tile_loop<F, double>(J, mt, sA, A_ST, full, empty, S, g, lane, ct)
-                           : conv_tile_loop_raw<F>(J, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct);
+                           : conv_tile_loop_raw<F>(J, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct, none);
             }
-            if (!ok) break;
         }
+        if (ok) epi_prev();
     }
     tc_fence_before();
     __syncthreads();

@@ -87,6 +87,20 @@ def test_tucker_matches_oracle(kron, m, n, prec):
     assert err <= tol(prec, sum(m)), (prec, m, n, err)
 
 
+def test_fx32_rows_far_below_the_largest_row_sum(kron):
+    """Rows of op(L_mu) whose magnitude is far below the largest row sum: in
+    the fixed-point chain their products are scaled down (a negative shift)
+    before rounding, and must keep their own scale (Eq. (tuckerop))."""
+    T = rnd(9, 10, 11)
+    Ls = [rnd(8, 9), rnd(7, 10), rnd(6, 11)]
+    for L in Ls:  # whichever mode runs last, the others produce fixed point
+        L[3, :] *= 2.0 ** -20
+        L[5, :] *= 2.0 ** -12
+    ref = oracle.tucker(T, Ls)
+    S = kron.tucker(to_dev(T), [to_dev(L) for L in Ls], prec="fx32")
+    assert rel_err(to_host(S), ref) <= TOL["fx32"]
+
+
 @pytest.mark.parametrize("prec", ["fp64", "3xtf32"])
 def test_tucker_transposed_plan(kron, prec):
     m, n = (7, 9, 5), (4, 10, 6)
