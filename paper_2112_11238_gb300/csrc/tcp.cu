@@ -18,6 +18,9 @@
 // Stages are guarded by full/empty mbarriers, accumulators by acc_full /
 // acc_empty mbarriers; with two accumulator buffers the epilogue of tile i
 // overlaps the main loop of tile i+1.  Every wait is bounded.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -36,6 +39,11 @@ constexpr int kItems = kBM * kChunks / (32 * kConv);  // (row, chunk) items per 
 constexpr int kMaxInline = 8;
 
 struct TcJob {
+    // raw A tiles by TMA (tma != 0): 2 = k-contiguous rows, box (BK, 128);
+    // 3 = [slab][k][row] with tmaP rows per slab, box (128, BK, 1)
+    CUtensorMap tmA;
+    int64_t tmaP;
+    int32_t tma;
     const void *A;
     IdxMap rowA, kA;
     int64_t M;
@@ -70,8 +78,8 @@ struct RawCfg {
 };
 
 struct TcLaunch {
+    TcJob inl[kMaxInline];  // small tables travel with the launch (tensor maps included)
     const TcJob *jobs;      // device table (when njobs > kMaxInline)
-    TcJob inl[kMaxInline];  // small tables travel with the launch
     int njobs, total_tiles;
     int *done;              // finished tiles per job (zeroed before the launch)
     int stages, nacc, nbuf, acc_cols, bn_max;
@@ -236,13 +244,15 @@ __device__ __forceinline__ void raw_issue(const TcJob &J, const int64_t (&base)[
 // Float sources: raw tiles arrive through cp.async several K-blocks ahead;
 // the converters split them from shared memory.
 template <int F, typename Join>
-__device__ __forceinline__ bool conv_tile_loop_raw(const TcJob &J, int mt, uint8_t *sA, uint32_t A_ST, uint8_t *sRaw,
+__device__ __forceinline__ bool conv_tile_loop_raw(const TcJob &J, const CUtensorMap *tm, uint64_t *rfull,
+                                                   uint32_t &rc, int mt, uint8_t *sA, uint32_t A_ST, uint8_t *sRaw,
                                                    uint64_t *full, uint64_t *empty, int S, uint32_t &g, int lane,
                                                    int ct, Join &&join) {
     using R = RawCfg<F>;
     constexpr int BK = R::BK;
     constexpr int CH = 16 / FT<F>::ELEM;
     const bool kc = J.akc != 0;
+    const bool tma = J.tma != 0;
     // per-unit source offsets (rows fixed over the tile)
     const int64_t row0 = (int64_t)mt * kBM;
     int64_t base[R::UNITS];
@@ -258,20 +268,45 @@ __device__ __forceinline__ bool conv_tile_loop_raw(const TcJob &J, int mt, uint8
     }
     named_bar(2, 32 * kConv);  // the raw ring is free (previous tile consumed)
     const uint32_t raw0 = smem_u32(sRaw);
+    // TMA: one thread loads K-block kbi of the tile into ring slot (rc + kbi)
+    auto tma_issue = [&](int kbi) {
+        const uint32_t slot = (rc + (uint32_t)kbi) % R::STAGES;
+        const uint32_t bar = smem_u32(&rfull[slot]);
+        mbar_arrive_expect_tx(bar, R::BYTES);
+        const int k0 = (J.kb0 + kbi) * BK;
+        if (J.tma == 2) {
+            tma_load_2d(raw0 + slot * R::BYTES, tm, k0, (int)row0, bar);
+        } else {
+            tma_load_3d(raw0 + slot * R::BYTES, tm, (int)(row0 % J.tmaP), k0, (int)(row0 / J.tmaP), bar);
+        }
+    };
+    if (tma) {
+        if (ct == 0)
+            for (int j = 0; j < R::STAGES - 1 && j < J.nkb; ++j) tma_issue(j);
+    } else {
 #pragma unroll
-    for (int j = 0; j < R::STAGES - 1; ++j) {
-        if (j < J.nkb) raw_issue<F>(J, base, nrow, row0, (int64_t)(J.kb0 + j) * BK, raw0 + j * R::BYTES, ct);
-        cp_async_commit();
+        for (int j = 0; j < R::STAGES - 1; ++j) {
+            if (j < J.nkb) raw_issue<F>(J, base, nrow, row0, (int64_t)(J.kb0 + j) * BK, raw0 + j * R::BYTES, ct);
+            cp_async_commit();
+        }
     }
     // conversion items of this thread
     int irow[kItems], ich[kItems];
 #pragma unroll
     for (int i = 0; i < kItems; ++i) item_rc(i, ct, kc, irow[i], ich[i]);
     for (int kb = 0; kb < J.nkb; ++kb, ++g) {
-        cp_async_wait<R::STAGES - 2>();
-        named_bar(2, 32 * kConv);
-        const int rs = kb % R::STAGES;
-        {
+        int rs;
+        if (tma) {
+            named_bar(2, 32 * kConv);  // every converter is done with K-block kb - 1
+            const int kn = kb + R::STAGES - 1;
+            if (ct == 0 && kn < J.nkb) tma_issue(kn);
+            const uint32_t u = rc + (uint32_t)kb;
+            rs = (int)(u % R::STAGES);
+            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&rfull[rs]), (u / R::STAGES) & 1u))) return false;
+        } else {
+            cp_async_wait<R::STAGES - 2>();
+            named_bar(2, 32 * kConv);
+            rs = kb % R::STAGES;
             const int kn = kb + R::STAGES - 1;
             if (kn < J.nkb)
                 raw_issue<F>(J, base, nrow, row0, (int64_t)(J.kb0 + kn) * BK, raw0 + (kn % R::STAGES) * R::BYTES, ct);
@@ -323,6 +358,7 @@ __device__ __forceinline__ bool conv_tile_loop_raw(const TcJob &J, int mt, uint8
         }
     }
     cp_async_wait<0>();
+    if (tma) rc += (uint32_t)J.nkb;
     return true;
 }
 
@@ -519,7 +555,7 @@ __device__ __forceinline__ bool fx_epi_tile(const TcLaunch &L, int t, int it, ui
 }
 
 template <int F>
-__global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const TcLaunch L) {
+__global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant__ TcLaunch L) {
     using T = FT<F>;
     constexpr int BK = kRowBytes / T::ELEM;
     constexpr uint32_t PIECE_A = kBM * kRowBytes;
@@ -535,7 +571,8 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const TcLaunch L) {
     uint8_t *sRaw = sB + (size_t)S * B_ST;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sRaw + (size_t)RawCfg<F>::STAGES * RawCfg<F>::BYTES);
     uint64_t *full = bars, *empty = bars + S, *accf = bars + 2 * S, *acce = bars + 2 * S + NBUF;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * S + 2 * NBUF);
+    uint64_t *rfull = bars + 2 * S + 2 * NBUF;  // raw A ring (TMA)
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(rfull + RawCfg<F>::STAGES);
     constexpr int RG = Regions<F>::N;
     uint32_t ncols = ACOLS * (uint32_t)RG * (uint32_t)NACC * (uint32_t)NBUF;
     ncols = ncols <= 32 ? 32u : (ncols <= 64 ? 64u : (ncols <= 128 ? 128u : (ncols <= 256 ? 256u : 512u)));
@@ -553,6 +590,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const TcLaunch L) {
             mbar_init(smem_u32(&accf[b]), 1);
             mbar_init(smem_u32(&acce[b]), (uint32_t)n_epi);
         }
+        for (int r = 0; r < RawCfg<F>::STAGES; ++r) mbar_init(smem_u32(&rfull[r]), 1);
         fence_mbar_init();
     }
     if (warp == 1) {
@@ -710,7 +748,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const TcLaunch L) {
     } else {
         // -------------------------------------------------------- converters
         const int ct = threadIdx.x - kConv0 * 32;
-        uint32_t g = 0;
+        uint32_t g = 0, rc = 0;
         // epilogue share of the previous tile, still due (join mode)
         int pend = -1, pend_it = 0;
         const int part = 1 + (warp - kConv0) / 4;
@@ -729,7 +767,9 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const TcLaunch L) {
         int it = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < L.total_tiles && ok; t += gridDim.x, ++it) {
-            const TcJob J = job_at(L, find_job(L, t));
+            const int jt = find_job(L, t);
+            const TcJob J = job_at(L, jt);
+            const CUtensorMap *tm = &job_at(L, jt).tmA;  // launch parameter space
             const int lt = t - J.tile_begin;
             const int mt = lt / J.tiles_n;
             if (J.dep >= 0) {
@@ -751,7 +791,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const TcLaunch L) {
                 named_bar(2, 32 * kConv);
             }
             if constexpr (F == kFX32) {  // always 32-bit fixed point
-                ok = conv_tile_loop_raw<F>(J, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct, epi_prev) &&
+                ok = conv_tile_loop_raw<F>(J, tm, rfull, rc, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct, epi_prev) &&
                      epi_prev();  // tiles of fewer than S K-blocks
                 if (join) {
                     pend = t;
@@ -760,7 +800,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const TcLaunch L) {
             } else {
                 auto none = []() { return true; };
                 ok = J.a64 ? conv_tile_loop<F, double>(J, mt, sA, A_ST, full, empty, S, g, lane, ct)
-                           : conv_tile_loop_raw<F>(J, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct, none);
+                           : conv_tile_loop_raw<F>(J, tm, rfull, rc, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct, none);
             }
         }
         if (ok) epi_prev();
@@ -825,6 +865,66 @@ static TcJob make_job(int form, const Contraction &c, const void *img) {
     return J;
 }
 
+// cuTensorMapEncodeTiled from the driver (no link-time dependency on it).
+static PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// Raw A tiles by TMA where the layout allows it (4-byte source): either rows
+// with contiguous k (one row stride), or slabs of tmaP contiguous rows (a
+// multiple of the 128-row tile, so no tile straddles two slabs) with k at a
+// fixed stride.  Strides must be multiples of 16 bytes.  Otherwise the
+// converters copy the tiles themselves (cp.async).
+static void setup_tma(int form, TcJob &J, const Contraction &c) {
+    J.tma = 0;
+    if (c.A_f64 || (reinterpret_cast<uintptr_t>(c.A) % 16) != 0 || c.M < 1 || c.K < 1) return;
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
+    if (!fn) return;
+    const cuuint32_t bk = (cuuint32_t)(form == kTF32x3 ? kRowBytes / 4 : kRowBytes / 2);
+    const cuuint32_t estr[3] = {1, 1, 1};
+    void *base = const_cast<void *>(c.A);
+    if (J.akc) {
+        if (!(c.kA.R0 == 0 && c.kA.s0 == 1 && c.rowA.R0 == 0 && c.rowA.s0 >= c.K && c.rowA.s0 % 4 == 0)) return;
+        const cuuint64_t dims[2] = {(cuuint64_t)c.K, (cuuint64_t)c.M};
+        const cuuint64_t strides[1] = {(cuuint64_t)c.rowA.s0 * 4};
+        const cuuint32_t box[2] = {bk, (cuuint32_t)kBM};
+        if (fn(&J.tmA, CU_TENSOR_MAP_DATA_TYPE_INT32, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return;
+        J.tma = 2;
+        return;
+    }
+    if (!(c.rowA.s0 == 1 && c.kA.R0 == 0 && c.kA.s0 % 4 == 0)) return;
+    int64_t P = c.M, Q = 1, sq = c.kA.s0 * c.K;
+    if (c.rowA.R0 != 0 && c.rowA.R0 < c.M) {
+        P = c.rowA.R0;
+        Q = (c.M + P - 1) / P;
+        sq = c.rowA.s1;
+        if (P % kBM != 0 || c.M % P != 0 || sq % 4 != 0) return;  // whole slabs only
+    }
+    if (c.kA.s0 < P) return;
+    const cuuint64_t dims[3] = {(cuuint64_t)P, (cuuint64_t)c.K, (cuuint64_t)Q};
+    const cuuint64_t strides[2] = {(cuuint64_t)c.kA.s0 * 4, (cuuint64_t)sq * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)kBM, bk, 1};
+    if (fn(&J.tmA, CU_TENSOR_MAP_DATA_TYPE_INT32, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return;
+    J.tmaP = P;
+    J.tma = 3;
+}
+
 static constexpr size_t kSmemMax = 227 * 1024;
 
 static void pick_config(int form, int bn_max, int nkb_max, int &stages, int &nacc, int &nbuf, int &acc_cols,
@@ -840,7 +940,7 @@ static void pick_config(int form, int bn_max, int nkb_max, int &stages, int &nac
     if (nkb_max < 2 || form == kFX32) nacc = 1;
     const size_t a_st = (size_t)pieces_of_f(form) * kBM * kRowBytes;
     const size_t b_st = (size_t)pieces_of_f(form) * bn_max * kRowBytes;
-    const size_t extra = 1024 + (size_t)(2 * 8 + 2 * 4 + 2) * 8;
+    const size_t extra = 1024 + (size_t)(2 * 8 + 2 * 4 + 4 + 2) * 8;
     size_t raw = 0;
     switch (form) {
         case kTF32x3: raw = (size_t)RawCfg<kTF32x3>::STAGES * RawCfg<kTF32x3>::BYTES; break;
@@ -922,6 +1022,7 @@ cudaError_t tcp_contract_fx(const Contraction &c, const void *img, const FxScale
     J.cfix = fxC != nullptr;
     J.a64 = 0;
     J.tile_begin = 0;
+    setup_tma(kFX32, J, c);
     const int tiles = J.tiles_m * J.tiles_n;
     return tcp_launch(kFX32, &J, 1, tiles, J.BN, J.nkb, nullptr, nullptr, st);
 }
@@ -931,6 +1032,7 @@ cudaError_t tcp_contract(int form, const Contraction &c, const void *img, cudaSt
     if (c.M == 0 || c.N == 0) return cudaSuccess;
     TcJob J = make_job(form, c, img);
     J.tile_begin = 0;
+    if (!c.A_f64) setup_tma(form, J, c);
     const int tiles = J.tiles_m * J.tiles_n;
     return tcp_launch(form, &J, 1, tiles, J.BN, J.nkb, nullptr, nullptr, st);
 }
