@@ -42,8 +42,12 @@ struct TcJob {
     // raw A tiles by TMA (tma != 0): 2 = k-contiguous rows, box (BK, 128);
     // 3 = [slab][k][row] with tmaP rows per slab, box (128, BK, 1)
     CUtensorMap tmA;
-    int64_t tmaP;
-    int32_t tma;
+    // fixed-point epilogue output by TMA stores of 32-row x 16-column boxes
+    // staged in shared memory (tmc != 0): 2 = column-contiguous rows, box
+    // (16, 32); 3 = [slab][column][row] with tmcP rows per slab, box (32, 16, 1)
+    CUtensorMap tmC;
+    int64_t tmaP, tmcP;
+    int32_t tma, tmc;
     const void *A;
     IdxMap rowA, kA;
     int64_t M;
@@ -283,11 +287,18 @@ __device__ __forceinline__ bool conv_tile_loop_raw(const TcJob &J, const CUtenso
     if (tma) {
         if (ct == 0)
             for (int j = 0; j < R::STAGES - 1 && j < J.nkb; ++j) tma_issue(j);
+        // the MMA of this tile waits for the epilogue of the previous one:
+        // take part in it first (the raw loads above run meanwhile)
+        if (!join()) return false;
     } else {
 #pragma unroll
         for (int j = 0; j < R::STAGES - 1; ++j) {
             if (j < J.nkb) raw_issue<F>(J, base, nrow, row0, (int64_t)(J.kb0 + j) * BK, raw0 + j * R::BYTES, ct);
             cp_async_commit();
+        }
+        if (!join()) {
+            cp_async_wait<0>();
+            return false;
         }
     }
     // conversion items of this thread
@@ -350,12 +361,6 @@ __device__ __forceinline__ bool conv_tile_loop_raw(const TcJob &J, const CUtenso
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&full[s]));
-        // every stage holds this tile: the accumulators of the previous tile
-        // are complete, and its epilogue is what the MMA waits for
-        if (kb == S - 1 && !join()) {
-            cp_async_wait<0>();
-            return false;
-        }
     }
     cp_async_wait<0>();
     if (tma) rc += (uint32_t)J.nkb;
@@ -428,8 +433,11 @@ __device__ __forceinline__ void fx_consts(const TcJob &J, int j, FxConsts &k) {
 // integers and scaled by 2^(eA + f_c - 30).
 // The 16-column chunks of the tile are shared by `nparts` warps of the same
 // tensor-memory lane quarter; this one takes chunks part, part + nparts, ...
+// stg: this warp's 4 KB of staging shared memory for TMA stores of C
+// through tmC (null: plain stores); rw0 is the warp's first tile row.
 __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, uint32_t lane_base, uint32_t ACOLS,
-                                            int64_t ro, int64_t n0, int lane, int part, int nparts) {
+                                            int64_t ro, int64_t n0, int lane, int part, int nparts, uint8_t *stg,
+                                            const CUtensorMap *tmC, int64_t rw0) {
     const int eA = k.eA, eC = k.eC;
     const int lim = (int)min(J.N - n0, (int64_t)J.BN);
     const bool unit = (J.colC.R0 == 0 && J.colC.s0 == 1);
@@ -437,6 +445,25 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, u
     const int step = 16 * nparts;
     const int base = eA + 17 - eC;
     unsigned mx = 0;
+    int cnt = 0;  // TMA stores issued by this warp
+    // one 16-column box: wait until its buffer is free, then write it (fill
+    // writes this lane's row), hand it to the TMA unit
+    auto stage = [&](int nb, uint8_t *buf, int64_t col, auto &&fill) {
+        if (lane == 0 && cnt >= nb) {
+            if (nb == 2) bulk_wait_read<1>();
+            else bulk_wait_read<0>();
+        }
+        __syncwarp();
+        fill(buf);
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0 && rw0 < J.M) {  // boxes wholly past the last row are not stored
+            if (J.tmc == 3) tma_store_3d(tmC, smem_u32(buf), (int)(rw0 % J.tmcP), (int)col, (int)(rw0 / J.tmcP));
+            else tma_store_2d(tmC, smem_u32(buf), (int)col, (int)rw0);
+            bulk_commit();
+        }
+        ++cnt;
+    };
     int c0 = 16 * part;
     // row exponent of this lane's column of the chunk (prefetched one chunk ahead)
     int fl = (c0 + (lane & 15) < lim) ? __ldg(J.fxF + n0 + c0 + (lane & 15)) : 0;
@@ -463,7 +490,19 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, u
                 xv[e] = x;
                 mx = max(mx, (unsigned)abs(x));
             }
-            if (ro >= 0) {
+            if (stg) {
+                // two 2 KB buffers; [column][row] or [row][column]
+                stage(2, stg + (cnt & 1) * 2048, n0 + c0, [&](uint8_t *buf) {
+                    if (J.tmc == 3) {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) reinterpret_cast<int32_t *>(buf)[e * 32 + lane] = xv[e];
+                    } else {
+                        int4 *d = reinterpret_cast<int4 *>(buf + lane * 64);
+#pragma unroll
+                        for (int e = 0; e < 16; e += 4) d[e / 4] = make_int4(xv[e], xv[e + 1], xv[e + 2], xv[e + 3]);
+                    }
+                });
+            } else if (ro >= 0) {
                 int32_t *cp = static_cast<int32_t *>(J.C) + ro + (n0 + c0) * cs;
                 if (unit && c0 + 16 <= lim && (reinterpret_cast<uintptr_t>(cp) & 15) == 0) {
 #pragma unroll
@@ -485,7 +524,19 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, u
                 v[e] = i64_scaled(I0 * 65536 + I1, eA + f - 30);
             }
             // the accumulate flag is tested outside the stores: no loads of C otherwise
-            if (ro < 0) {
+            if (stg) {
+                // one 4 KB buffer of doubles (value output is FP64 when staged)
+                stage(1, stg, n0 + c0, [&](uint8_t *buf) {
+                    if (J.tmc == 3) {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) reinterpret_cast<double *>(buf)[e * 32 + lane] = v[e];
+                    } else {
+                        double2 *d = reinterpret_cast<double2 *>(buf + lane * 128);
+#pragma unroll
+                        for (int e = 0; e < 16; e += 2) d[e / 2] = make_double2(v[e], v[e + 1]);
+                    }
+                });
+            } else if (ro < 0) {
             } else if (J.c64) {
                 double *d = static_cast<double *>(J.C) + ro + (n0 + c0) * cs;
                 if (J.acc) {
@@ -512,6 +563,13 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, u
         }
         fl = fnext;
     }
+    if (stg && lane == 0) {
+        // the staging memory is handed back, and a tile read later in the
+        // same launch must see the stores
+        if (J.publish) bulk_wait<0>();
+        else bulk_wait_read<0>();
+    }
+    __syncwarp();
     if (J.cfix) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -522,9 +580,10 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, u
 // Epilogue share of one fixed-point tile (tile t, it-th tile of this CTA):
 // waits for its accumulators, drains this warp's column share, releases the
 // accumulators and publishes the tile.  `nbar` threads take part.
+// stg: the warp's staging memory (used when the job stores C by TMA).
 __device__ __forceinline__ bool fx_epi_tile(const TcLaunch &L, int t, int it, uint32_t tmem, uint32_t ACOLS, int NBUF,
                                             uint64_t *accf, uint64_t *acce, FxConsts &k, int q, int lane, bool lead,
-                                            int part, int nparts, int nbar) {
+                                            int part, int nparts, int nbar, uint8_t *stg) {
     const int j = find_job(L, t);
     const TcJob J = job_at(L, j);
     const int lt = t - J.tile_begin;
@@ -540,7 +599,9 @@ __device__ __forceinline__ bool fx_epi_tile(const TcLaunch &L, int t, int it, ui
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * Regions<kFX32>::N) * ACOLS;
     fx_consts(J, j, k);
     if (J.cfix && lead && lane == 0) J.fxC->e = k.eC;
-    fx_epilogue(J, k, lane_base, ACOLS, ro, (int64_t)nt * J.BN, lane, part, nparts);
+    const bool staged = stg != nullptr && J.tmc != 0;
+    fx_epilogue(J, k, lane_base, ACOLS, ro, (int64_t)nt * J.BN, lane, part, nparts, staged ? stg : nullptr,
+                &job_at(L, j).tmC, (int64_t)mt * kBM + q * 32);
     tc_fence_before();
     __syncwarp();
     if (lane == 0) mbar_arrive(smem_u32(&acce[buf]));
@@ -581,6 +642,10 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
     // warps, idle while the MMA waits for the epilogue, take two thirds of it
     const bool join = (F == kFX32) && NBUF == 1;
     const int n_epi = kEpi + (join ? kConv : 0);
+    // in that mode every A stage is free during the epilogue (the converters
+    // fill them only after it): 4 KB of staging per epilogue warp
+    uint8_t *stg = (join && (uint32_t)S * A_ST >= 4096u * (kEpi + kConv) && warp >= 2)
+                       ? sA + (size_t)(warp - 2) * 4096 : nullptr;
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(smem_u32(&full[s]), kConv + 1);
@@ -681,7 +746,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
             FxConsts k;
             for (int t = blockIdx.x; t < L.total_tiles; t += gridDim.x, ++it)
                 if (!fx_epi_tile(L, t, it, tmem, ACOLS, NBUF, accf, acce, k, q, lane, warp == 2, 0, join ? 3 : 1,
-                                 32 * n_epi))
+                                 32 * n_epi, stg))
                     break;
         } else
         for (int t = blockIdx.x; t < L.total_tiles; t += gridDim.x, ++it) {
@@ -760,8 +825,14 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
                 if (pend < 0) return true;
                 const int t = pend;
                 pend = -1;
-                return fx_epi_tile(L, t, pend_it, tmem, ACOLS, NBUF, accf, acce, k, warp & 3, lane, false, part, 3,
-                                   32 * n_epi);
+                if (!fx_epi_tile(L, t, pend_it, tmem, ACOLS, NBUF, accf, acce, k, warp & 3, lane, false, part, 3,
+                                 32 * n_epi, stg))
+                    return false;
+                // the A stages double as staging memory: wait until every
+                // warp of the epilogue is done with it
+                int ok = (lane == 0) ? (int)mbar_wait(smem_u32(&acce[pend_it % NBUF]), (uint32_t)(pend_it / NBUF) & 1u)
+                                     : 1;
+                return __shfl_sync(0xffffffffu, ok, 0) != 0;
             }
         };
         int it = 0;
@@ -791,8 +862,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
                 named_bar(2, 32 * kConv);
             }
             if constexpr (F == kFX32) {  // always 32-bit fixed point
-                ok = conv_tile_loop_raw<F>(J, tm, rfull, rc, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct, epi_prev) &&
-                     epi_prev();  // tiles of fewer than S K-blocks
+                ok = conv_tile_loop_raw<F>(J, tm, rfull, rc, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct, epi_prev);
                 if (join) {
                     pend = t;
                     pend_it = it;
@@ -925,6 +995,54 @@ static void setup_tma(int form, TcJob &J, const Contraction &c) {
     J.tma = 3;
 }
 
+// TMA stores of the fixed-point epilogue output (not for accumulating jobs):
+// rows contiguous within slabs of tmcP rows (a multiple of the 32 rows one
+// warp stores, whole slabs), or columns contiguous with one row stride.
+static void setup_tmc(TcJob &J, const Contraction &c) {
+    J.tmc = 0;
+    if (c.accumulate || (reinterpret_cast<uintptr_t>(c.C) % 16) != 0 || c.M < 1 || c.N < 1) return;
+    if (!J.cfix && !c.C_f64) return;  // staged value output is FP64
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
+    if (!fn) return;
+    const int64_t es = J.cfix ? 4 : 8;
+    const CUtensorMapDataType dt = J.cfix ? CU_TENSOR_MAP_DATA_TYPE_INT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    const cuuint32_t estr[3] = {1, 1, 1};
+    void *base = c.C;
+    if (c.rowC.s0 == 1 && c.colC.R0 == 0) {
+        const int64_t cs = c.colC.s0;
+        int64_t P = c.M, Q = 1, sq = cs * c.N;
+        if (c.rowC.R0 != 0 && c.rowC.R0 < c.M) {
+            P = c.rowC.R0;
+            Q = c.M / P;
+            sq = c.rowC.s1;
+            if (P % 32 != 0 || c.M % P != 0) return;
+        }
+        if (cs < P || (cs * es) % 16 != 0 || (sq * es) % 16 != 0) return;
+        const cuuint64_t dims[3] = {(cuuint64_t)P, (cuuint64_t)c.N, (cuuint64_t)Q};
+        const cuuint64_t strides[2] = {(cuuint64_t)(cs * es), (cuuint64_t)(sq * es)};
+        const cuuint32_t box[3] = {32, 16, 1};
+        if (fn(&J.tmC, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return;
+        J.tmcP = P;
+        J.tmc = 3;
+        return;
+    }
+    if (c.colC.R0 == 0 && c.colC.s0 == 1 && c.rowC.R0 == 0) {
+        const int64_t rs = c.rowC.s0;
+        if (rs < c.N || (rs * es) % 16 != 0) return;
+        const cuuint64_t dims[2] = {(cuuint64_t)c.N, (cuuint64_t)c.M};
+        const cuuint64_t strides[1] = {(cuuint64_t)(rs * es)};
+        const cuuint32_t box[2] = {16, 32};
+        if (fn(&J.tmC, dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return;
+        J.tmc = 2;
+    }
+}
+
 static constexpr size_t kSmemMax = 227 * 1024;
 
 static void pick_config(int form, int bn_max, int nkb_max, int &stages, int &nacc, int &nbuf, int &acc_cols,
@@ -1023,6 +1141,7 @@ cudaError_t tcp_contract_fx(const Contraction &c, const void *img, const FxScale
     J.a64 = 0;
     J.tile_begin = 0;
     setup_tma(kFX32, J, c);
+    setup_tmc(J, c);
     const int tiles = J.tiles_m * J.tiles_n;
     return tcp_launch(kFX32, &J, 1, tiles, J.BN, J.nkb, nullptr, nullptr, st);
 }
