@@ -648,7 +648,7 @@ kron_status kron_expm(int64_t n, const double *A, int64_t ldA, double tau, doubl
 // Workspace: [expm ws][E_0..E_{d-1} (FP64)][images x d][state0][state1]
 namespace {
 struct StepLayout {
-    size_t expm, E[KRON_MAX_D], img[KRON_MAX_D], st[2], stbytes, total;
+    size_t expm, expm_each, E[KRON_MAX_D], img[KRON_MAX_D], st[2], stbytes, total;
     size_t fxf[KRON_MAX_D], fxg[KRON_MAX_D], fxsc;  // fixed-point form
 };
 
@@ -657,8 +657,9 @@ StepLayout step_layout(const kron_plan_s *pl) {
     size_t off = 0;
     int64_t nmax = 1;
     for (int k = 0; k < pl->d; ++k) nmax = std::max(nmax, pl->n[k]);
-    s.expm = off;
-    off += align_up(expm_workspace_bytes(nmax));
+    s.expm = off;  // one expm workspace per mode: the exponentials run in one launch
+    s.expm_each = align_up(expm_workspace_bytes(nmax));
+    off += (size_t)pl->d * s.expm_each;
     for (int k = 0; k < pl->d; ++k) {
         s.E[k] = off;
         off += align_up((size_t)pl->n[k] * pl->n[k] * 8);
@@ -833,6 +834,12 @@ kron_status kron_expkronsum_step(kron_plan plan, const double *const *A, const i
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     const double *Ep[KRON_MAX_D];
     int64_t ldE[KRON_MAX_D];
+    // the distinct A_mu, all exponentials in one launch
+    int cnt = 0;
+    int64_t bn[KRON_MAX_D], bld[KRON_MAX_D];
+    const double *bA[KRON_MAX_D];
+    double *bE[KRON_MAX_D];
+    void *bws[KRON_MAX_D];
     for (int k = 0; k < plan->d; ++k) {
         int same = -1;
         for (int j = 0; j < k; ++j)
@@ -843,9 +850,15 @@ kron_status kron_expkronsum_step(kron_plan plan, const double *const *A, const i
             continue;
         }
         double *Ek = reinterpret_cast<double *>(w + lay.E[k]);
-        if (expm_pade13(plan->n[k], A[k], ldA[k], tau, Ek, w + lay.expm, cs) != cudaSuccess) return KRON_ERR_CUDA;
+        bn[cnt] = plan->n[k];
+        bA[cnt] = A[k];
+        bld[cnt] = ldA[k];
+        bE[cnt] = Ek;
+        bws[cnt] = w + lay.expm + (size_t)cnt * lay.expm_each;
+        ++cnt;
         Ep[k] = Ek;
     }
+    if (expm_pade13_batch(cnt, bn, bA, bld, tau, bE, bws, cs) != cudaSuccess) return KRON_ERR_CUDA;
     return run_steps(plan, Ep, ldE, nsteps, U, w, lay, cs);
 }
 

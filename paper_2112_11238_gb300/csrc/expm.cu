@@ -13,13 +13,18 @@
 // iterative refinement with the FP64 residual R = (V+U) - (V-U) X:
 // X <- X + (V-U)^{-1} R.
 //
-// Everything runs in ONE cooperative launch (one block per SM) whose phases
-// are separated by a grid barrier with a bounded wait; FP64 GEMMs are split
-// into 16 x 16 tiles spread over the blocks.
+// Several exponentials (one per mode) run in ONE cooperative launch (one
+// block per SM): the blocks are split into one group per matrix, and each
+// group's phases are separated by its own barrier with a bounded wait.  FP64
+// GEMMs are split into 16 x 16 tiles spread over the group.  The elimination
+// goes by panels of kNB columns: every block of the group factors the panel
+// in shared memory (the same pivots everywhere), then updates the columns it
+// owns, one warp per column -- one barrier per panel instead of per column.
 #include <cooperative_groups.h>
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "internal.h"
 #include "ptx.cuh"
@@ -30,21 +35,29 @@ namespace {
 
 constexpr int kT = 16;          // GEMM tile
 constexpr int kThreadsE = 256;  // = kT * kT
+constexpr int kNB = 16;         // Gauss-Jordan panel width
+constexpr int kWarpsE = kThreadsE / 32;
 
-struct ExpmDev {
+struct ExpmProb {
     int n;
     const double *A;
     int64_t ldA;
-    double tau;
     double *E;
     double *w;           // workspace base (doubles)
     unsigned *bar;       // [0] count, [1] generation
     unsigned long long *norm_bits;
+};
+
+struct ExpmDev {
+    int count;
+    ExpmProb p[KRON_MAX_D];
+    double tau;
     double b[14];
     double theta;
 };
 
-__device__ bool grid_sync(unsigned *bar) {
+// Barrier of the gs blocks of one group (bounded wait).
+__device__ bool grid_sync(unsigned *bar, int gs) {
     __syncthreads();
     __shared__ int failed;
     if (threadIdx.x == 0) {
@@ -53,7 +66,7 @@ __device__ bool grid_sync(unsigned *bar) {
         const unsigned my_gen = *vgen;
         __threadfence();
         const unsigned arrived = atomicAdd(bar, 1u);
-        if (arrived == gridDim.x - 1) {
+        if (arrived == (unsigned)gs - 1) {
             atomicExch(bar, 0u);
             __threadfence();
             atomicAdd(bar + 1, 1u);
@@ -74,13 +87,13 @@ __device__ bool grid_sync(unsigned *bar) {
 }
 
 // C = alpha * A * B + beta * C0 (+ gamma * I), all n x n with ld n.  C0 may
-// alias C; A and B must not.  Tiles are spread over the grid.
+// alias C; A and B must not.  Tiles are spread over the group (block lb of gs).
 __device__ void gemm(int n, double alpha, const double *A, const double *B, double beta,
-                     const double *C0, double gamma, double *C) {
+                     const double *C0, double gamma, double *C, int lb, int gs) {
     __shared__ double As[kT][kT + 1], Bs[kT][kT + 1];
     const int tiles = (n + kT - 1) / kT;
     const int tr = threadIdx.x % kT, tc = threadIdx.x / kT;
-    for (int t = blockIdx.x; t < tiles * tiles; t += gridDim.x) {
+    for (int t = lb; t < tiles * tiles; t += gs) {
         const int i0 = (t % tiles) * kT, j0 = (t / tiles) * kT;
         double acc = 0.0;
         for (int k0 = 0; k0 < n; k0 += kT) {
@@ -104,12 +117,11 @@ __device__ void gemm(int n, double alpha, const double *A, const double *B, doub
     }
 }
 
-// Y = sum_k c_k X_k (+ g I), elementwise over the grid.
+// Y = sum_k c_k X_k (+ g I), elementwise over the group.
 __device__ void lincomb(int n, double *Y, double c1, const double *X1, double c2, const double *X2,
-                        double c3, const double *X3, double g) {
+                        double c3, const double *X3, double g, int lb, int gs) {
     const int64_t nn = (int64_t)n * n;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn;
-         e += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t e = (int64_t)lb * blockDim.x + threadIdx.x; e < nn; e += (int64_t)gs * blockDim.x) {
         double v = 0.0;
         if (X1) v += c1 * X1[e];
         if (X2) v += c2 * X2[e];
@@ -119,20 +131,123 @@ __device__ void lincomb(int n, double *Y, double c1, const double *X1, double c2
     }
 }
 
-__global__ void __launch_bounds__(kThreadsE) expm_kernel(const ExpmDev p) {
+// Gauss-Jordan elimination with partial pivoting on the n x 3n matrix G
+// (ld n), by panels of kNB columns (see the file comment).  smem holds the
+// panel (kNB x n) and one n-column buffer per warp.
+__device__ bool gauss_jordan(int n, double *G, unsigned *bar, int lb, int gs, double *smem) {
+    double *pan = smem;
+    double *cb = smem + (size_t)kNB * n + (size_t)(threadIdx.x >> 5) * n;
+    __shared__ int pivs[kNB];
+    __shared__ double invs[kNB], rr[kNB], rv[kWarpsE];
+    __shared__ int ri[kWarpsE];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int k0 = 0; k0 < n; k0 += kNB) {
+        const int kw = min(kNB, n - k0);
+        for (int e = tid; e < kw * n; e += blockDim.x) pan[e] = G[(int64_t)n * k0 + e];
+        __syncthreads();
+        for (int kk = 0; kk < kw; ++kk) {
+            const int k = k0 + kk;
+            const double *pc = pan + (size_t)kk * n;
+            // pivot: largest |entry| in rows k.., lowest row on ties
+            double best = -1.0;
+            int bi = k;
+            for (int i = k + tid; i < n; i += blockDim.x) {
+                const double a = fabs(pc[i]);
+                if (a > best) {
+                    best = a;
+                    bi = i;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_down_sync(0xffffffffu, best, o);
+                const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) {
+                    best = ob;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) {
+                rv[wid] = best;
+                ri[wid] = bi;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double b = rv[0];
+                int i0 = ri[0];
+                for (int w = 1; w < kWarpsE; ++w)
+                    if (rv[w] > b || (rv[w] == b && ri[w] < i0)) {
+                        b = rv[w];
+                        i0 = ri[w];
+                    }
+                pivs[kk] = i0;
+            }
+            __syncthreads();
+            const int piv = pivs[kk];
+            if (tid >= kk && tid < kw && piv != k) {
+                double *c = pan + (size_t)tid * n;
+                const double t = c[k];
+                c[k] = c[piv];
+                c[piv] = t;
+            }
+            __syncthreads();
+            const double inv = 1.0 / pc[k];
+            if (tid == 0) invs[kk] = inv;
+            if (tid > kk && tid < kw) rr[tid] = pan[(size_t)tid * n + k] * inv;
+            __syncthreads();
+            for (int i = tid; i < n; i += blockDim.x) {
+                const double m = pc[i];
+                for (int c = kk + 1; c < kw; ++c) {
+                    double *pcol = pan + (size_t)c * n;
+                    pcol[i] = (i == k) ? rr[c] : fma(-m, rr[c], pcol[i]);
+                }
+            }
+            __syncthreads();
+        }
+        // the columns right of the panel, one warp per column
+        for (int j = k0 + kw + lb * kWarpsE + wid; j < 3 * n; j += gs * kWarpsE) {
+            double *col = G + (int64_t)n * j;
+            for (int i = lane; i < n; i += 32) cb[i] = col[i];
+            __syncwarp();
+            for (int kk = 0; kk < kw; ++kk) {
+                const int k = k0 + kk, piv = pivs[kk];
+                if (lane == 0 && piv != k) {
+                    const double t = cb[k];
+                    cb[k] = cb[piv];
+                    cb[piv] = t;
+                }
+                __syncwarp();
+                const double r = cb[k] * invs[kk];
+                __syncwarp();
+                const double *m = pan + (size_t)kk * n;
+                for (int i = lane; i < n; i += 32) cb[i] = (i == k) ? r : fma(-m[i], r, cb[i]);
+                __syncwarp();
+            }
+            for (int i = lane; i < n; i += 32) col[i] = cb[i];
+            __syncwarp();
+        }
+        if (!grid_sync(bar, gs)) return false;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kThreadsE) expm_kernel(const __grid_constant__ ExpmDev d) {
+    extern __shared__ double esm[];
+    const int gs = gridDim.x / d.count;  // blocks per matrix
+    const int g = blockIdx.x / gs, lb = blockIdx.x % gs;
+    if (g >= d.count) return;  // spare blocks take part in nothing
+    const ExpmProb &p = d.p[g];
     const int n = p.n;
     const int64_t nn = (int64_t)n * n;
     double *B = p.w, *B2 = B + nn, *B4 = B2 + nn, *B6 = B4 + nn, *T1 = B6 + nn, *T2 = T1 + nn;
     double *U = T2 + nn, *V = U + nn, *Q0 = V + nn, *P0 = Q0 + nn, *X = P0 + nn, *R = X + nn;
     double *G = R + nn;  // augmented [Q | P | I]: n x 3n, ld n
-    __shared__ double colk[1024];
     __shared__ double red_v[kThreadsE];
-    __shared__ int red_i[kThreadsE];
 
     // ---- ||tau A||_1
-    for (int j = blockIdx.x; j < n; j += gridDim.x) {
+    for (int j = lb; j < n; j += gs) {
         double s = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) s += fabs(p.tau * p.A[i + p.ldA * j]);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) s += fabs(d.tau * p.A[i + p.ldA * j]);
         red_v[threadIdx.x] = s;
         __syncthreads();
         for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -142,42 +257,39 @@ __global__ void __launch_bounds__(kThreadsE) expm_kernel(const ExpmDev p) {
         if (threadIdx.x == 0) atomicMax(p.norm_bits, (unsigned long long)__double_as_longlong(red_v[0]));
         __syncthreads();
     }
-    if (!grid_sync(p.bar)) return;
+    if (!grid_sync(p.bar, gs)) return;
     const double nrm = __longlong_as_double((long long)*(volatile unsigned long long *)p.norm_bits);
     if (!isfinite(nrm)) {  // non-finite input
-        if (blockIdx.x == 0 && threadIdx.x == 0) latch_error(kErrNumeric);
+        if (lb == 0 && threadIdx.x == 0) latch_error(kErrNumeric);
         return;
     }
     int s = 0;
-    if (nrm > p.theta) s = (int)ceil(log2(nrm / p.theta));
-    const double scale = ldexp(p.tau, -s);
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn;
-         e += (int64_t)gridDim.x * blockDim.x)
+    if (nrm > d.theta) s = (int)ceil(log2(nrm / d.theta));
+    const double scale = ldexp(d.tau, -s);
+    for (int64_t e = (int64_t)lb * blockDim.x + threadIdx.x; e < nn; e += (int64_t)gs * blockDim.x)
         B[e] = scale * p.A[(e % n) + p.ldA * (e / n)];
-    if (!grid_sync(p.bar)) return;
-    gemm(n, 1.0, B, B, 0.0, nullptr, 0.0, B2);
-    if (!grid_sync(p.bar)) return;
-    gemm(n, 1.0, B2, B2, 0.0, nullptr, 0.0, B4);
-    if (!grid_sync(p.bar)) return;
-    gemm(n, 1.0, B4, B2, 0.0, nullptr, 0.0, B6);
-    if (!grid_sync(p.bar)) return;
-    const double *b = p.b;
+    if (!grid_sync(p.bar, gs)) return;
+    gemm(n, 1.0, B, B, 0.0, nullptr, 0.0, B2, lb, gs);
+    if (!grid_sync(p.bar, gs)) return;
+    gemm(n, 1.0, B2, B2, 0.0, nullptr, 0.0, B4, lb, gs);
+    if (!grid_sync(p.bar, gs)) return;
+    gemm(n, 1.0, B4, B2, 0.0, nullptr, 0.0, B6, lb, gs);
+    if (!grid_sync(p.bar, gs)) return;
+    const double *b = d.b;
     // T1 = b13 B6 + b11 B4 + b9 B2 ; T2 = b12 B6 + b10 B4 + b8 B2
-    lincomb(n, T1, b[13], B6, b[11], B4, b[9], B2, 0.0);
-    lincomb(n, T2, b[12], B6, b[10], B4, b[8], B2, 0.0);
-    if (!grid_sync(p.bar)) return;
+    lincomb(n, T1, b[13], B6, b[11], B4, b[9], B2, 0.0, lb, gs);
+    lincomb(n, T2, b[12], B6, b[10], B4, b[8], B2, 0.0, lb, gs);
     // U' = B6 T1 + b7 B6 + b5 B4 + b3 B2 + b1 I  (into R as scratch first)
-    lincomb(n, R, b[7], B6, b[5], B4, b[3], B2, b[1]);
-    lincomb(n, X, b[6], B6, b[4], B4, b[2], B2, b[0]);
-    if (!grid_sync(p.bar)) return;
-    gemm(n, 1.0, B6, T1, 1.0, R, 0.0, R);
-    gemm(n, 1.0, B6, T2, 1.0, X, 0.0, V);
-    if (!grid_sync(p.bar)) return;
-    gemm(n, 1.0, B, R, 0.0, nullptr, 0.0, U);
-    if (!grid_sync(p.bar)) return;
+    lincomb(n, R, b[7], B6, b[5], B4, b[3], B2, b[1], lb, gs);
+    lincomb(n, X, b[6], B6, b[4], B4, b[2], B2, b[0], lb, gs);
+    if (!grid_sync(p.bar, gs)) return;
+    gemm(n, 1.0, B6, T1, 1.0, R, 0.0, R, lb, gs);
+    gemm(n, 1.0, B6, T2, 1.0, X, 0.0, V, lb, gs);
+    if (!grid_sync(p.bar, gs)) return;
+    gemm(n, 1.0, B, R, 0.0, nullptr, 0.0, U, lb, gs);
+    if (!grid_sync(p.bar, gs)) return;
     // Q0 = V - U, P0 = V + U, augmented G = [Q0 | P0 | I]
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn;
-         e += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t e = (int64_t)lb * blockDim.x + threadIdx.x; e < nn; e += (int64_t)gs * blockDim.x) {
         const double q = V[e] - U[e], pp = V[e] + U[e];
         Q0[e] = q;
         P0[e] = pp;
@@ -185,82 +297,24 @@ __global__ void __launch_bounds__(kThreadsE) expm_kernel(const ExpmDev p) {
         G[nn + e] = pp;
         G[2 * nn + e] = (e % n == e / n) ? 1.0 : 0.0;
     }
-    if (!grid_sync(p.bar)) return;
-    // ---- Gauss-Jordan with partial pivoting.  Column j of G is owned by
-    // block (j % gridDim.x); at step k every block reads column k (final
-    // after the previous barrier), finds the pivot, and updates only its own
-    // columns j > k.
-    for (int k = 0; k < n; ++k) {
-        for (int i = threadIdx.x; i < n; i += blockDim.x) colk[i] = G[i + (int64_t)n * k];
-        __syncthreads();
-        double best = -1.0;
-        int bi = k;
-        for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
-            const double a = fabs(colk[i]);
-            if (a > best) { best = a; bi = i; }
-        }
-        red_v[threadIdx.x] = best;
-        red_i[threadIdx.x] = bi;
-        __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if (threadIdx.x < o) {
-                const double ov = red_v[threadIdx.x + o];
-                const int oi = red_i[threadIdx.x + o];
-                if (ov > red_v[threadIdx.x] || (ov == red_v[threadIdx.x] && oi < red_i[threadIdx.x])) {
-                    red_v[threadIdx.x] = ov;
-                    red_i[threadIdx.x] = oi;
-                }
-            }
-            __syncthreads();
-        }
-        const int piv = red_i[0];
-        const double pv = colk[piv];
-        // multipliers after the swap of rows k and piv
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const double t = colk[k];
-            colk[k] = colk[piv];
-            colk[piv] = t;
-        }
-        __syncthreads();
-        const double inv = 1.0 / pv;
-        for (int j = blockIdx.x; j < 3 * n; j += gridDim.x) {
-            if (j <= k) continue;
-            double *col = G + (int64_t)n * j;
-            // swap rows k and piv of this column
-            __syncthreads();
-            double rk = 0.0;
-            if (threadIdx.x == 0) {
-                const double t = col[k];
-                col[k] = col[piv];
-                col[piv] = t;
-            }
-            __syncthreads();
-            rk = col[k] * inv;
-            __syncthreads();
-            for (int i = threadIdx.x; i < n; i += blockDim.x)
-                col[i] = (i == k) ? rk : fma(-colk[i], rk, col[i]);
-            __syncthreads();
-        }
-        if (!grid_sync(p.bar)) return;
-    }
+    if (!grid_sync(p.bar, gs)) return;
+    if (!gauss_jordan(n, G, p.bar, lb, gs, esm)) return;
     double *Xs = G + nn, *Qi = G + 2 * nn;
     // ---- one refinement step: R = P0 - Q0 Xs ; X = Xs + Qi R
-    gemm(n, -1.0, Q0, Xs, 1.0, P0, 0.0, R);
-    if (!grid_sync(p.bar)) return;
-    gemm(n, 1.0, Qi, R, 1.0, Xs, 0.0, X);
-    if (!grid_sync(p.bar)) return;
+    gemm(n, -1.0, Q0, Xs, 1.0, P0, 0.0, R, lb, gs);
+    if (!grid_sync(p.bar, gs)) return;
+    gemm(n, 1.0, Qi, R, 1.0, Xs, 0.0, X, lb, gs);
+    if (!grid_sync(p.bar, gs)) return;
     // ---- squaring: ping-pong between X and T1, last one into E
     double *cur = X;
     for (int r = 0; r < s; ++r) {
         double *dst = (r == s - 1) ? p.E : (cur == X ? T1 : X);
-        gemm(n, 1.0, cur, cur, 0.0, nullptr, 0.0, dst);
-        if (!grid_sync(p.bar)) return;
+        gemm(n, 1.0, cur, cur, 0.0, nullptr, 0.0, dst, lb, gs);
+        if (!grid_sync(p.bar, gs)) return;
         cur = dst;
     }
     if (s == 0) {
-        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn;
-             e += (int64_t)gridDim.x * blockDim.x)
+        for (int64_t e = (int64_t)lb * blockDim.x + threadIdx.x; e < nn; e += (int64_t)gs * blockDim.x)
             p.E[e] = X[e];
     }
 }
@@ -284,30 +338,51 @@ size_t expm_workspace_bytes(int64_t n) {
     return (size_t)(16 * n * n) * sizeof(double) + 256;
 }
 
-cudaError_t expm_pade13(int64_t n, const double *A, int64_t ldA, double tau, double *E, void *ws,
-                        cudaStream_t st) {
-    ExpmDev p{};
-    p.n = (int)n;
-    p.A = A;
-    p.ldA = ldA;
-    p.tau = tau;
-    p.E = E;
-    auto *base = static_cast<uint8_t *>(ws);
-    p.bar = reinterpret_cast<unsigned *>(base);
-    p.norm_bits = reinterpret_cast<unsigned long long *>(base + 64);
-    p.w = reinterpret_cast<double *>(base + 256);
-    pade13(p.b);
-    p.theta = 5.371920351148152;  // theta_13 of Higham (2005), Table 2.3
-    cudaError_t e = cudaMemsetAsync(base, 0, 256, st);
-    if (e != cudaSuccess) return e;
+cudaError_t expm_pade13_batch(int count, const int64_t *n, const double *const *A, const int64_t *ldA, double tau,
+                              double *const *E, void *const *ws, cudaStream_t st) {
+    if (count < 1 || count > KRON_MAX_D) return cudaErrorInvalidValue;
+    ExpmDev d{};
+    d.count = count;
+    d.tau = tau;
+    pade13(d.b);
+    d.theta = 5.371920351148152;  // theta_13 of Higham (2005), Table 2.3
+    int64_t nmax = 1;
+    for (int i = 0; i < count; ++i) {
+        ExpmProb &p = d.p[i];
+        p.n = (int)n[i];
+        p.A = A[i];
+        p.ldA = ldA[i];
+        p.E = E[i];
+        auto *base = static_cast<uint8_t *>(ws[i]);
+        p.bar = reinterpret_cast<unsigned *>(base);
+        p.norm_bits = reinterpret_cast<unsigned long long *>(base + 64);
+        p.w = reinterpret_cast<double *>(base + 256);
+        nmax = std::max(nmax, n[i]);
+        cudaError_t e = cudaMemsetAsync(base, 0, 256, st);
+        if (e != cudaSuccess) return e;
+    }
+    const size_t smem = (size_t)(kNB + kWarpsE) * nmax * sizeof(double);
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(expm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)((kNB + kWarpsE) * 1024 * sizeof(double)));
+    });
+    if (attr != cudaSuccess) return attr;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expm_kernel, kThreadsE, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expm_kernel, kThreadsE, smem);
     if (e != cudaSuccess) return e;
-    const int blocks = std::max(1, sms * std::min(per_sm, 1));
-    void *args[] = {&p};
-    return cudaLaunchCooperativeKernel((void *)expm_kernel, dim3(blocks), dim3(kThreadsE), args, 0, st);
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int blocks = std::max(count, sms);  // one block per SM, whole groups
+    void *args[] = {&d};
+    return cudaLaunchCooperativeKernel((void *)expm_kernel, dim3(blocks), dim3(kThreadsE), args, smem, st);
+}
+
+cudaError_t expm_pade13(int64_t n, const double *A, int64_t ldA, double tau, double *E, void *ws,
+                        cudaStream_t st) {
+    return expm_pade13_batch(1, &n, &A, &ldA, tau, &E, &ws, st);
 }
 
 }  // namespace kron

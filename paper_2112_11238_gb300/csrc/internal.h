@@ -126,6 +126,10 @@ cudaError_t simt_contract_splitk(bool f64, const Contraction &c, void *partial, 
 size_t expm_workspace_bytes(int64_t n);
 cudaError_t expm_pade13(int64_t n, const double *A, int64_t ldA, double tau, double *E, void *ws,
                         cudaStream_t st);
+// count exponentials in one launch (disjoint block groups); ws[i] of
+// expm_workspace_bytes(n[i]) bytes each
+cudaError_t expm_pade13_batch(int count, const int64_t *n, const double *const *A, const int64_t *ldA, double tau,
+                              double *const *E, void *const *ws, cudaStream_t st);
 
 // Device error words of the translation units that have bounded waits.
 cudaError_t tc_error_word(unsigned int *out, bool clear);
