@@ -393,6 +393,29 @@ def run_kernel_only(args):
     return 0
 
 
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
+# capture of `bench.py --kernel-only --prec fx32` (the summary and its command
+# are in profiles/tcp_kernel_fx32_mode_product_256cubed.md).  The counters
+# hold for the kernel sources they were taken on only: another hash of those
+# files reports the traffic as unknown (null).
+KERNEL_SOURCES = ["tcp.cu", "tc_common.cuh", "ptx.cuh", "internal.h"]
+TRAFFIC = {"fx32": {"bytes": 68.092416e6 + 22.993920e6, "src_sha1": "2af3211c68bbfa4753bfa33ab22110bb49ecef60"}}
+
+
+def kernel_src_sha1():
+    import hashlib
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2112_11238_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(prec):
+    t = TRAFFIC.get(prec)
+    return t["bytes"] if t and t["src_sha1"] == kernel_src_sha1() else None
+
+
 def roofline(kern, peaks, src, prec):
     """Roofline of the dominant kernel (one mode product, 256^3 FP32 in/out).
 
@@ -422,7 +445,8 @@ def roofline(kern, peaks, src, prec):
         return {"bound": "hbm", "achieved": byts / t / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": (byts / t / 1e9) / peaks["hbm_gbs"], "traffic": None, "peak_source": src}
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "peak_source": f"{src} (sustained bf16 x nominal ratio / {mult} products)",
+            "traffic": measured_traffic(prec), "algorithmic_bytes": byts,
+            "peak_source": f"{src} (sustained bf16 x nominal ratio / {mult} products)",
             "kernel_ms": kern["ms"]}
 
 
