@@ -203,14 +203,30 @@ KRON_API kron_status kron_tucker_adjoint(kron_plan plan, const void *T, const vo
                                 kron_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Action of a Kronecker sum: Section 2, Eq. (actkron)                       */
+/* ------------------------------------------------------------------------ */
+/*
+ * S = sum_mu V x_mu op(L_mu), i.e. vec(S) = (L_d (+) ... (+) L_1) vec(V)
+ * (Eq. (actkron); Appendix A for the Kronecker sum), without forming the
+ * Kronecker sum.  The plan must be square (m == n); its precision and the
+ * flag KRON_PLAN_TRANS_L apply as for kron_tucker.  The d mu-mode products
+ * all read V; the first writes S and the others accumulate into it, in mode
+ * order 1..d (results are deterministic).  V and S must not alias.
+ */
+KRON_API kron_status kron_kronsumv_workspace_size(kron_plan plan, size_t *bytes);
+KRON_API kron_status kron_kronsumv(kron_plan plan, const void *V, const void *const *L, const int64_t *ldL,
+                                   void *S, void *ws, size_t ws_bytes, kron_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Exponential of a Kronecker sum: Section 3.3, Eqs. (expmat), (exptucker)   */
 /* ------------------------------------------------------------------------ */
 /*
  * E = exp(tau A) for a dense n x n FP64 matrix (device, ld ldA >= n), E dense
  * n x n (ld n), by scaling and squaring with the [13/13] Pade approximant
  * (Higham, SIAM J. Matrix Anal. Appl. 26, 2005), all in FP64 on the GPU; the
- * Pade linear system is solved by LU with partial pivoting followed by one
- * step of iterative refinement with an FP64 residual.  1 <= n <= 1024.
+ * Pade linear system is solved by Gauss-Jordan elimination with partial
+ * pivoting followed by one step of iterative refinement with an FP64
+ * residual.  1 <= n <= 1024.
  */
 KRON_API kron_status kron_expm_workspace_size(int64_t n, size_t *bytes);
 KRON_API kron_status kron_expm(int64_t n, const double *A, int64_t ldA, double tau, double *E,

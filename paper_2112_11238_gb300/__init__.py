@@ -66,6 +66,8 @@ _sig("kron_plan_workspace_size", [_vp, ctypes.POINTER(_sz)])
 _sig("kron_plan_order", [_vp, ctypes.POINTER(_ci)])
 _sig("kron_plan_flops", [_vp], ctypes.c_double)
 _sig("kron_tucker", [_vp, _vp, ctypes.POINTER(_vp), _i64p, _vp, _vp, _sz, _vp])
+_sig("kron_kronsumv_workspace_size", [_vp, ctypes.POINTER(_sz)])
+_sig("kron_kronsumv", [_vp, _vp, ctypes.POINTER(_vp), _i64p, _vp, _vp, _sz, _vp])
 _sig("kron_adjoint_workspace_size", [_vp, ctypes.POINTER(_sz)])
 _sig("kron_tucker_adjoint", [_vp, _vp, ctypes.POINTER(_vp), _i64p, _vp, _vp, ctypes.POINTER(_vp), _vp, _sz, _vp])
 _sig("kron_expm_workspace_size", [ctypes.c_int64, ctypes.POINTER(_sz)])
@@ -83,7 +85,7 @@ _sig("kron_batched_run", [_vp, _vp, _sz, _vp])
 EXPORTS = [
     "kron_status_string", "kron_version", "kron_get_device_error", "kron_mump_workspace_size",
     "kron_mump", "kron_mump_noalloc", "kron_plan_create", "kron_plan_destroy", "kron_plan_workspace_size",
-    "kron_plan_order", "kron_plan_flops", "kron_tucker", "kron_adjoint_workspace_size",
+    "kron_plan_order", "kron_plan_flops", "kron_tucker", "kron_kronsumv_workspace_size", "kron_kronsumv", "kron_adjoint_workspace_size",
     "kron_tucker_adjoint", "kron_expm_workspace_size", "kron_expm",
     "kron_expkronsum_workspace_size", "kron_expkronsum_step", "kron_expkronsum_apply",
     "kron_batched_plan_create", "kron_batched_plan_destroy", "kron_batched_workspace_size",
@@ -294,6 +296,21 @@ class TuckerPlan:
                                 S.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)), "kron_tucker")
         return S
 
+    def kronsumv_workspace_bytes(self) -> int:
+        b = ctypes.c_size_t(0)
+        _check(_lib.kron_kronsumv_workspace_size(self._h, ctypes.byref(b)), "kron_kronsumv_workspace_size")
+        return b.value
+
+    def kronsumv_into(self, V, Ls, S, ws=None, stream=None):
+        """S = sum_mu V x_mu op(L_mu) with preallocated column-major S (Eq. (actkron))."""
+        _require_cuda(V, S, *Ls)
+        mats = [_mat(L) for L in Ls]
+        if ws is None:
+            ws = _workspace(self.kronsumv_workspace_bytes(), V.device)
+        _check(_lib.kron_kronsumv(self._h, V.data_ptr(), _ptrs([L for L, _ in mats]), _i64([ld for _, ld in mats]),
+                                  S.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)), "kron_kronsumv")
+        return S
+
     def adjoint_into(self, T, Ls, dS, dT=None, dLs=None, ws=None, stream=None):
         mats = [_mat(L) for L in Ls]
         if ws is None:
@@ -315,6 +332,16 @@ def tucker(T: torch.Tensor, Ls, prec="fp64", trans: bool = False, natural_order:
     plan = TuckerPlan(T.shape, n, T.dtype, prec, trans, natural_order)
     S = empty_colmajor(n, T.dtype, T.device)
     return plan.tucker_into(T, Ls, S, stream=stream)
+
+
+def kronsumv(V: torch.Tensor, Ls, prec="fp64", trans: bool = False, stream=None) -> torch.Tensor:
+    """Action of the Kronecker sum: sum_mu V x_mu op(L_mu), i.e.
+    vec(S) = (L_d (+) ... (+) L_1) vec(V) (Eq. (actkron)); L_mu square."""
+    V = colmajor(V)
+    Ls = [L.to(V.dtype) for L in Ls]
+    plan = TuckerPlan(V.shape, list(V.shape), V.dtype, prec, trans, natural_order=True)
+    S = empty_colmajor(V.shape, V.dtype, V.device)
+    return plan.kronsumv_into(V, Ls, S, stream=stream)
 
 
 def tucker_adjoint(T: torch.Tensor, Ls, dS: torch.Tensor, prec="fp64", want_dT: bool = True,

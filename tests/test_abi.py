@@ -101,6 +101,17 @@ def test_call_validation_without_gpu(lib):
     assert lib.kron_plan_create(ctypes.byref(h), 2, _i64([3, 4]), _i64([3, 3]), 0, 0, 0) == 0
     assert lib.kron_expkronsum_workspace_size(h, ctypes.byref(ws)) == 1
     lib.kron_plan_destroy(h)
+    # the Kronecker-sum action needs a square plan, and V and S apart
+    assert lib.kron_plan_create(ctypes.byref(h), 2, _i64([3, 4]), _i64([3, 3]), 0, 0, 0) == 0
+    assert lib.kron_kronsumv_workspace_size(h, ctypes.byref(ws)) == 1
+    lib.kron_plan_destroy(h)
+    assert lib.kron_plan_create(ctypes.byref(h), 2, _i64([3, 3]), _i64([3, 3]), 0, 2, 0) == 0
+    assert lib.kron_kronsumv_workspace_size(h, ctypes.byref(ws)) == 0 and ws.value > 0
+    assert lib.kron_kronsumv(h, ctypes.c_void_p(8), L, ld, ctypes.c_void_p(8), None, ctypes.c_size_t(0), None) == 1
+    assert lib.kron_kronsumv(h, ctypes.c_void_p(8), L, ld, ctypes.c_void_p(64), None, ctypes.c_size_t(0), None) == 1
+    assert lib.kron_kronsumv(h, ctypes.c_void_p(8), L, ld, ctypes.c_void_p(64), ctypes.c_void_p(256),
+                             ctypes.c_size_t(0), None) == 4
+    lib.kron_plan_destroy(h)
     # expm size limits
     assert lib.kron_expm_workspace_size(0, ctypes.byref(ws)) == 1
     assert lib.kron_expm_workspace_size(2048, ctypes.byref(ws)) == 1

@@ -87,6 +87,38 @@ def test_tucker_matches_oracle(kron, m, n, prec):
     assert err <= tol(prec, sum(m)), (prec, m, n, err)
 
 
+KSV_SHAPES = [(7,), (37, 19), (9, 33, 17), (130, 5, 3), (20, 20, 20, 3), (3, 4, 5, 6, 7)]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("shape", KSV_SHAPES)
+def test_kronsumv_matches_oracle(kron, shape, prec):
+    """sum_mu V x_mu L_mu against the oracle (Eq. (actkron))."""
+    V = rnd(*shape)
+    Ls = [rnd(n, n) for n in shape]
+    ref = oracle.kronsumv(V, Ls)
+    S = kron.kronsumv(to_dev(V), [to_dev(L) for L in Ls], prec=prec)
+    err = rel_err(to_host(S), ref)
+    assert err <= tol(prec, max(shape)), (prec, shape, err)
+    assert kron.device_error() == 0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "3xtf32", "fx32"])
+def test_kronsumv_transposed_and_float32(kron, prec):
+    import torch
+    shape = (11, 23, 5)
+    V = rnd(*shape)
+    Ls = [rnd(n, n) for n in shape]
+    ref_t = oracle.kronsumv(V, [L.T.copy(order="F") for L in Ls])
+    S = kron.kronsumv(to_dev(V), [to_dev(L) for L in Ls], prec=prec, trans=True)
+    assert rel_err(to_host(S), ref_t) <= TOL[prec]
+    if prec != "fp64":
+        S32 = kron.kronsumv(to_dev(V).float(), [to_dev(L).float() for L in Ls], prec=prec)
+        ref32 = oracle.kronsumv(to_host(to_dev(V).float()), [to_host(to_dev(L).float()) for L in Ls])
+        assert S32.dtype == torch.float32
+        assert rel_err(to_host(S32), ref32) <= max(TOL[prec], 1e-6)
+
+
 def test_fx32_rows_far_below_the_largest_row_sum(kron):
     """Rows of op(L_mu) whose magnitude is far below the largest row sum: in
     the fixed-point chain their products are scaled down (a negative shift)
