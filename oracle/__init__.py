@@ -208,3 +208,21 @@ def kronsumv(V, Ls) -> np.ndarray:
     S = np.zeros(n, order="F")
     _check(_load().oracle_kronsumv(d, _i64(n), _ptr(V), ptrs, lds, _ptr(S)), "kronsumv")
     return S
+
+
+def itucker(V, Ps, transL: bool = False) -> np.ndarray:
+    """V x_1 op(P_1)^{-1} x_2 ... x_d op(P_d)^{-1} (Section 3.4, Eq. (preconnd)).
+
+    Mode by mode in the order 1..d: the mu-mode product with op(P_mu)^{-1} is
+    the solution X^{(mu)} of op(P_mu) X^{(mu)} = current^{(mu)} on the
+    mu-unfolding (Eq. (mmp)), by LU with partial pivoting (numpy.linalg.solve,
+    LAPACK gesv); no inverse is formed."""
+    X = np.array(V, dtype=np.float64)
+    for mu in range(X.ndim):
+        P = np.asarray(Ps[mu], dtype=np.float64)
+        A = P.T if transL else P
+        Xm = np.moveaxis(X, mu, 0)
+        shape = Xm.shape
+        Y = np.linalg.solve(A, Xm.reshape(shape[0], -1))
+        X = np.moveaxis(Y.reshape(shape), 0, mu)
+    return np.asfortranarray(X)

@@ -318,3 +318,44 @@ def test_runge_interpolation_errors_match_paper_m35(m, printed):
     ref = float(printed)
     ulp = 10.0 ** (np.floor(np.log10(ref)) - (digits - 1))
     assert abs(err - ref) <= 0.5 * ulp, (m, err, printed)
+
+
+# ---------------------------------------------------------------- itucker
+
+def _wc(rng, n):
+    """A well-conditioned n x n matrix (I plus a small random part)."""
+    return np.eye(n) + 0.3 * rng.standard_normal((n, n)) / np.sqrt(n)
+
+
+def test_itucker_solves_the_explicit_kronecker_system():
+    """vec(S) = (P_3 (x) P_2 (x) P_1)^{-1} vec(V): a dense solve of the
+    explicit Kronecker product (Eq. (preconnd) with Lemma "krontomu")."""
+    rng = np.random.default_rng(41)
+    m = (2, 3, 4)
+    V = rng.standard_normal(m)
+    Ps = [_wc(rng, n) for n in m]
+    K = np.kron(np.kron(Ps[2], Ps[1]), Ps[0])
+    ref = np.linalg.solve(K, V.reshape(-1, order="F"))
+    S = oracle.itucker(V, Ps)
+    np.testing.assert_allclose(S.reshape(-1, order="F"), ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
+def test_itucker_inverts_the_tucker_operator():
+    rng = np.random.default_rng(42)
+    m = (5, 7, 3, 4)
+    V = rng.standard_normal(m)
+    Ps = [_wc(rng, n) for n in m]
+    back = oracle.itucker(oracle.tucker(V, Ps), Ps)
+    np.testing.assert_allclose(back, V, rtol=0, atol=1e-12 * np.abs(V).max())
+    back_t = oracle.itucker(oracle.tucker(V, Ps, transL=True), Ps, transL=True)
+    np.testing.assert_allclose(back_t, V, rtol=0, atol=1e-12 * np.abs(V).max())
+
+
+def test_itucker_identity_and_two_dimensional_case():
+    rng = np.random.default_rng(43)
+    V = rng.standard_normal((6, 5))
+    assert np.array_equal(oracle.itucker(V, [np.eye(6), np.eye(5)]), V)
+    P1, P2 = _wc(rng, 6), _wc(rng, 5)
+    # d = 2: P_1^{-1} V P_2^{-T} (Section 3.4)
+    ref = np.linalg.inv(P1) @ V @ np.linalg.inv(P2).T
+    np.testing.assert_allclose(oracle.itucker(V, [P1, P2]), ref, rtol=0, atol=1e-13 * np.abs(ref).max())
