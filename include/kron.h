@@ -218,6 +218,27 @@ KRON_API kron_status kron_kronsumv(kron_plan plan, const void *V, const void *co
                                    void *S, void *ws, size_t ws_bytes, kron_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Inverse Tucker operator (preconditioner): Section 3.4, Eqs. (prec),       */
+/* (preconnd)                                                                */
+/* ------------------------------------------------------------------------ */
+/*
+ * S = V x_1 op(P_1)^{-1} x_2 ... x_d op(P_d)^{-1}, i.e.
+ * vec(S) = (op(P_d) (x) ... (x) op(P_1))^{-1} vec(V)  (Eq. (preconnd) with
+ * Lemma "krontomu"; op as set by KRON_PLAN_TRANS_L).  The plan must be square
+ * (m == n, every n_mu <= 1024); P_mu are device matrices of the plan's dtype
+ * with leading dimensions ldP[mu].  The P_mu are inverted in FP64 on the GPU
+ * (Gauss-Jordan with partial pivoting, one launch for all modes); the chain
+ * of inverses runs in the plan's precision; then `refine` (0..8) steps of
+ * iterative refinement: R = V - S x_1 op(P_1) ... x_d op(P_d) in FP64 and
+ * S += R x_1 op(P_1)^{-1} ... x_d op(P_d)^{-1} in the plan's precision.
+ * A zero pivot (singular P_mu) sets KRON_ERR_NUMERIC in the device error word
+ * (kron_get_device_error).  V and S must not alias.
+ */
+KRON_API kron_status kron_itucker_workspace_size(kron_plan plan, int refine, size_t *bytes);
+KRON_API kron_status kron_itucker(kron_plan plan, const void *V, const void *const *P, const int64_t *ldP,
+                                  int refine, void *S, void *ws, size_t ws_bytes, kron_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Exponential of a Kronecker sum: Section 3.3, Eqs. (expmat), (exptucker)   */
 /* ------------------------------------------------------------------------ */
 /*

@@ -68,6 +68,8 @@ _sig("kron_plan_flops", [_vp], ctypes.c_double)
 _sig("kron_tucker", [_vp, _vp, ctypes.POINTER(_vp), _i64p, _vp, _vp, _sz, _vp])
 _sig("kron_kronsumv_workspace_size", [_vp, ctypes.POINTER(_sz)])
 _sig("kron_kronsumv", [_vp, _vp, ctypes.POINTER(_vp), _i64p, _vp, _vp, _sz, _vp])
+_sig("kron_itucker_workspace_size", [_vp, _ci, ctypes.POINTER(_sz)])
+_sig("kron_itucker", [_vp, _vp, ctypes.POINTER(_vp), _i64p, _ci, _vp, _vp, _sz, _vp])
 _sig("kron_adjoint_workspace_size", [_vp, ctypes.POINTER(_sz)])
 _sig("kron_tucker_adjoint", [_vp, _vp, ctypes.POINTER(_vp), _i64p, _vp, _vp, ctypes.POINTER(_vp), _vp, _sz, _vp])
 _sig("kron_expm_workspace_size", [ctypes.c_int64, ctypes.POINTER(_sz)])
@@ -85,7 +87,7 @@ _sig("kron_batched_run", [_vp, _vp, _sz, _vp])
 EXPORTS = [
     "kron_status_string", "kron_version", "kron_get_device_error", "kron_mump_workspace_size",
     "kron_mump", "kron_mump_noalloc", "kron_plan_create", "kron_plan_destroy", "kron_plan_workspace_size",
-    "kron_plan_order", "kron_plan_flops", "kron_tucker", "kron_kronsumv_workspace_size", "kron_kronsumv", "kron_adjoint_workspace_size",
+    "kron_plan_order", "kron_plan_flops", "kron_tucker", "kron_kronsumv_workspace_size", "kron_kronsumv", "kron_itucker_workspace_size", "kron_itucker", "kron_adjoint_workspace_size",
     "kron_tucker_adjoint", "kron_expm_workspace_size", "kron_expm",
     "kron_expkronsum_workspace_size", "kron_expkronsum_step", "kron_expkronsum_apply",
     "kron_batched_plan_create", "kron_batched_plan_destroy", "kron_batched_workspace_size",
@@ -311,6 +313,22 @@ class TuckerPlan:
                                   S.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)), "kron_kronsumv")
         return S
 
+    def itucker_workspace_bytes(self, refine: int = 0) -> int:
+        b = ctypes.c_size_t(0)
+        _check(_lib.kron_itucker_workspace_size(self._h, int(refine), ctypes.byref(b)), "kron_itucker_workspace_size")
+        return b.value
+
+    def itucker_into(self, V, Ps, S, refine: int = 0, ws=None, stream=None):
+        """S = V x_1 op(P_1)^{-1} ... x_d op(P_d)^{-1} (Eq. (preconnd))."""
+        _require_cuda(V, S, *Ps)
+        mats = [_mat(P) for P in Ps]
+        if ws is None:
+            ws = _workspace(self.itucker_workspace_bytes(refine), V.device)
+        _check(_lib.kron_itucker(self._h, V.data_ptr(), _ptrs([P for P, _ in mats]), _i64([ld for _, ld in mats]),
+                                 int(refine), S.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)),
+               "kron_itucker")
+        return S
+
     def adjoint_into(self, T, Ls, dS, dT=None, dLs=None, ws=None, stream=None):
         mats = [_mat(L) for L in Ls]
         if ws is None:
@@ -342,6 +360,16 @@ def kronsumv(V: torch.Tensor, Ls, prec="fp64", trans: bool = False, stream=None)
     plan = TuckerPlan(V.shape, list(V.shape), V.dtype, prec, trans, natural_order=True)
     S = empty_colmajor(V.shape, V.dtype, V.device)
     return plan.kronsumv_into(V, Ls, S, stream=stream)
+
+
+def itucker(V: torch.Tensor, Ps, prec="fp64", trans: bool = False, refine: int = 0, stream=None) -> torch.Tensor:
+    """Inverse Tucker operator V x_1 op(P_1)^{-1} ... x_d op(P_d)^{-1} (Eq. (preconnd)),
+    with `refine` steps of FP64-residual iterative refinement."""
+    V = colmajor(V)
+    Ps = [P.to(V.dtype) for P in Ps]
+    plan = TuckerPlan(V.shape, list(V.shape), V.dtype, prec, trans)
+    S = empty_colmajor(V.shape, V.dtype, V.device)
+    return plan.itucker_into(V, Ps, S, refine=refine, stream=stream)
 
 
 def tucker_adjoint(T: torch.Tensor, Ls, dS: torch.Tensor, prec="fp64", want_dT: bool = True,

@@ -148,7 +148,7 @@ namespace {
 // dst (dtype); intermediates in ws buffers.  Images of the split L live in
 // ws at the plan's offsets.
 kron_status run_chain_fx(const kron_plan_s *pl, const void *T, const void *const *L, const int64_t *ldL,
-                         void *S, uint8_t *ws, cudaStream_t st, bool trans) {
+                         void *S, uint8_t *ws, cudaStream_t st, bool trans, bool acc_last) {
     const int d = pl->d;
     const bool io64 = pl->dtype == KRON_F64;
     FxScale *sc = reinterpret_cast<FxScale *>(ws + pl->fxsc_off);  // [0] input, [1], [2] buffers
@@ -166,6 +166,7 @@ kron_status run_chain_fx(const kron_plan_s *pl, const void *T, const void *const
         void *dst = last ? S : (void *)(ws + pl->buf_off[s & 1]);
         FxScale *sdst = last ? nullptr : &sc[1 + (s & 1)];
         Contraction c = tc_mode_contraction(g, src, false, L[mu], io64, ldL[mu], trans, dst, last ? io64 : false);
+        c.accumulate = last && acc_last;
         void *img = ws + pl->img_off[mu];
         int *f = reinterpret_cast<int *>(ws + pl->fxf_off[mu]);
         auto *gb = reinterpret_cast<unsigned long long *>(ws + pl->fxg_off[mu]);
@@ -180,9 +181,10 @@ kron_status run_chain_fx(const kron_plan_s *pl, const void *T, const void *const
     return KRON_OK;
 }
 
+// acc_last: the last product adds into S instead of overwriting it.
 kron_status run_chain(const kron_plan_s *pl, const void *T, const void *const *L, const int64_t *ldL,
-                      void *S, uint8_t *ws, cudaStream_t st, bool trans) {
-    if (is_fx(pl->prec)) return run_chain_fx(pl, T, L, ldL, S, ws, st, trans);
+                      void *S, uint8_t *ws, cudaStream_t st, bool trans, bool acc_last = false) {
+    if (is_fx(pl->prec)) return run_chain_fx(pl, T, L, ldL, S, ws, st, trans, acc_last);
     const int d = pl->d;
     const bool io64 = pl->dtype == KRON_F64;
     const bool split = is_split(pl->prec);
@@ -201,12 +203,14 @@ kron_status run_chain(const kron_plan_s *pl, const void *T, const void *const *L
         cudaError_t e;
         if (split) {
             Contraction c = tc_mode_contraction(g, src, src64, L[mu], io64, ldL[mu], trans, dst, dst64);
+            c.accumulate = last && acc_last;
             void *img = ws + pl->img_off[mu];
             e = tc_build_bimage(form, c, img, st);
             if (e == cudaSuccess) e = tcp_contract(form, c, img, st);
         } else {
             Contraction c =
                 simt_mode_contraction(g, src, src64, L[mu], io64, ldL[mu], trans, dst, dst64);
+            c.accumulate = last && acc_last;
             e = simt_contract(i64, c, st);
         }
         if (e != cudaSuccess) return KRON_ERR_CUDA;
@@ -739,6 +743,167 @@ kron_status kron_kronsumv(kron_plan plan, const void *V, const void *const *L, c
         }
     }
     return cuda_status(e);
+}
+
+// ------------------------------------------------------------ inverse Tucker
+//
+// S = V x_1 op(P_1)^{-1} ... x_d op(P_d)^{-1} (Eq. (preconnd)).  Workspace:
+// [inversion x d][inverses in FP32 (FP32 plans)][chain of the plan]
+// [refinement: S and P_mu in FP64 (FP32 plans), forward result Y (FP64),
+//  residual R (plan dtype), chain of an FP64 plan].
+namespace {
+struct ItLayout {
+    size_t inv[KRON_MAX_D], pin32[KRON_MAX_D], chain, s64, p64[KRON_MAX_D], y64, r, chain64, total;
+    kron_plan_s pl64;  // the same shapes in FP64 (residual of the refinement)
+};
+
+ItLayout itucker_layout(const kron_plan_s *pl, int refine) {
+    ItLayout l{};
+    const int d = pl->d;
+    const bool f32 = pl->dtype == KRON_F32;
+    const int64_t N = prod(pl->n, 0, d);
+    size_t off = 0;
+    for (int k = 0; k < d; ++k) {
+        l.inv[k] = off;
+        off += align_up(inv_workspace_bytes(pl->n[k]));
+    }
+    for (int k = 0; k < d; ++k) {
+        l.pin32[k] = off;
+        if (f32) off += align_up((size_t)pl->n[k] * pl->n[k] * 4);
+    }
+    l.chain = off;
+    off += align_up(pl->ws_bytes);
+    if (refine > 0) {
+        l.pl64 = *pl;
+        l.pl64.dtype = KRON_F64;
+        l.pl64.prec = KRON_PREC_FP64;
+        plan_layout(&l.pl64);
+        l.s64 = off;
+        if (f32) off += align_up((size_t)N * 8);
+        for (int k = 0; k < d; ++k) {
+            l.p64[k] = off;
+            if (f32) off += align_up((size_t)pl->n[k] * pl->n[k] * 8);
+        }
+        l.y64 = off;
+        off += align_up((size_t)N * 8);
+        l.r = off;
+        off += align_up((size_t)N * esize(pl->dtype));
+        l.chain64 = off;
+        off += align_up(l.pl64.ws_bytes);
+    }
+    l.total = std::max(off, kAlign);
+    return l;
+}
+
+// dst[i + ldd j] = src[i + lds j] for an r x c block, FP64/FP32 either side.
+__global__ void cast2d_kernel(const void *src, bool s64, int64_t lds, void *dst, bool d64, int64_t ldd, int64_t r,
+                              int64_t c) {
+    const int64_t total = r * c;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % r, j = e / r;
+        const double v = s64 ? static_cast<const double *>(src)[i + lds * j]
+                             : (double)static_cast<const float *>(src)[i + lds * j];
+        if (d64) static_cast<double *>(dst)[i + ldd * j] = v;
+        else static_cast<float *>(dst)[i + ldd * j] = (float)v;
+    }
+}
+
+cudaError_t cast2d(const void *src, bool s64, int64_t lds, void *dst, bool d64, int64_t ldd, int64_t r, int64_t c,
+                   cudaStream_t st) {
+    const int64_t total = r * c;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 8));
+    cast2d_kernel<<<blocks, 256, 0, st>>>(src, s64, lds, dst, d64, ldd, r, c);
+    return cudaGetLastError();
+}
+
+// R = V - Y (Y FP64), R and V in the plan dtype.
+__global__ void residual_kernel(const void *V, const double *Y, void *R, bool io64, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (io64) static_cast<double *>(R)[i] = static_cast<const double *>(V)[i] - Y[i];
+        else static_cast<float *>(R)[i] = (float)((double)static_cast<const float *>(V)[i] - Y[i]);
+    }
+}
+}  // namespace
+
+kron_status kron_itucker_workspace_size(kron_plan plan, int refine, size_t *bytes) {
+    if (!plan || !bytes || refine < 0 || refine > 8) return KRON_ERR_INVALID_ARG;
+    if (!square_plan(plan)) return KRON_ERR_INVALID_ARG;
+    for (int k = 0; k < plan->d; ++k)
+        if (plan->n[k] > 1024) return KRON_ERR_UNSUPPORTED;
+    *bytes = itucker_layout(plan, refine).total;
+    return KRON_OK;
+}
+
+kron_status kron_itucker(kron_plan plan, const void *V, const void *const *P, const int64_t *ldP, int refine,
+                         void *S, void *ws, size_t ws_bytes, kron_stream_t stream) {
+    size_t need = 0;
+    kron_status st = kron_itucker_workspace_size(plan, refine, &need);
+    if (st != KRON_OK) return st;
+    if (!V || !S || V == S) return KRON_ERR_INVALID_ARG;
+    const bool trans = (plan->flags & KRON_PLAN_TRANS_L) != 0;
+    st = check_L(plan, P, ldP, trans);
+    if (st != KRON_OK) return st;
+    const size_t es = esize(plan->dtype);
+    if (!aligned(V, es) || !aligned(S, es)) return KRON_ERR_ALIGNMENT;
+    st = check_ws(ws, ws_bytes, need);
+    if (st != KRON_OK) return st;
+    const ItLayout lay = itucker_layout(plan, refine);
+    auto *w = static_cast<uint8_t *>(ws);
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    const int d = plan->d;
+    const bool io64 = plan->dtype == KRON_F64;
+    const int64_t N = prod(plan->n, 0, d);
+    // FP64 inverses, one launch
+    void *iws[KRON_MAX_D];
+    for (int k = 0; k < d; ++k) iws[k] = w + lay.inv[k];
+    cudaError_t e = inv_gj_batch(d, plan->n, P, ldP, io64, iws, cs);
+    const void *Li[KRON_MAX_D];
+    int64_t ldi[KRON_MAX_D];
+    for (int k = 0; k < d && e == cudaSuccess; ++k) {
+        const double *inv = inv_result(plan->n[k], iws[k]);
+        ldi[k] = plan->n[k];
+        if (io64) {
+            Li[k] = inv;
+        } else {
+            e = cast2d(inv, true, plan->n[k], w + lay.pin32[k], false, plan->n[k], plan->n[k], plan->n[k], cs);
+            Li[k] = w + lay.pin32[k];
+        }
+    }
+    if (e != cudaSuccess) return KRON_ERR_CUDA;
+    st = run_chain(plan, V, Li, ldi, S, w + lay.chain, cs, trans);
+    if (st != KRON_OK) return st;
+    // refinement: R = V - S x_mu op(P_mu) in FP64, S += R x_mu op(P_mu)^{-1}
+    const void *P64[KRON_MAX_D];
+    int64_t ld64[KRON_MAX_D];
+    for (int k = 0; k < d; ++k) {
+        P64[k] = P[k];
+        ld64[k] = ldP[k];
+    }
+    if (refine > 0 && !io64) {
+        for (int k = 0; k < d && e == cudaSuccess; ++k) {
+            const int64_t r = trans ? plan->m[k] : plan->n[k];  // rows of the stored P
+            e = cast2d(P[k], false, ldP[k], w + lay.p64[k], true, r, r, r, cs);
+            P64[k] = w + lay.p64[k];
+            ld64[k] = r;
+        }
+        if (e != cudaSuccess) return KRON_ERR_CUDA;
+    }
+    for (int it = 0; it < refine; ++it) {
+        const void *S64 = S;
+        if (!io64) {
+            if (cast2d(S, false, N, w + lay.s64, true, N, N, 1, cs) != cudaSuccess) return KRON_ERR_CUDA;
+            S64 = w + lay.s64;
+        }
+        auto *Y = reinterpret_cast<double *>(w + lay.y64);
+        st = run_chain(&lay.pl64, S64, P64, ld64, Y, w + lay.chain64, cs, trans);
+        if (st != KRON_OK) return st;
+        const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 152 * 8));
+        residual_kernel<<<blocks, 256, 0, cs>>>(V, Y, w + lay.r, io64, N);
+        if (cudaGetLastError() != cudaSuccess) return KRON_ERR_CUDA;
+        st = run_chain(plan, w + lay.r, Li, ldi, S, w + lay.chain, cs, trans, true);
+        if (st != KRON_OK) return st;
+    }
+    return KRON_OK;
 }
 
 // ------------------------------------------------ exponential-of-Kronecker-sum stepper

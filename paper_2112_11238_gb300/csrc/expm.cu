@@ -131,10 +131,11 @@ __device__ void lincomb(int n, double *Y, double c1, const double *X1, double c2
     }
 }
 
-// Gauss-Jordan elimination with partial pivoting on the n x 3n matrix G
-// (ld n), by panels of kNB columns (see the file comment).  smem holds the
-// panel (kNB x n) and one n-column buffer per warp.
-__device__ bool gauss_jordan(int n, double *G, unsigned *bar, int lb, int gs, double *smem) {
+// Gauss-Jordan elimination with partial pivoting on the n x ncols matrix G
+// (ld n, ncols >= n), by panels of kNB columns (see the file comment).  smem
+// holds the panel (kNB x n) and one n-column buffer per warp.  A zero pivot
+// (singular matrix) latches kErrNumeric.
+__device__ bool gauss_jordan(int n, int ncols, double *G, unsigned *bar, int lb, int gs, double *smem) {
     double *pan = smem;
     double *cb = smem + (size_t)kNB * n + (size_t)(threadIdx.x >> 5) * n;
     __shared__ int pivs[kNB];
@@ -181,6 +182,7 @@ __device__ bool gauss_jordan(int n, double *G, unsigned *bar, int lb, int gs, do
                         i0 = ri[w];
                     }
                 pivs[kk] = i0;
+                if (!(b > 0.0) && lb == 0) latch_error(kErrNumeric);
             }
             __syncthreads();
             const int piv = pivs[kk];
@@ -205,7 +207,7 @@ __device__ bool gauss_jordan(int n, double *G, unsigned *bar, int lb, int gs, do
             __syncthreads();
         }
         // the columns right of the panel, one warp per column
-        for (int j = k0 + kw + lb * kWarpsE + wid; j < 3 * n; j += gs * kWarpsE) {
+        for (int j = k0 + kw + lb * kWarpsE + wid; j < ncols; j += gs * kWarpsE) {
             double *col = G + (int64_t)n * j;
             for (int i = lane; i < n; i += 32) cb[i] = col[i];
             __syncwarp();
@@ -298,7 +300,7 @@ __global__ void __launch_bounds__(kThreadsE) expm_kernel(const __grid_constant__
         G[2 * nn + e] = (e % n == e / n) ? 1.0 : 0.0;
     }
     if (!grid_sync(p.bar, gs)) return;
-    if (!gauss_jordan(n, G, p.bar, lb, gs, esm)) return;
+    if (!gauss_jordan(n, 3 * n, G, p.bar, lb, gs, esm)) return;
     double *Xs = G + nn, *Qi = G + 2 * nn;
     // ---- one refinement step: R = P0 - Q0 Xs ; X = Xs + Qi R
     gemm(n, -1.0, Q0, Xs, 1.0, P0, 0.0, R, lb, gs);
@@ -317,6 +319,39 @@ __global__ void __launch_bounds__(kThreadsE) expm_kernel(const __grid_constant__
         for (int64_t e = (int64_t)lb * blockDim.x + threadIdx.x; e < nn; e += (int64_t)gs * blockDim.x)
             p.E[e] = X[e];
     }
+}
+
+struct InvProb {
+    int n;
+    const void *P;
+    int64_t ldP;
+    double *G;      // n x 2n: [P | I] -> [I | P^{-1}]
+    unsigned *bar;  // [0] count, [1] generation
+};
+
+struct InvDev {
+    int count, p64;
+    InvProb p[KRON_MAX_D];
+};
+
+// P^{-1} of several matrices (one group of blocks each), Gauss-Jordan with
+// partial pivoting on [P | I] in FP64.
+__global__ void __launch_bounds__(kThreadsE) inv_kernel(const __grid_constant__ InvDev d) {
+    extern __shared__ double esm[];
+    const int gs = gridDim.x / d.count;
+    const int g = blockIdx.x / gs, lb = blockIdx.x % gs;
+    if (g >= d.count) return;
+    const InvProb &p = d.p[g];
+    const int n = p.n;
+    const int64_t nn = (int64_t)n * n;
+    for (int64_t e = (int64_t)lb * blockDim.x + threadIdx.x; e < nn; e += (int64_t)gs * blockDim.x) {
+        const int64_t i = e % n, j = e / n;
+        const int64_t src = i + p.ldP * j;
+        p.G[e] = d.p64 ? static_cast<const double *>(p.P)[src] : (double)static_cast<const float *>(p.P)[src];
+        p.G[nn + e] = (i == j) ? 1.0 : 0.0;
+    }
+    if (!grid_sync(p.bar, gs)) return;
+    gauss_jordan(n, 2 * n, p.G, p.bar, lb, gs, esm);
 }
 
 // [13/13] Pade numerator coefficients, b13 = 1, from the closed form
@@ -383,6 +418,50 @@ cudaError_t expm_pade13_batch(int count, const int64_t *n, const double *const *
 cudaError_t expm_pade13(int64_t n, const double *A, int64_t ldA, double tau, double *E, void *ws,
                         cudaStream_t st) {
     return expm_pade13_batch(1, &n, &A, &ldA, tau, &E, &ws, st);
+}
+
+size_t inv_workspace_bytes(int64_t n) { return (size_t)(2 * n * n) * sizeof(double) + 256; }
+
+double *inv_result(int64_t n, void *ws) {
+    return reinterpret_cast<double *>(static_cast<uint8_t *>(ws) + 256) + n * n;
+}
+
+cudaError_t inv_gj_batch(int count, const int64_t *n, const void *const *P, const int64_t *ldP, bool p64,
+                         void *const *ws, cudaStream_t st) {
+    if (count < 1 || count > KRON_MAX_D) return cudaErrorInvalidValue;
+    InvDev d{};
+    d.count = count;
+    d.p64 = p64 ? 1 : 0;
+    int64_t nmax = 1;
+    for (int i = 0; i < count; ++i) {
+        InvProb &p = d.p[i];
+        p.n = (int)n[i];
+        p.P = P[i];
+        p.ldP = ldP[i];
+        auto *base = static_cast<uint8_t *>(ws[i]);
+        p.bar = reinterpret_cast<unsigned *>(base);
+        p.G = reinterpret_cast<double *>(base + 256);
+        nmax = std::max(nmax, n[i]);
+        cudaError_t e = cudaMemsetAsync(base, 0, 256, st);
+        if (e != cudaSuccess) return e;
+    }
+    const size_t smem = (size_t)(kNB + kWarpsE) * nmax * sizeof(double);
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)((kNB + kWarpsE) * 1024 * sizeof(double)));
+    });
+    if (attr != cudaSuccess) return attr;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, inv_kernel, kThreadsE, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int blocks = std::max(count, sms);
+    void *args[] = {&d};
+    return cudaLaunchCooperativeKernel((void *)inv_kernel, dim3(blocks), dim3(kThreadsE), args, smem, st);
 }
 
 }  // namespace kron

@@ -130,6 +130,13 @@ cudaError_t expm_pade13(int64_t n, const double *A, int64_t ldA, double tau, dou
 // expm_workspace_bytes(n[i]) bytes each
 cudaError_t expm_pade13_batch(int count, const int64_t *n, const double *const *A, const int64_t *ldA, double tau,
                               double *const *E, void *const *ws, cudaStream_t st);
+// P^{-1} of count matrices (FP64 Gauss-Jordan, one launch): ws[i] of
+// inv_workspace_bytes(n[i]) bytes each; the inverse (n x n, ld n, FP64) is
+// at inv_result(n[i], ws[i]).  P is FP64 (p64) or FP32 with leading dim ldP.
+size_t inv_workspace_bytes(int64_t n);
+double *inv_result(int64_t n, void *ws);
+cudaError_t inv_gj_batch(int count, const int64_t *n, const void *const *P, const int64_t *ldP, bool p64,
+                         void *const *ws, cudaStream_t st);
 
 // Device error words of the translation units that have bounded waits.
 cudaError_t tc_error_word(unsigned int *out, bool clear);

@@ -119,6 +119,65 @@ def test_kronsumv_transposed_and_float32(kron, prec):
         assert rel_err(to_host(S32), ref32) <= max(TOL[prec], 1e-6)
 
 
+def _wc(n):
+    """A well-conditioned n x n matrix (I plus a small random part)."""
+    return np.asfortranarray(np.eye(n) + 0.3 * RNG.standard_normal((n, n)) / np.sqrt(n))
+
+
+IT_SHAPES = [(7,), (37, 19), (9, 33, 17), (130, 5, 3), (20, 20, 20, 3)]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("shape", IT_SHAPES)
+def test_itucker_matches_oracle(kron, shape, prec):
+    """V x_mu P_mu^{-1} (FP64 inverses on the GPU, chain in prec) against the
+    oracle's mode-by-mode LU solves (Eq. (preconnd))."""
+    V = rnd(*shape)
+    Ps = [_wc(n) for n in shape]
+    ref = oracle.itucker(V, Ps)
+    S = kron.itucker(to_dev(V), [to_dev(P) for P in Ps], prec=prec)
+    err = rel_err(to_host(S), ref)
+    assert err <= 2 * tol(prec, max(shape)), (prec, shape, err)
+    assert kron.device_error() == 0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "3xtf32", "bf16x3", "bf16x6", "fx32"])
+def test_itucker_refinement_reaches_fp64_accuracy(kron, prec):
+    """FP64-residual iterative refinement of the low-precision chain."""
+    shape = (9, 33, 17)
+    V = rnd(*shape)
+    Ps = [_wc(n) for n in shape]
+    ref = oracle.itucker(V, Ps)
+    e0 = rel_err(to_host(kron.itucker(to_dev(V), [to_dev(P) for P in Ps], prec=prec)), ref)
+    e3 = rel_err(to_host(kron.itucker(to_dev(V), [to_dev(P) for P in Ps], prec=prec, refine=3)), ref)
+    assert e3 <= 1e-12 and e3 < e0 / 100, (prec, e0, e3)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "3xtf32", "fx32"])
+def test_itucker_transposed_and_float32(kron, prec):
+    import torch
+    shape = (11, 23, 5)
+    V = rnd(*shape)
+    Ps = [_wc(n) for n in shape]
+    ref_t = oracle.itucker(V, Ps, transL=True)
+    S = kron.itucker(to_dev(V), [to_dev(P) for P in Ps], prec=prec, trans=True, refine=1)
+    assert rel_err(to_host(S), ref_t) <= 1e-12
+    V32, P32 = to_dev(V).float(), [to_dev(P).float() for P in Ps]
+    ref32 = oracle.itucker(to_host(V32), [to_host(P) for P in P32])
+    S32 = kron.itucker(V32, P32, prec=prec, refine=2)
+    assert S32.dtype == torch.float32
+    assert rel_err(to_host(S32), ref32) <= 2e-7  # FP32 storage of S
+
+
+def test_itucker_singular_matrix_sets_the_numeric_flag(kron):
+    shape = (6, 5)
+    V = rnd(*shape)
+    Ps = [np.zeros((6, 6), order="F"), _wc(5)]
+    kron.itucker(to_dev(V), [to_dev(P) for P in Ps], prec="fp64")
+    assert kron.device_error() & 2
+    assert kron.device_error() == 0  # cleared by the read
+
+
 def test_fx32_rows_far_below_the_largest_row_sum(kron):
     """Rows of op(L_mu) whose magnitude is far below the largest row sum: in
     the fixed-point chain their products are scaled down (a negative shift)
