@@ -226,3 +226,42 @@ def itucker(V, Ps, transL: bool = False) -> np.ndarray:
         Y = np.linalg.solve(A, Xm.reshape(shape[0], -1))
         X = np.moveaxis(Y.reshape(shape), 0, mu)
     return np.asfortranarray(X)
+
+
+def laplacian_eig(n: int):
+    """Eigenpairs of tridiag(1, -2, 1) / h^2, h = 1/(n+1) (textbook closed
+    form): lambda_k = -4 / h^2 sin^2(k pi / (2 (n + 1))), orthonormal
+    eigenvectors Q_jk = sqrt(2 / (n + 1)) sin(j k pi / (n + 1)), j, k = 1..n."""
+    k = np.arange(1, n + 1)
+    h = 1.0 / (n + 1)
+    lam = -4.0 / h ** 2 * np.sin(k * np.pi / (2.0 * (n + 1))) ** 2
+    Q = np.sqrt(2.0 / (n + 1)) * np.sin(np.outer(k, k) * np.pi / (n + 1))
+    return lam, np.asfortranarray(Q)
+
+
+def kronsum_solve_laplacian(V, n, tau: float):
+    """x with (M_d (+) ... (+) M_1) x = v, M_mu = I/d - tau A_mu, A_mu the FD
+    Laplacians: exact (up to rounding) by diagonalisation, x = Q D^{-1} Q^T v
+    with Q = Q_d (x) ... (x) Q_1 applied as Tucker operators and
+    D = 1 - tau (lambda_d (+) ... (+) lambda_1)."""
+    eig = [laplacian_eig(k) for k in n]
+    W = tucker(V, [Q.T.copy(order="F") for _, Q in eig])
+    D = np.ones(tuple(n))
+    for mu, (lam, _) in enumerate(eig):
+        shape = [1] * len(n)
+        shape[mu] = n[mu]
+        D = D - tau * lam.reshape(shape)
+    return tucker(np.asfortranarray(W / D), [Q for _, Q in eig])
+
+
+def semilinear_imex(case) -> np.ndarray:
+    """Backward-forward (IMEX) Euler of Section 4.5, Eq. (semilin-disc):
+    M u_{k+1} = u_k + tau f(t_k, u_k), f = 1 / (1 + u^2) + Phi(t_k, x),
+    M = M_3 (+) M_2 (+) M_1, every system solved exactly
+    (kronsum_solve_laplacian).  Returns u at t* = nsteps tau."""
+    u = np.array(case.U0, order="F")
+    for k in range(case.nsteps):
+        t = k * case.tau
+        rhs = u + case.tau * (1.0 / (1.0 + u ** 2) + case.phi(t))
+        u = kronsum_solve_laplacian(rhs, case.n, case.tau)
+    return u

@@ -359,3 +359,50 @@ def test_itucker_identity_and_two_dimensional_case():
     # d = 2: P_1^{-1} V P_2^{-T} (Section 3.4)
     ref = np.linalg.inv(P1) @ V @ np.linalg.inv(P2).T
     np.testing.assert_allclose(oracle.itucker(V, [P1, P2]), ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
+# ----------------------------------------------- semilinear IMEX (Section 4.5)
+
+def _golden_table3():
+    path = os.path.join(os.path.dirname(__file__), "golden", "table3_semilinear.txt")
+    with open(path) as f:
+        row = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")][0]
+    return tuple(int(v) for v in row[:3]), float(row[3]), float(row[4]), float(row[5]), int(row[6]), int(row[7])
+
+
+def test_laplacian_eigenpairs_closed_form():
+    n = 9
+    lam, Q = oracle.laplacian_eig(n)
+    A = W.tridiag_dense(n, (n + 1.0) ** 2, -2.0 * (n + 1.0) ** 2, (n + 1.0) ** 2)
+    np.testing.assert_allclose(A @ Q, Q * lam, rtol=0, atol=1e-10 * np.abs(lam).max())
+    np.testing.assert_allclose(Q.T @ Q, np.eye(n), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(np.sort(lam), np.linalg.eigvalsh(A), rtol=1e-13)
+
+
+def test_kronsum_solve_inverts_the_kronecker_sum():
+    """The diagonalised solve against the Kronecker-sum action (Eq. (actkron))
+    and a dense solve of the assembled matrix."""
+    c = W.semilinear(n=(5, 6, 7), tau=0.01)
+    rng = np.random.default_rng(44)
+    v = rng.standard_normal(c.n)
+    x = oracle.kronsum_solve_laplacian(v, c.n, c.tau)
+    np.testing.assert_allclose(oracle.kronsumv(x, c.M), v, rtol=0, atol=1e-13 * np.abs(v).max())
+    I = [np.eye(k) for k in c.n]
+    Mfull = (np.kron(np.kron(I[2], I[1]), c.M[0]) + np.kron(np.kron(I[2], c.M[1]), I[0])
+             + np.kron(np.kron(c.M[2], I[1]), I[0]))
+    ref = np.linalg.solve(Mfull, v.reshape(-1, order="F"))
+    np.testing.assert_allclose(x.reshape(-1, order="F"), ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
+def test_semilinear_final_error_matches_the_paper():
+    """Section 4.5: final relative error 9.7e-3 at n = (40, 44, 48), tau = 0.01,
+    t* = 1.  The scheme with exact solves gives 9.76e-3, which agrees with the
+    printed two digits when the printed value is truncated; accepted band
+    [9.6e-3, 9.8e-3]."""
+    n, tau, tstar, printed, _, _ = _golden_table3()
+    c = W.semilinear(n=n, tau=tau, tstar=tstar)
+    u = oracle.semilinear_imex(c)
+    ex = c.exact(tstar)
+    err = np.abs(u - ex).max() / np.abs(ex).max()
+    assert abs(err - printed) <= 0.1e-3, err
+    assert err == pytest.approx(9.7576e-3, rel=1e-3)

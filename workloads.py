@@ -23,6 +23,11 @@ Workloads (sizes are the ones the benchmark and the parity tests use):
                       n_mu = ceil(1.5 m_mu), L_mu barycentric Lagrange
                       matrices from Chebyshev points to uniform points.
 * ``adjoint``       : d = 4, n = m = 48, T, L_mu, S_target standard normal.
+* ``semilinear``    : the 3-D semilinear problem of Section 4.5, n = (40, 44,
+                      48) interior points, tau = 0.01, t* = 1: FD Laplacians,
+                      the IMEX factors M_mu = I/3 - tau A_mu and the ADI
+                      factors P_mu = I - tau A_mu, u_0, and the forcing Phi
+                      that makes e^t u_0 the exact solution.
 """
 from __future__ import annotations
 
@@ -269,3 +274,49 @@ def rel_err_max(x, ref) -> float:
         return num
     return num / den
 
+
+
+@dataclass
+class SemilinearCase:
+    """u_t = Laplace(u) + 1 / (1 + u^2) + Phi(t, x) on [0, 1]^3, homogeneous
+    Dirichlet, u_0 = prod_mu x_mu (1 - x_mu), exact solution e^t u_0
+    (Section 4.5, Eq. (semilinear))."""
+    n: tuple
+    tau: float
+    nsteps: int
+    x: list                # interior points x_j = j h, h = 1 / (n + 1)
+    A: list                # dense FD Laplacians tridiag(1, -2, 1) / h^2
+    M: list                # I / d - tau A_mu: M = M_d (+) ... (+) M_1
+    P: list                # I - tau A_mu: ADI preconditioner P_d (x) ... (x) P_1
+    U0: np.ndarray
+    LU0: np.ndarray        # Laplacian of u_0 (its FD Laplacian is the same: u_0 is quadratic per axis)
+
+    def phi(self, t: float) -> np.ndarray:
+        """Phi = u_t - Laplace(u) - 1 / (1 + u^2) at u = e^t u_0."""
+        et = np.exp(t)
+        return np.asfortranarray(et * (self.U0 - self.LU0) - 1.0 / (1.0 + (et * self.U0) ** 2))
+
+    def exact(self, t: float) -> np.ndarray:
+        return np.asfortranarray(np.exp(t) * self.U0)
+
+
+def semilinear(n=(40, 44, 48), tau: float = 0.01, tstar: float = 1.0) -> SemilinearCase:
+    d = len(n)
+    x = [np.arange(1, k + 1) / (k + 1.0) for k in n]
+    A = [tridiag_dense(k, (k + 1.0) ** 2, -2.0 * (k + 1.0) ** 2, (k + 1.0) ** 2) for k in n]
+    M = [np.asfortranarray(np.eye(k) / d - tau * a) for k, a in zip(n, A)]
+    P = [np.asfortranarray(np.eye(k) - tau * a) for k, a in zip(n, A)]
+    g = [xx * (1.0 - xx) for xx in x]
+
+    def outer(vs):
+        out = vs[0]
+        for v in vs[1:]:
+            out = np.multiply.outer(out, v)
+        return np.asfortranarray(out)
+
+    U0 = outer(g)
+    LU0 = np.zeros(tuple(n), order="F")
+    for mu in range(d):
+        LU0 += outer([(-2.0 * np.ones(k)) if nu == mu else g[nu] for nu, k in enumerate(n)])
+    nsteps = int(round(tstar / tau))
+    return SemilinearCase(tuple(n), tau, nsteps, x, A, M, P, U0, np.asfortranarray(LU0))
