@@ -238,6 +238,27 @@ KRON_API kron_status kron_itucker_workspace_size(kron_plan plan, int refine, siz
 KRON_API kron_status kron_itucker(kron_plan plan, const void *V, const void *const *P, const int64_t *ldP,
                                   int refine, void *S, void *ws, size_t ws_bytes, kron_stream_t stream);
 
+/*
+ * Preconditioned conjugate gradients for M x = b with the Kronecker-sum
+ * matrix M = M_d (+) ... (+) M_1 (symmetric positive definite) and the
+ * ADI-type preconditioner P = P_d (x) ... (x) P_1 (Section 3.4, Eq. (prec);
+ * Section 4.5): M v by kron_kronsumv, P^{-1} v by kron_itucker (no
+ * refinement).  P == NULL runs plain CG.  X holds the initial guess on entry
+ * and the solution on return; B and X (sizes n, the plan's dtype) must not
+ * alias.  Stops when ||b - M x||_2 <= tol ||b||_2 or after maxit iterations;
+ * *iters and *relres (host pointers, may be NULL) receive the iteration count
+ * and ||b - M x|| / ||b|| of the returned x (recurrence residual).  Dot
+ * products are FP64 with a fixed summation order.  Unlike the other calls,
+ * this one synchronises `stream` once per iteration (it reads the residual
+ * norm on the host).  The plan's precision applies to the products (FP64 for
+ * a solve to FP64 accuracy).
+ */
+KRON_API kron_status kron_kronsum_pcg_workspace_size(kron_plan plan, int precondition, size_t *bytes);
+KRON_API kron_status kron_kronsum_pcg(kron_plan plan, const void *const *M, const int64_t *ldM,
+                                      const void *const *P, const int64_t *ldP, const void *B, void *X,
+                                      double tol, int maxit, int *iters, double *relres, void *ws,
+                                      size_t ws_bytes, kron_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Exponential of a Kronecker sum: Section 3.3, Eqs. (expmat), (exptucker)   */
 /* ------------------------------------------------------------------------ */

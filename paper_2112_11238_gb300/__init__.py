@@ -70,6 +70,9 @@ _sig("kron_kronsumv_workspace_size", [_vp, ctypes.POINTER(_sz)])
 _sig("kron_kronsumv", [_vp, _vp, ctypes.POINTER(_vp), _i64p, _vp, _vp, _sz, _vp])
 _sig("kron_itucker_workspace_size", [_vp, _ci, ctypes.POINTER(_sz)])
 _sig("kron_itucker", [_vp, _vp, ctypes.POINTER(_vp), _i64p, _ci, _vp, _vp, _sz, _vp])
+_sig("kron_kronsum_pcg_workspace_size", [_vp, _ci, ctypes.POINTER(_sz)])
+_sig("kron_kronsum_pcg", [_vp, ctypes.POINTER(_vp), _i64p, ctypes.POINTER(_vp), _i64p, _vp, _vp, ctypes.c_double,
+                          _ci, ctypes.POINTER(_ci), ctypes.POINTER(ctypes.c_double), _vp, _sz, _vp])
 _sig("kron_adjoint_workspace_size", [_vp, ctypes.POINTER(_sz)])
 _sig("kron_tucker_adjoint", [_vp, _vp, ctypes.POINTER(_vp), _i64p, _vp, _vp, ctypes.POINTER(_vp), _vp, _sz, _vp])
 _sig("kron_expm_workspace_size", [ctypes.c_int64, ctypes.POINTER(_sz)])
@@ -87,7 +90,7 @@ _sig("kron_batched_run", [_vp, _vp, _sz, _vp])
 EXPORTS = [
     "kron_status_string", "kron_version", "kron_get_device_error", "kron_mump_workspace_size",
     "kron_mump", "kron_mump_noalloc", "kron_plan_create", "kron_plan_destroy", "kron_plan_workspace_size",
-    "kron_plan_order", "kron_plan_flops", "kron_tucker", "kron_kronsumv_workspace_size", "kron_kronsumv", "kron_itucker_workspace_size", "kron_itucker", "kron_adjoint_workspace_size",
+    "kron_plan_order", "kron_plan_flops", "kron_tucker", "kron_kronsumv_workspace_size", "kron_kronsumv", "kron_itucker_workspace_size", "kron_itucker", "kron_kronsum_pcg_workspace_size", "kron_kronsum_pcg", "kron_adjoint_workspace_size",
     "kron_tucker_adjoint", "kron_expm_workspace_size", "kron_expm",
     "kron_expkronsum_workspace_size", "kron_expkronsum_step", "kron_expkronsum_apply",
     "kron_batched_plan_create", "kron_batched_plan_destroy", "kron_batched_workspace_size",
@@ -329,6 +332,31 @@ class TuckerPlan:
                "kron_itucker")
         return S
 
+    def pcg_workspace_bytes(self, precondition: bool = True) -> int:
+        b = ctypes.c_size_t(0)
+        _check(_lib.kron_kronsum_pcg_workspace_size(self._h, int(bool(precondition)), ctypes.byref(b)),
+               "kron_kronsum_pcg_workspace_size")
+        return b.value
+
+    def kronsum_pcg(self, Ms, B, X, Ps=None, tol: float = 1e-6, maxit: int = 20, ws=None, stream=None):
+        """Solve (M_d (+) ... (+) M_1) x = b by CG, preconditioned by
+        P_d (x) ... (x) P_1 when Ps is given; X: initial guess, overwritten.
+        Returns (X, iterations, relative residual)."""
+        _require_cuda(B, X, *Ms, *(Ps or []))
+        mats = [_mat(M) for M in Ms]
+        pm = [_mat(P) for P in Ps] if Ps is not None else None
+        if ws is None:
+            ws = _workspace(self.pcg_workspace_bytes(Ps is not None), B.device)
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        _check(_lib.kron_kronsum_pcg(self._h, _ptrs([M for M, _ in mats]), _i64([ld for _, ld in mats]),
+                                     _ptrs([P for P, _ in pm]) if pm else None,
+                                     _i64([ld for _, ld in pm]) if pm else None,
+                                     B.data_ptr(), X.data_ptr(), float(tol), int(maxit), ctypes.byref(it),
+                                     ctypes.byref(rr), ws.data_ptr(), ws.numel(), _stream(stream)),
+               "kron_kronsum_pcg")
+        return X, it.value, rr.value
+
     def adjoint_into(self, T, Ls, dS, dT=None, dLs=None, ws=None, stream=None):
         mats = [_mat(L) for L in Ls]
         if ws is None:
@@ -370,6 +398,22 @@ def itucker(V: torch.Tensor, Ps, prec="fp64", trans: bool = False, refine: int =
     plan = TuckerPlan(V.shape, list(V.shape), V.dtype, prec, trans)
     S = empty_colmajor(V.shape, V.dtype, V.device)
     return plan.itucker_into(V, Ps, S, refine=refine, stream=stream)
+
+
+def kronsum_pcg(Ms, B: torch.Tensor, X0=None, Ps=None, tol: float = 1e-6, maxit: int = 20, prec="fp64",
+                stream=None):
+    """(M_d (+) ... (+) M_1) x = b by (preconditioned) CG on the tensor B;
+    returns (X, iterations, relative residual) (Sections 3.4 and 4.5)."""
+    B = colmajor(B)
+    Ms = [M.to(B.dtype) for M in Ms]
+    Ps = [P.to(B.dtype) for P in Ps] if Ps is not None else None
+    plan = TuckerPlan(B.shape, list(B.shape), B.dtype, prec, natural_order=True)
+    X = empty_colmajor(B.shape, B.dtype, B.device)
+    if X0 is None:
+        X.zero_()
+    else:
+        X.copy_(X0)
+    return plan.kronsum_pcg(Ms, B, X, Ps, tol, maxit, stream=stream)
 
 
 def tucker_adjoint(T: torch.Tensor, Ls, dS: torch.Tensor, prec="fp64", want_dT: bool = True,

@@ -825,6 +825,28 @@ __global__ void residual_kernel(const void *V, const double *Y, void *R, bool io
 }
 }  // namespace
 
+// FP64 inverses of the P_mu (one launch) into the layout; Li / ldi receive
+// the matrices the chain uses (FP64, or FP32 copies for FP32 plans).
+cudaError_t itucker_prepare(const kron_plan_s *plan, const void *const *P, const int64_t *ldP, uint8_t *w,
+                            const ItLayout &lay, const void **Li, int64_t *ldi, cudaStream_t cs) {
+    const int d = plan->d;
+    const bool io64 = plan->dtype == KRON_F64;
+    void *iws[KRON_MAX_D];
+    for (int k = 0; k < d; ++k) iws[k] = w + lay.inv[k];
+    cudaError_t e = inv_gj_batch(d, plan->n, P, ldP, io64, iws, cs);
+    for (int k = 0; k < d && e == cudaSuccess; ++k) {
+        const double *inv = inv_result(plan->n[k], iws[k]);
+        ldi[k] = plan->n[k];
+        if (io64) {
+            Li[k] = inv;
+        } else {
+            e = cast2d(inv, true, plan->n[k], w + lay.pin32[k], false, plan->n[k], plan->n[k], plan->n[k], cs);
+            Li[k] = w + lay.pin32[k];
+        }
+    }
+    return e;
+}
+
 kron_status kron_itucker_workspace_size(kron_plan plan, int refine, size_t *bytes) {
     if (!plan || !bytes || refine < 0 || refine > 8) return KRON_ERR_INVALID_ARG;
     if (!square_plan(plan)) return KRON_ERR_INVALID_ARG;
@@ -854,21 +876,9 @@ kron_status kron_itucker(kron_plan plan, const void *V, const void *const *P, co
     const bool io64 = plan->dtype == KRON_F64;
     const int64_t N = prod(plan->n, 0, d);
     // FP64 inverses, one launch
-    void *iws[KRON_MAX_D];
-    for (int k = 0; k < d; ++k) iws[k] = w + lay.inv[k];
-    cudaError_t e = inv_gj_batch(d, plan->n, P, ldP, io64, iws, cs);
     const void *Li[KRON_MAX_D];
     int64_t ldi[KRON_MAX_D];
-    for (int k = 0; k < d && e == cudaSuccess; ++k) {
-        const double *inv = inv_result(plan->n[k], iws[k]);
-        ldi[k] = plan->n[k];
-        if (io64) {
-            Li[k] = inv;
-        } else {
-            e = cast2d(inv, true, plan->n[k], w + lay.pin32[k], false, plan->n[k], plan->n[k], plan->n[k], cs);
-            Li[k] = w + lay.pin32[k];
-        }
-    }
+    cudaError_t e = itucker_prepare(plan, P, ldP, w, lay, Li, ldi, cs);
     if (e != cudaSuccess) return KRON_ERR_CUDA;
     st = run_chain(plan, V, Li, ldi, S, w + lay.chain, cs, trans);
     if (st != KRON_OK) return st;
@@ -903,6 +913,144 @@ kron_status kron_itucker(kron_plan plan, const void *V, const void *const *P, co
         st = run_chain(plan, w + lay.r, Li, ldi, S, w + lay.chain, cs, trans, true);
         if (st != KRON_OK) return st;
     }
+    return KRON_OK;
+}
+
+// --------------------------------------------- PCG for Kronecker-sum systems
+//
+// Workspace: [r][z][p][q] (N values of the plan dtype), [scalars][dot
+// partials], [kron_kronsumv workspace], [kron_itucker workspace].
+namespace {
+struct PcgLayout {
+    size_t r, z, p, q, sc, part, ksv, itk, total;
+};
+
+PcgLayout pcg_layout(const kron_plan_s *pl, bool pre) {
+    PcgLayout l{};
+    const size_t vb = align_up((size_t)prod(pl->n, 0, pl->d) * esize(pl->dtype));
+    size_t off = 0;
+    l.r = off;
+    off += vb;
+    l.z = off;
+    off += vb;
+    l.p = off;
+    off += vb;
+    l.q = off;
+    off += vb;
+    l.sc = off;
+    off += kAlign;
+    l.part = off;
+    off += align_up(pcg_partial_doubles() * sizeof(double));
+    l.ksv = off;
+    off += align_up(kronsumv_layout(pl).total);
+    l.itk = off;
+    if (pre) off += align_up(itucker_layout(pl, 0).total);
+    l.total = off;
+    return l;
+}
+}  // namespace
+
+kron_status kron_kronsum_pcg_workspace_size(kron_plan plan, int precondition, size_t *bytes) {
+    if (!plan || !bytes) return KRON_ERR_INVALID_ARG;
+    if (!square_plan(plan)) return KRON_ERR_INVALID_ARG;
+    if (precondition)
+        for (int k = 0; k < plan->d; ++k)
+            if (plan->n[k] > 1024) return KRON_ERR_UNSUPPORTED;
+    *bytes = pcg_layout(plan, precondition != 0).total;
+    return KRON_OK;
+}
+
+kron_status kron_kronsum_pcg(kron_plan plan, const void *const *M, const int64_t *ldM, const void *const *P,
+                             const int64_t *ldP, const void *B, void *X, double tol, int maxit, int *iters,
+                             double *relres, void *ws, size_t ws_bytes, kron_stream_t stream) {
+    const bool pre = P != nullptr;
+    size_t need = 0;
+    kron_status st = kron_kronsum_pcg_workspace_size(plan, pre ? 1 : 0, &need);
+    if (st != KRON_OK) return st;
+    if (!B || !X || B == X || !(tol >= 0.0) || maxit < 0) return KRON_ERR_INVALID_ARG;
+    const bool trans = (plan->flags & KRON_PLAN_TRANS_L) != 0;
+    st = check_L(plan, M, ldM, trans);
+    if (st == KRON_OK && pre) st = check_L(plan, P, ldP, trans);
+    if (st != KRON_OK) return st;
+    const size_t es = esize(plan->dtype);
+    if (!aligned(B, es) || !aligned(X, es)) return KRON_ERR_ALIGNMENT;
+    st = check_ws(ws, ws_bytes, need);
+    if (st != KRON_OK) return st;
+    const PcgLayout lay = pcg_layout(plan, pre);
+    auto *w = static_cast<uint8_t *>(ws);
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    const bool f64 = plan->dtype == KRON_F64;
+    const int64_t N = prod(plan->n, 0, plan->d);
+    void *r = w + lay.r, *z = w + lay.z, *p = w + lay.p, *q = w + lay.q;
+    double *sc = reinterpret_cast<double *>(w + lay.sc);  // [0] b.b [1] r.z [2] p.q [3] r.r [4] new r.z
+    double *part = reinterpret_cast<double *>(w + lay.part);
+    const size_t ksv_bytes = kronsumv_layout(plan).total;
+    auto matvec = [&](const void *v, void *out) {
+        return kron_kronsumv(plan, v, M, ldM, out, w + lay.ksv, ksv_bytes, stream);
+    };
+    // the preconditioner's inverses once per solve
+    const ItLayout itl = itucker_layout(plan, 0);
+    const void *Li[KRON_MAX_D];
+    int64_t ldi[KRON_MAX_D];
+    if (pre && itucker_prepare(plan, P, ldP, w + lay.itk, itl, Li, ldi, cs) != cudaSuccess) return KRON_ERR_CUDA;
+    auto precond = [&](const void *v, void *out) -> kron_status {
+        if (pre) return run_chain(plan, v, Li, ldi, out, w + lay.itk + itl.chain, cs, trans);
+        return cuda_status(cudaMemcpyAsync(out, v, (size_t)N * es, cudaMemcpyDeviceToDevice, cs));
+    };
+    auto host = [&](const double *dev, double *out) {
+        cudaError_t e = cudaMemcpyAsync(out, dev, sizeof(double), cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+        return e;
+    };
+    int done = 0;
+    double bb = 0.0, rr = 0.0;
+    // r = b - M x ; z = P^{-1} r ; p = z
+    st = matvec(X, q);
+    if (st != KRON_OK) return st;
+    cudaError_t e = pcg_axpby(f64, N, 1.0, nullptr, nullptr, B, 0.0, nullptr, nullptr, r, cs);
+    if (e == cudaSuccess) e = pcg_axpby(f64, N, -1.0, nullptr, nullptr, q, 1.0, nullptr, nullptr, r, cs);
+    if (e == cudaSuccess) e = pcg_dot(B, B, f64, N, part, &sc[0], cs);
+    if (e == cudaSuccess) e = pcg_dot(r, r, f64, N, part, &sc[3], cs);
+    if (e == cudaSuccess) e = host(&sc[0], &bb);
+    if (e == cudaSuccess) e = host(&sc[3], &rr);
+    if (e != cudaSuccess) return KRON_ERR_CUDA;
+    if (bb == 0.0) {  // b = 0: x = 0
+        e = cudaMemsetAsync(X, 0, (size_t)N * es, cs);
+        if (iters) *iters = 0;
+        if (relres) *relres = 0.0;
+        return cuda_status(e);
+    }
+    const double bn = std::sqrt(bb);
+    if (std::sqrt(rr) > tol * bn && maxit > 0) {
+        st = precond(r, z);
+        if (st != KRON_OK) return st;
+        e = pcg_axpby(f64, N, 1.0, nullptr, nullptr, z, 0.0, nullptr, nullptr, p, cs);
+        if (e == cudaSuccess) e = pcg_dot(r, z, f64, N, part, &sc[1], cs);
+        if (e != cudaSuccess) return KRON_ERR_CUDA;
+        while (done < maxit) {
+            st = matvec(p, q);
+            if (st != KRON_OK) return st;
+            e = pcg_dot(p, q, f64, N, part, &sc[2], cs);
+            // x += (rz / pq) p ; r -= (rz / pq) q
+            if (e == cudaSuccess) e = pcg_axpby(f64, N, 1.0, &sc[1], &sc[2], p, 1.0, nullptr, nullptr, X, cs);
+            if (e == cudaSuccess) e = pcg_axpby(f64, N, -1.0, &sc[1], &sc[2], q, 1.0, nullptr, nullptr, r, cs);
+            if (e == cudaSuccess) e = pcg_dot(r, r, f64, N, part, &sc[3], cs);
+            if (e == cudaSuccess) e = host(&sc[3], &rr);
+            if (e != cudaSuccess) return KRON_ERR_CUDA;
+            ++done;
+            if (std::sqrt(rr) <= tol * bn || !std::isfinite(rr)) break;
+            st = precond(r, z);
+            if (st != KRON_OK) return st;
+            // p = z + (rz_new / rz) p
+            e = pcg_dot(r, z, f64, N, part, &sc[4], cs);
+            if (e == cudaSuccess) e = pcg_axpby(f64, N, 1.0, nullptr, nullptr, z, 1.0, &sc[4], &sc[1], p, cs);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(&sc[1], &sc[4], sizeof(double), cudaMemcpyDeviceToDevice, cs);
+            if (e != cudaSuccess) return KRON_ERR_CUDA;
+        }
+    }
+    if (iters) *iters = done;
+    if (relres) *relres = std::sqrt(rr) / bn;
     return KRON_OK;
 }
 

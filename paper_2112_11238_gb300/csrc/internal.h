@@ -134,6 +134,11 @@ cudaError_t expm_pade13_batch(int count, const int64_t *n, const double *const *
 // inv_workspace_bytes(n[i]) bytes each; the inverse (n x n, ld n, FP64) is
 // at inv_result(n[i], ws[i]).  P is FP64 (p64) or FP32 with leading dim ldP.
 size_t inv_workspace_bytes(int64_t n);
+// PCG vector kernels (pcg.cu): FP64 dot products in a fixed order, scaled updates
+cudaError_t pcg_dot(const void *x, const void *y, bool f64, int64_t n, double *partial, double *out, cudaStream_t st);
+cudaError_t pcg_axpby(bool f64, int64_t n, double a, const double *num, const double *den, const void *x, double b,
+                      const double *bnum, const double *bden, void *y, cudaStream_t st);
+size_t pcg_partial_doubles();
 double *inv_result(int64_t n, void *ws);
 cudaError_t inv_gj_batch(int count, const int64_t *n, const void *const *P, const int64_t *ldP, bool p64,
                          void *const *ws, cudaStream_t st);

@@ -1,0 +1,126 @@
+"""GPU parity of the Kronecker-sum PCG solver (matvec by kron_kronsumv, ADI
+preconditioner by kron_itucker; Section 3.4) and of the IMEX Euler run of the
+3-D semilinear problem of Section 4.5, against the FP64 oracle (exact solves by
+diagonalisation) and the values printed with Table 3."""
+import math
+import os
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_util import rel_err, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+RNG = np.random.default_rng(2026)
+
+
+@pytest.fixture(scope="module")
+def kron():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2112_11238_gb300 as k
+    return k
+
+
+def _golden():
+    path = os.path.join(os.path.dirname(__file__), "golden", "table3_semilinear.txt")
+    with open(path) as f:
+        row = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")][0]
+    return tuple(int(v) for v in row[:3]), float(row[3]), float(row[4]), float(row[5]), int(row[6]), int(row[7])
+
+
+@pytest.mark.parametrize("pre", [True, False])
+@pytest.mark.parametrize("n", [(5, 6, 7), (16, 9, 33), (40, 44, 48)])
+def test_pcg_matches_the_exact_solve(kron, n, pre):
+    import torch
+    c = W.semilinear(n=n, tau=0.01)
+    b = RNG.standard_normal(n)
+    ref = oracle.kronsum_solve_laplacian(b, n, c.tau)
+    X, it, rr = kron.kronsum_pcg([to_dev(m) for m in c.M], to_dev(b), Ps=[to_dev(p) for p in c.P] if pre else None,
+                                 tol=1e-10, maxit=2000)
+    assert rr <= 1e-10, (it, rr)
+    assert rel_err(to_host(X), ref) <= 1e-8
+    assert X.dtype == torch.float64
+    assert kron.device_error() == 0
+
+
+def test_pcg_edge_cases(kron):
+    import torch
+    c = W.semilinear(n=(4, 5, 6), tau=0.01)
+    M = [to_dev(m) for m in c.M]
+    P = [to_dev(p) for p in c.P]
+    zero = torch.zeros(c.n, dtype=torch.float64, device="cuda")
+    X, it, rr = kron.kronsum_pcg(M, zero, X0=to_dev(RNG.standard_normal(c.n)), Ps=P)
+    assert it == 0 and rr == 0.0 and float(X.abs().max()) == 0.0  # b = 0 gives x = 0
+    b = to_dev(RNG.standard_normal(c.n))
+    x0 = to_dev(RNG.standard_normal(c.n))
+    X, it, rr = kron.kronsum_pcg(M, b, X0=x0, Ps=P, maxit=0)
+    assert it == 0 and rr > 0.1 and bool(torch.equal(X, x0))  # no iteration: the guess comes back
+    # an exact initial guess needs no iteration
+    ref = to_dev(oracle.kronsum_solve_laplacian(to_host(b), c.n, c.tau))
+    X, it, rr = kron.kronsum_pcg(M, b, X0=ref, Ps=P, tol=1e-6)
+    assert it == 0 and rr <= 1e-6
+
+
+def test_pcg_float32_storage(kron):
+    import torch
+    c = W.semilinear(n=(16, 9, 33), tau=0.01)
+    b = RNG.standard_normal(c.n)
+    ref = oracle.kronsum_solve_laplacian(b, c.n, c.tau)
+    X, it, rr = kron.kronsum_pcg([to_dev(m).float() for m in c.M], to_dev(b).float(),
+                                 Ps=[to_dev(p).float() for p in c.P], tol=1e-6, maxit=100)
+    assert X.dtype == torch.float32 and rr <= 1e-6
+    assert rel_err(to_host(X), ref) <= 1e-5
+
+
+def _imex_gpu(kron, c, pre: bool, tol: float = 1e-5, maxit: int = 200):
+    """IMEX Euler of Section 4.5 on the GPU: the right-hand side
+    u_k + tau (1 / (1 + u_k^2) + Phi(t_k)) is the test's own elementwise
+    code; each system M u_{k+1} = rhs is solved by kron_kronsum_pcg from the
+    initial guess u_k (as the paper's pcg call)."""
+    import torch
+    U0, LU0 = to_dev(c.U0), to_dev(c.LU0)
+    M = [to_dev(m) for m in c.M]
+    P = [to_dev(p) for p in c.P] if pre else None
+    plan = kron.TuckerPlan(c.n, c.n, torch.float64, "fp64", natural_order=True)
+    ws = torch.empty(plan.pcg_workspace_bytes(pre), dtype=torch.uint8, device="cuda")
+    u = U0.clone()
+    iters = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(c.nsteps):
+        et = math.exp(k * c.tau)
+        phi = et * (U0 - LU0) - 1.0 / (1.0 + (et * U0) ** 2)
+        rhs = kron.colmajor(u + c.tau * (1.0 / (1.0 + u * u) + phi))
+        X = kron.colmajor(u.clone())
+        X, it, rr = plan.kronsum_pcg(M, rhs, X, P, tol, maxit, ws=ws)
+        assert rr <= tol
+        iters.append(it)
+        u = X
+    torch.cuda.synchronize()
+    return u, iters, time.perf_counter() - t0
+
+
+@pytest.mark.parametrize("pre", [True, False])
+def test_semilinear_imex_run(kron, pre):
+    n, tau, tstar, printed, cg_iters, pcg_iters = _golden()
+    c = W.semilinear(n=n, tau=tau, tstar=tstar)
+    u, iters, sec = _imex_gpu(kron, c, pre)
+    u = to_host(u)
+    ref = oracle.semilinear_imex(c)
+    ex = c.exact(tstar)
+    err = np.abs(u - ex).max() / np.abs(ex).max()
+    avg = sum(iters) / len(iters)
+    print(f"\nsemilinear n={n} {'PCG' if pre else 'CG'}: final rel err {err:.4e}, avg iterations {avg:.2f}, "
+          f"{sec:.3f} s for {c.nsteps} steps")
+    assert rel_err(u, ref) <= 1e-4          # the PCG tolerance (1e-5) per step, against exact solves
+    assert abs(err - printed) <= 0.1e-3     # Section 4.5: 9.7e-3
+    if pre:
+        assert avg <= 2 * pcg_iters         # Table 3: 2 iterations per step
+    else:
+        assert 0.6 * cg_iters <= avg <= 1.5 * cg_iters  # Table 3: 30 iterations per step
