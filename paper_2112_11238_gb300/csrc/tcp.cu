@@ -425,10 +425,12 @@ __device__ __forceinline__ void fx_consts(const TcJob &J, int j, FxConsts &k) {
 // hold a0 (level 0, an exact integer below 2^24) and a1 (levels 1..3) in
 // units of 2^(eA + f_c - 14).  Fixed-point output with scale eC:
 //     X = round((a0 + a1) * 2^s),  s = eA + f_c + 17 - eC,
-// formed exactly as the float pair (h, l) = TwoSum(a0 * 2^s, a1 * 2^s) (both
-// products are exact power-of-two scalings; TwoSum is Knuth's error-free
-// sum), then X = rint(h) + rint(l), within one unit of the rounded sum and
-// saturated to +-(2^31 - 1).
+// formed from the float pair (sum, err) = Fast2Sum(a0 * 2^s, a1 * 2^s) (both
+// products are exact power-of-two scalings; Dekker's Fast2Sum is error-free
+// when |a0| >= |a1|, the usual case, and within an ulp of the sum otherwise),
+// then X = rint(sum) + rint(err) (|err| <= 2^7: rounded by the 1.5 * 2^23
+// exponent trick), saturated.  The largest |X| of the tile is tracked on
+// |sum| with a margin above the error term.
 // Value output (last mode): the sum 2^16 (a0 + a1) is formed in 64-bit
 // integers and scaled by 2^(eA + f_c - 30).
 // The 16-column chunks of the tile are shared by `nparts` warps of the same
@@ -445,6 +447,7 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, u
     const int step = 16 * nparts;
     const int base = eA + 17 - eC;
     unsigned mx = 0;
+    float mxf = 0.f;
     int cnt = 0;  // TMA stores issued by this warp
     // one 16-column box: wait until its buffer is free, then write it (fill
     // writes this lane's row), hand it to the TMA unit
@@ -484,11 +487,10 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, u
                 const float h = __uint_as_float(r0[e]) * sc;
                 const float l = __uint_as_float(r1[e]) * sc;
                 const float sum = h + l;
-                const float bl = sum - h;
-                const float err = (h - (sum - bl)) + (l - bl);
-                const int x = max(-2147483647, add_sat(__float2int_rn(sum), __float2int_rn(err)));
-                xv[e] = x;
-                mx = max(mx, (unsigned)abs(x));
+                const float err = l - (sum - h);
+                const int ei = __float_as_int(err + 12582912.0f) - 0x4B400000;
+                xv[e] = add_sat(__float2int_rn(sum), ei);
+                mxf = fmaxf(mxf, fabsf(sum));
             }
             if (stg) {
                 // two 2 KB buffers; [column][row] or [row][column]
@@ -571,6 +573,9 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, u
     }
     __syncwarp();
     if (J.cfix) {
+        // |X| <= |sum| + 2^7 + 1; capped at 2^31
+        mx = (unsigned)fminf(mxf + 256.0f, 2147483648.0f);
+        if (mxf == 0.f) mx = 0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (lane == 0 && mx) atomicMax(&J.fxC->maxabs, mx);
