@@ -465,6 +465,135 @@ def roofline(kern, peaks, src, prec):
             "kernel_ms": kern["ms"]}
 
 
+# ------------------------------------------------- the other configurations
+
+def _timed(torch, fn, reps=10, flush=None):
+    """Median CUDA-event time (ms) of fn() with L2 flushed before each run."""
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        fn()
+        e.record()
+        torch.cuda.synchronize()
+        ts.append(s.elapsed_time(e))
+    return statistics.median(ts)
+
+
+def _line(name, prec, ms, flops, byts, peaks, mult=None):
+    """One JSON line: effective TFLOP/s, GB/s of the minimum bytes, and the
+    fraction of the bound (tensor pipe over `mult` products, or HBM) that the
+    smaller of the two times gives."""
+    t = ms * 1e-3
+    out = {"config": name, "prec": prec, "ms": ms, "tflops": flops / t / 1e12, "min_bytes": byts,
+           "gbs": byts / t / 1e9}
+    hbm_t = byts / (peaks["hbm_gbs"] * 1e9)
+    if mult:
+        pipe = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        if prec == "3xtf32":
+            pipe = pipe * NOMINAL["tf32"] / NOMINAL["bf16"]
+        tc_t = flops * mult / (pipe * 1e12)
+        bound_t, bound = (tc_t, "tensor") if tc_t >= hbm_t else (hbm_t, "hbm")
+    else:
+        bound_t, bound = hbm_t, "hbm"
+    out["roofline"] = {"bound": bound, "frac": bound_t / t}
+    print(json.dumps(out), flush=True)
+
+
+MULT = {"3xtf32": 3, "bf16x3": 3, "bf16x6": 6, "fx32": 10}
+
+
+def run_configs(args):
+    """Times every configuration of the survey's measurement table through
+    the public API (CUDA events, L2 flushed before each run), plus the next
+    rows at the stepper's size.  One JSON line each; not the headline."""
+    import torch
+    import paper_2112_11238_gb300 as kron
+    dev = torch.device("cuda", 0)
+    peaks, _ = load_peaks()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    # cfg1: Tucker d=3, n = m = 100, FP64 storage
+    c = W.tucker_d3()
+    T = kron.colmajor(torch.from_numpy(c.T).to(dev))
+    Ls = [kron.colmajor(torch.from_numpy(L).to(dev)) for L in c.L]
+    fl = W.tucker_flops([100] * 3, [100] * 3)
+    for prec in ("fp64", "fp32", "3xtf32", "bf16x6", "fx32"):
+        plan = kron.TuckerPlan(T.shape, [100] * 3, torch.float64, prec)
+        ws = plan.workspace(dev)
+        S = kron.empty_colmajor([100] * 3, torch.float64, dev)
+        ms = _timed(torch, lambda: plan.tucker_into(T, Ls, S, ws=ws), flush=flush)
+        _line("tucker d=3 n=m=100 f64 storage", prec, ms, fl, 2 * 8e6 + 3 * 8e4, peaks, MULT.get(prec))
+    del T, Ls
+
+    # cfg3: Tucker d=6, n = m = 20 (64M elements), FP32 storage
+    c = W.tucker_d6()
+    T = kron.colmajor(torch.from_numpy(c.T).float().to(dev))
+    Ls = [kron.colmajor(torch.from_numpy(L).float().to(dev)) for L in c.L]
+    fl = W.tucker_flops([20] * 6, [20] * 6)
+    for prec in ("fp32", "3xtf32", "bf16x3", "bf16x6", "fx32"):
+        plan = kron.TuckerPlan(T.shape, [20] * 6, torch.float32, prec)
+        ws = plan.workspace(dev)
+        S = kron.empty_colmajor([20] * 6, torch.float32, dev)
+        ms = _timed(torch, lambda: plan.tucker_into(T, Ls, S, ws=ws), flush=flush)
+        _line("tucker d=6 n=m=20 f32 storage", prec, ms, fl, 2 * 4 * 20.0 ** 6, peaks, MULT.get(prec))
+    del T, Ls, S, ws
+
+    # cfg4: 512 batched d=3 interpolation problems, FP32
+    c = W.batched()
+    Ts = [kron.colmajor(torch.from_numpy(t).float().to(dev)) for t in c.T]
+    Lb = [[kron.colmajor(torch.from_numpy(L).float().to(dev)) for L in row] for row in c.L]
+    Ss = [kron.empty_colmajor(tuple(int(v) for v in c.n[b]), torch.float32, dev) for b in range(len(Ts))]
+    byts = 4.0 * (sum(int(np.prod(c.m[b])) + int(np.prod(c.n[b])) for b in range(len(Ts))))
+    for prec in ("3xtf32", "bf16x3", "bf16x6"):
+        plan = kron.BatchedPlan(c.m, c.n, torch.float32, prec)
+        ws = plan.workspace(dev)
+        plan.bind(Ts, Lb, Ss, ws)
+        ms = _timed(torch, lambda: plan.run(ws), flush=flush)
+        _line("batched 512 x d=3, m in [8,64], n = ceil(1.5 m), f32", prec, ms, plan.flops(), byts, peaks,
+              MULT.get(prec))
+    del Ts, Lb, Ss
+
+    # cfg5: adjoint d=4, n = m = 48, FP32: forward + backward through the autograd function
+    c, target = W.adjoint()
+    T = kron.colmajor(torch.from_numpy(c.T).float().to(dev)).requires_grad_(True)
+    Ls = [kron.colmajor(torch.from_numpy(L).float().to(dev)).requires_grad_(True) for L in c.L]
+    tgt = kron.colmajor(torch.from_numpy(target).float().to(dev))
+    fl_f = W.tucker_flops([48] * 4, [48] * 4)
+    for prec in ("3xtf32", "bf16x6"):
+        def fwd_bwd():
+            S = kron.tucker_autograd(T, Ls, prec=prec)
+            ((S - tgt) ** 2).sum().mul(0.5).backward()
+        ms = _timed(torch, fwd_bwd, flush=flush)
+        _line("adjoint d=4 n=m=48 f32, forward + backward", prec, ms, fl_f * (1 + 7.1e9 / 2.04e9),
+              4 * 4 * 48.0 ** 4, peaks, MULT.get(prec))
+    del T, Ls, tgt
+
+    # next rows at the stepper's size: Kronecker-sum action and inverse Tucker, 256^3 FP64
+    st = W.stepper(n=N, tau=TAU, nsteps=NSTEPS, with_u0=False)
+    V = kron.empty_colmajor([N] * D, torch.float64, dev)
+    V.normal_()
+    A = [kron.colmajor(torch.from_numpy(np.asfortranarray(a)).to(dev)) for a in st.A]
+    Ps = [kron.colmajor((torch.eye(N, dtype=torch.float64, device=dev) - TAU * a)) for a in A]
+    S = kron.empty_colmajor([N] * D, torch.float64, dev)
+    fl = D * 2.0 * N ** (D + 1)
+    for prec in ("fp64", "fx32", "3xtf32"):
+        plan = kron.TuckerPlan([N] * D, [N] * D, torch.float64, prec, natural_order=True)
+        ws = torch.empty(plan.kronsumv_workspace_bytes(), dtype=torch.uint8, device=dev)
+        ms = _timed(torch, lambda: plan.kronsumv_into(V, A, S, ws=ws), reps=5, flush=flush)
+        _line("kronsumv 256^3 f64 storage", prec, ms, fl, (D + 1 + D - 1) * 8.0 * N ** D, peaks, MULT.get(prec))
+        ws = torch.empty(plan.itucker_workspace_bytes(0), dtype=torch.uint8, device=dev)
+        ms = _timed(torch, lambda: plan.itucker_into(V, Ps, S, 0, ws=ws), reps=5, flush=flush)
+        _line("itucker 256^3 f64 storage (inverses included)", prec, ms, fl, 2 * 8.0 * N ** D, peaks,
+              MULT.get(prec))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -476,9 +605,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-only", action="store_true",
                     help="run only the dominant kernel (256^3 mode products) a few times, for profilers")
+    ap.add_argument("--configs", action="store_true",
+                    help="time the other configurations and the next rows (one JSON line each)")
     args = ap.parse_args()
     if args.kernel_only:
         return run_kernel_only(args)
+    if args.configs:
+        return run_configs(args)
     if args.warmup < 3 and args.impl == "kron":
         args.warmup = 3
     if args.impl == "reference":
