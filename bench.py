@@ -41,7 +41,7 @@ FLOPS_PER_STEP = NSTEPS * FLOPS_PER_TSTEP           # one benchmark step
 WORKLOAD = "expkronsum stepper d=3 n=256 tau=1e-4 100 steps, FP64 state, FD Laplacian + advection 0.5"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # GB300 nominal dense tensor rates (PFLOP/s), used only as ratios between dtypes
-NOMINAL = {"bf16": 2.25, "tf32": 1.1}
+NOMINAL = {"bf16": 2.25, "tf32": 1.1, "fp64": 0.00125}
 
 
 def dist_env():
@@ -493,6 +493,13 @@ def _line(name, prec, ms, flops, byts, peaks, mult=None):
     out = {"config": name, "prec": prec, "ms": ms, "tflops": flops / t / 1e12, "min_bytes": byts,
            "gbs": byts / t / 1e9}
     hbm_t = byts / (peaks["hbm_gbs"] * 1e9)
+    if prec == "fp64":
+        # CUDA-core FP64: GB300's nominal 1.25 TFLOP/s (no measured FP64 peak in the peaks file)
+        fp_t = flops / (NOMINAL["fp64"] * 1e15)
+        bound_t, bound = (fp_t, "fp64 (nominal)") if fp_t >= hbm_t else (hbm_t, "hbm")
+        out["roofline"] = {"bound": bound, "frac": bound_t / t}
+        print(json.dumps(out), flush=True)
+        return
     if mult:
         pipe = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
         if prec == "3xtf32":
