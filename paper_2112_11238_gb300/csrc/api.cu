@@ -1061,6 +1061,7 @@ namespace {
 struct StepLayout {
     size_t expm, expm_each, E[KRON_MAX_D], img[KRON_MAX_D], st[2], stbytes, total;
     size_t fxf[KRON_MAX_D], fxg[KRON_MAX_D], fxsc;  // fixed-point form
+    size_t imgh[KRON_MAX_D];                        // fixed point: half-width images (tail tiles)
 };
 
 StepLayout step_layout(const kron_plan_s *pl) {
@@ -1091,6 +1092,9 @@ StepLayout step_layout(const kron_plan_s *pl) {
             off += align_up((size_t)pl->n[k] * sizeof(int));
             s.fxg[k] = off;
             off += kAlign;
+            s.imgh[k] = off;
+            const int bn = tc_tile_n(kFX32, pl->n[k]);
+            if (bn % 32 == 0) off += align_up(tc_bimage_bytes_bn(kFX32, pl->n[k], pl->n[k], bn / 2));
         }
         s.fxsc = off;
         off += kAlign;
@@ -1116,6 +1120,12 @@ kron_status run_steps_fx(const kron_plan_s *pl, const double *const *E, const in
         if (fx_build_bimage(c, w + lay.img[k], reinterpret_cast<int *>(w + lay.fxf[k]),
                             reinterpret_cast<unsigned long long *>(w + lay.fxg[k]), cs) != cudaSuccess)
             return KRON_ERR_CUDA;
+        // half-width image for the tail tiles (same row exponents and bound)
+        const int bn = tc_tile_n(kFX32, pl->n[k]);
+        if (bn % 32 == 0 &&
+            fx_build_bimage_bn(c, w + lay.imgh[k], reinterpret_cast<int *>(w + lay.fxf[k]),
+                               reinterpret_cast<unsigned long long *>(w + lay.fxg[k]), bn / 2, cs) != cudaSuccess)
+            return KRON_ERR_CUDA;
     }
     const int64_t N = prod(pl->n, 0, d);
     if (fx_from_float(U, io64, N, reinterpret_cast<int32_t *>(w + lay.st[0]), &sc[0], scratch, cs) != cudaSuccess)
@@ -1131,9 +1141,11 @@ kron_status run_steps_fx(const kron_plan_s *pl, const double *const *E, const in
             Contraction c = tc_mode_contraction(g, w + lay.st[cur], false, E[mu], true, ldE[mu], false, dst,
                                                 last ? io64 : false);
             cudaError_t e = sdst ? fx_reset(sdst, cs) : cudaSuccess;
+            const bool half = tc_tile_n(kFX32, pl->n[mu]) % 32 == 0;
             if (e == cudaSuccess)
-                e = tcp_contract_fx(c, w + lay.img[mu], &sc[cur], reinterpret_cast<const int *>(w + lay.fxf[mu]),
-                                    reinterpret_cast<const unsigned long long *>(w + lay.fxg[mu]), sdst, cs);
+                e = tcp_contract_fx_tail(c, w + lay.img[mu], half ? w + lay.imgh[mu] : nullptr, &sc[cur],
+                                         reinterpret_cast<const int *>(w + lay.fxf[mu]),
+                                         reinterpret_cast<const unsigned long long *>(w + lay.fxg[mu]), sdst, cs);
             if (e != cudaSuccess) return KRON_ERR_CUDA;
             cur ^= 1;
         }

@@ -156,6 +156,11 @@ cudaError_t fx_reset(FxScale *s, cudaStream_t st) {
 }
 
 cudaError_t fx_build_bimage(const Contraction &c, void *img, int *f, unsigned long long *g, cudaStream_t st) {
+    return fx_build_bimage_bn(c, img, f, g, tc_tile_n(kFX32, c.N), st);
+}
+
+cudaError_t fx_build_bimage_bn(const Contraction &c, void *img, int *f, unsigned long long *g, int bn,
+                               cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(g, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     const unsigned rows_blocks = (unsigned)((c.N + 7) / 8);
@@ -165,7 +170,6 @@ cudaError_t fx_build_bimage(const Contraction &c, void *img, int *f, unsigned lo
         fx_rows_kernel<float><<<rows_blocks, 256, 0, st>>>(static_cast<const float *>(c.B), c.colB, c.kB, c.N, c.K, f, g);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int bn = tc_tile_n(kFX32, c.N);
     const int64_t nt = (c.N + bn - 1) / bn;
     const int64_t kb = (c.K + kRowBytes / 2 - 1) / (kRowBytes / 2);
     const int64_t total = nt * kb * bn * kChunks;

@@ -65,6 +65,8 @@ struct FxScale {
 // ---- tensor-core path (tc.cu) ----
 // Bytes of the pre-split, pre-swizzled image of an (N x K) B operand.
 size_t tc_bimage_bytes(int form, int64_t N, int64_t K);
+// the same for an explicit N-tile width bn
+size_t tc_bimage_bytes_bn(int form, int64_t N, int64_t K, int bn);
 // N-tile width the tensor-core kernels use for a given N.
 int tc_tile_n(int form, int64_t N);
 // Writes the image of B (given as a Contraction's B side: colB/kB maps over
@@ -91,6 +93,15 @@ cudaError_t tcp_contract_fx(const Contraction &c, const void *img, const FxScale
 // Image of op(L) for the FX32 form (same layout as tc_build_bimage, four
 // slices), per-row exponents f[N] and the row-sum bound *g (zeroed here).
 cudaError_t fx_build_bimage(const Contraction &c, void *img, int *f, unsigned long long *g, cudaStream_t st);
+// the same image for N-tiles of width bn (the tail tiles of tcp_contract_fx_tail)
+cudaError_t fx_build_bimage_bn(const Contraction &c, void *img, int *f, unsigned long long *g, int bn,
+                               cudaStream_t st);
+// tcp_contract_fx with the last, partial round of tiles split into tiles of
+// half the width (second image img_half, tiles of width tc_tile_n / 2), so
+// that it takes about half a tile's time; one launch.  Falls back to
+// tcp_contract_fx when the split does not apply.
+cudaError_t tcp_contract_fx_tail(const Contraction &c, const void *img, const void *img_half, const FxScale *fxA,
+                                 const int *fxF, const unsigned long long *fxG, FxScale *fxC, cudaStream_t st);
 // Dense FP64/FP32 tensor of `count` elements -> 32-bit fixed point X with
 // one scale (written to *s); `scratch` is 8 bytes of device memory.
 cudaError_t fx_from_float(const void *src, bool src64, int64_t count, int32_t *X, FxScale *s,

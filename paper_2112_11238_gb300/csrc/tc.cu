@@ -396,8 +396,9 @@ int tc_tile_n(int form, int64_t N) {
     return (int)std::max<int64_t>(bn, 16);
 }
 
-size_t tc_bimage_bytes(int form, int64_t N, int64_t K) {
-    const int bn = tc_tile_n(form, N);
+size_t tc_bimage_bytes(int form, int64_t N, int64_t K) { return tc_bimage_bytes_bn(form, N, K, tc_tile_n(form, N)); }
+
+size_t tc_bimage_bytes_bn(int form, int64_t N, int64_t K, int bn) {
     const int64_t nt = (N + bn - 1) / bn;
     const int64_t kb = (K + bk_of(form) - 1) / bk_of(form);
     return (size_t)(nt * kb * pieces_of(form)) * bn * kRowBytes;

@@ -77,7 +77,7 @@ constexpr int kRowBytes = 64;       // bytes of one K-major row per K-block (64-
 constexpr int kChunks = kRowBytes / 16;  // 16-byte chunks per row
 constexpr int kBM = 128;            // rows per tile (MMA M)
 
-__device__ __forceinline__ int64_t imap(const IdxMap &m, int64_t x) {
+__host__ __device__ __forceinline__ int64_t imap(const IdxMap &m, int64_t x) {
     if (m.R0 == 0) return x * m.s0;
     return (x % m.R0) * m.s0 + (x / m.R0) * m.s1;
 }

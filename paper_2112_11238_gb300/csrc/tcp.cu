@@ -898,7 +898,7 @@ static int bk_of_f(int form) { return form == kTF32x3 ? kRowBytes / 4 : kRowByte
 size_t tcp_job_bytes() { return sizeof(TcJob); }
 
 // Fills a job for contraction c (B side from `img`, built with tcp_tile_n).
-static TcJob make_job(int form, const Contraction &c, const void *img) {
+static TcJob make_job(int form, const Contraction &c, const void *img, int bn = 0) {
     TcJob J{};
     J.A = c.A;
     J.rowA = c.rowA;
@@ -914,7 +914,7 @@ static TcJob make_job(int form, const Contraction &c, const void *img) {
     J.kb_img = (c.K + bk - 1) / bk;
     J.kb0 = 0;
     J.nkb = (int32_t)J.kb_img;
-    J.BN = tc_tile_n(form, c.N);
+    J.BN = bn > 0 ? bn : tc_tile_n(form, c.N);
     J.tiles_m = (int32_t)((c.M + kBM - 1) / kBM);
     J.tiles_n = (int32_t)((c.N + J.BN - 1) / J.BN);
     J.dep = -1;
@@ -1149,6 +1149,53 @@ cudaError_t tcp_contract_fx(const Contraction &c, const void *img, const FxScale
     setup_tmc(J, c);
     const int tiles = J.tiles_m * J.tiles_n;
     return tcp_launch(kFX32, &J, 1, tiles, J.BN, J.nkb, nullptr, nullptr, st);
+}
+
+// Rows r0..M-1 of a row map are the same map shifted by imap(m, r0): one
+// level, one slab holding all M rows, or r0 on a slab boundary.
+static bool shifts_at(const IdxMap &m, int64_t r0, int64_t M) { return m.R0 == 0 || M <= m.R0 || r0 % m.R0 == 0; }
+
+cudaError_t tcp_contract_fx_tail(const Contraction &c, const void *img, const void *img_half, const FxScale *fxA,
+                                 const int *fxF, const unsigned long long *fxG, FxScale *fxC, cudaStream_t st) {
+    if (c.M == 0 || c.N == 0) return cudaSuccess;
+    TcJob J = make_job(kFX32, c, img);
+    const int tiles = J.tiles_m * J.tiles_n;
+    const int grid = num_sms();
+    const int tail = tiles % grid;
+    const int64_t R1 = (int64_t)(tiles - tail) * kBM;
+    const bool split = img_half != nullptr && J.tiles_n == 1 && J.BN % 32 == 0 && tiles > grid && tail > 0 &&
+                       2 * tail <= grid && !c.A_f64 && shifts_at(c.rowA, R1, c.M) && shifts_at(c.rowC, R1, c.M);
+    if (!split) return tcp_contract_fx(c, img, fxA, fxF, fxG, fxC, st);
+    // job 0: the full rounds
+    J.M = R1;
+    J.tiles_m = tiles - tail;
+    J.fxA = fxA;
+    J.fxF = fxF;
+    J.fxG = fxG;
+    J.fxC = fxC;
+    J.cfix = fxC != nullptr;
+    J.a64 = 0;
+    J.tile_begin = 0;
+    setup_tma(kFX32, J, c);
+    setup_tmc(J, c);
+    // job 1: the remaining rows in tiles of half the width
+    Contraction cb = c;
+    cb.M = c.M - R1;
+    cb.A = static_cast<const int32_t *>(c.A) + imap(c.rowA, R1);
+    const size_t esC = c.C_f64 ? 8 : 4;  // FX32 output: int32 or a value tensor (FP32 / FP64)
+    cb.C = static_cast<uint8_t *>(c.C) + (size_t)imap(c.rowC, R1) * esC;
+    TcJob H = make_job(kFX32, cb, img_half, J.BN / 2);
+    H.fxA = fxA;
+    H.fxF = fxF;
+    H.fxG = fxG;
+    H.fxC = fxC;
+    H.cfix = fxC != nullptr;
+    H.a64 = 0;
+    H.tile_begin = J.tiles_m * J.tiles_n;
+    setup_tma(kFX32, H, cb);
+    setup_tmc(H, cb);
+    TcJob jobs[2] = {J, H};
+    return tcp_launch(kFX32, jobs, 2, H.tile_begin + H.tiles_m * H.tiles_n, J.BN, J.nkb, nullptr, nullptr, st);
 }
 
 // One contraction with the B side from an image built by tc_build_bimage.
