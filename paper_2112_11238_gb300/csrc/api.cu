@@ -1112,8 +1112,11 @@ kron_status run_steps_fx(const kron_plan_s *pl, const double *const *E, const in
     const bool io64 = pl->dtype == KRON_F64;
     const int total = nsteps * d;
     if (total == 0) return KRON_OK;
-    FxScale *sc = reinterpret_cast<FxScale *>(w + lay.fxsc);  // [0], [1]: state buffers
-    auto *scratch = reinterpret_cast<unsigned long long *>(sc + 2);
+    // three rotating scale words: product k reads sc[k % 3] and writes
+    // sc[(k + 1) % 3], and clears sc[(k + 2) % 3] for product k + 1 once the
+    // launches before it are complete (no memset between the launches)
+    FxScale *sc = reinterpret_cast<FxScale *>(w + lay.fxsc);
+    auto *scratch = reinterpret_cast<unsigned long long *>(sc + 3);
     for (int k = 0; k < d; ++k) {
         const ModeGeom g{1, 1, pl->n[k], pl->n[k]};
         Contraction c = tc_mode_contraction(g, nullptr, false, E[k], true, ldE[k], false, nullptr, false);
@@ -1130,6 +1133,7 @@ kron_status run_steps_fx(const kron_plan_s *pl, const double *const *E, const in
     const int64_t N = prod(pl->n, 0, d);
     if (fx_from_float(U, io64, N, reinterpret_cast<int32_t *>(w + lay.st[0]), &sc[0], scratch, cs) != cudaSuccess)
         return KRON_ERR_CUDA;
+    if (fx_reset(&sc[1], cs) != cudaSuccess) return KRON_ERR_CUDA;
     int cur = 0, idx = 0;
     for (int s = 0; s < nsteps; ++s) {
         for (int j = 0; j < d; ++j, ++idx) {
@@ -1137,15 +1141,15 @@ kron_status run_steps_fx(const kron_plan_s *pl, const double *const *E, const in
             const ModeGeom g = mode_geom(d, pl->n, mu, pl->n[mu]);
             const bool last = (idx == total - 1);
             void *dst = last ? U : (void *)(w + lay.st[cur ^ 1]);
-            FxScale *sdst = last ? nullptr : &sc[cur ^ 1];
+            FxScale *sdst = last ? nullptr : &sc[(idx + 1) % 3];
+            FxScale *snext = (idx + 2 < total) ? &sc[(idx + 2) % 3] : nullptr;
             Contraction c = tc_mode_contraction(g, w + lay.st[cur], false, E[mu], true, ldE[mu], false, dst,
                                                 last ? io64 : false);
-            cudaError_t e = sdst ? fx_reset(sdst, cs) : cudaSuccess;
             const bool half = tc_tile_n(kFX32, pl->n[mu]) % 32 == 0;
-            if (e == cudaSuccess)
-                e = tcp_contract_fx_tail(c, w + lay.img[mu], half ? w + lay.imgh[mu] : nullptr, &sc[cur],
-                                         reinterpret_cast<const int *>(w + lay.fxf[mu]),
-                                         reinterpret_cast<const unsigned long long *>(w + lay.fxg[mu]), sdst, cs);
+            const cudaError_t e =
+                tcp_contract_fx_tail(c, w + lay.img[mu], half ? w + lay.imgh[mu] : nullptr, &sc[idx % 3],
+                                     reinterpret_cast<const int *>(w + lay.fxf[mu]),
+                                     reinterpret_cast<const unsigned long long *>(w + lay.fxg[mu]), sdst, snext, cs);
             if (e != cudaSuccess) return KRON_ERR_CUDA;
             cur ^= 1;
         }

@@ -86,8 +86,12 @@ cudaError_t tcp_contract(int form, const Contraction &c, const void *img, cudaSt
 // One fixed-point contraction (FX32): A 32-bit fixed point (scale fxA), B
 // from an image made by fx_build_bimage (row exponents fxF, row-sum bound
 // fxG); C 32-bit fixed point with scale fxC, or values when fxC is null.
+// reset_next: a scale word that the launch clears once the launches before it
+// are complete (the output scale of the next fixed-point product; launches are
+// programmatic dependent launches, so no memset may sit between them).
 cudaError_t tcp_contract_fx(const Contraction &c, const void *img, const FxScale *fxA, const int *fxF,
-                            const unsigned long long *fxG, FxScale *fxC, cudaStream_t st);
+                            const unsigned long long *fxG, FxScale *fxC, cudaStream_t st,
+                            FxScale *reset_next = nullptr);
 
 // ---- fixed-point helpers (fx.cu) ----
 // Image of op(L) for the FX32 form (same layout as tc_build_bimage, four
@@ -101,7 +105,8 @@ cudaError_t fx_build_bimage_bn(const Contraction &c, void *img, int *f, unsigned
 // that it takes about half a tile's time; one launch.  Falls back to
 // tcp_contract_fx when the split does not apply.
 cudaError_t tcp_contract_fx_tail(const Contraction &c, const void *img, const void *img_half, const FxScale *fxA,
-                                 const int *fxF, const unsigned long long *fxG, FxScale *fxC, cudaStream_t st);
+                                 const int *fxF, const unsigned long long *fxG, FxScale *fxC, FxScale *reset_next,
+                                 cudaStream_t st);
 // Dense FP64/FP32 tensor of `count` elements -> 32-bit fixed point X with
 // one scale (written to *s); `scratch` is 8 bytes of device memory.
 cudaError_t fx_from_float(const void *src, bool src64, int64_t count, int32_t *X, FxScale *s,

@@ -86,6 +86,7 @@ struct TcLaunch {
     const TcJob *jobs;      // device table (when njobs > kMaxInline)
     int njobs, total_tiles;
     int *done;              // finished tiles per job (zeroed before the launch)
+    FxScale *reset_next;    // fixed point: scale word the next launch writes, cleared here
     int stages, nacc, nbuf, acc_cols, bn_max;
 };
 
@@ -641,6 +642,10 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
     uint32_t *tslot = reinterpret_cast<uint32_t *>(rfull + RawCfg<F>::STAGES);
     constexpr int RG = Regions<F>::N;
     uint32_t ncols = ACOLS * (uint32_t)RG * (uint32_t)NACC * (uint32_t)NBUF;
+    // programmatic dependent launch: the next launch may be scheduled now (it
+    // gets an SM as soon as a CTA of this one exits) and runs its prologue
+    // while this one finishes
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     ncols = ncols <= 32 ? 32u : (ncols <= 64 ? 64u : (ncols <= 128 ? 128u : (ncols <= 256 ? 256u : 512u)));
 
     // one accumulator buffer (fixed point, 256-column tiles): the converter
@@ -671,6 +676,12 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
+    // everything below may read what earlier launches wrote
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (L.reset_next && blockIdx.x == 0 && threadIdx.x == 0) {
+        L.reset_next->maxabs = 0u;
+        L.reset_next->e = 0;
+    }
 
     if (warp == 0) {
         // ---------------------------------------------- op(L) image producer
@@ -1084,8 +1095,17 @@ static cudaError_t launch_f(const TcLaunch &L, int grid, size_t smem, cudaStream
         attr = cudaFuncSetAttribute(tcp_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
     });
     if (attr != cudaSuccess) return attr;
-    tcp_kernel<F><<<grid, kPThreads, smem, st>>>(L);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)kPThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, tcp_kernel<F>, L);
 }
 
 static int num_sms() {
@@ -1103,13 +1123,14 @@ static int num_sms() {
 // device copy of the jobs when there are more than kMaxInline of them;
 // `done` holds one int per job, zeroed here.
 static cudaError_t tcp_launch(int form, const TcJob *jobs, int njobs, int total_tiles, int bn_max, int nkb_max,
-                              const void *table, int *done, cudaStream_t st) {
+                              const void *table, int *done, cudaStream_t st, FxScale *reset_next = nullptr) {
     if (total_tiles <= 0) return cudaSuccess;
     TcLaunch L;
     std::memset(&L, 0, sizeof(L));
     L.njobs = njobs;
     L.total_tiles = total_tiles;
     L.done = done;
+    L.reset_next = reset_next;
     if (njobs <= kMaxInline)
         for (int j = 0; j < njobs; ++j) L.inl[j] = jobs[j];
     else
@@ -1135,7 +1156,7 @@ static cudaError_t tcp_launch(int form, const TcJob *jobs, int njobs, int total_
 // image of op(L) comes with its row exponents and row-sum bound; C is fixed
 // point with scale fxC (cfix) or a value tensor.
 cudaError_t tcp_contract_fx(const Contraction &c, const void *img, const FxScale *fxA, const int *fxF,
-                            const unsigned long long *fxG, FxScale *fxC, cudaStream_t st) {
+                            const unsigned long long *fxG, FxScale *fxC, cudaStream_t st, FxScale *reset_next) {
     if (c.M == 0 || c.N == 0) return cudaSuccess;
     TcJob J = make_job(kFX32, c, img);
     J.fxA = fxA;
@@ -1148,7 +1169,7 @@ cudaError_t tcp_contract_fx(const Contraction &c, const void *img, const FxScale
     setup_tma(kFX32, J, c);
     setup_tmc(J, c);
     const int tiles = J.tiles_m * J.tiles_n;
-    return tcp_launch(kFX32, &J, 1, tiles, J.BN, J.nkb, nullptr, nullptr, st);
+    return tcp_launch(kFX32, &J, 1, tiles, J.BN, J.nkb, nullptr, nullptr, st, reset_next);
 }
 
 // Rows r0..M-1 of a row map are the same map shifted by imap(m, r0): one
@@ -1156,7 +1177,8 @@ cudaError_t tcp_contract_fx(const Contraction &c, const void *img, const FxScale
 static bool shifts_at(const IdxMap &m, int64_t r0, int64_t M) { return m.R0 == 0 || M <= m.R0 || r0 % m.R0 == 0; }
 
 cudaError_t tcp_contract_fx_tail(const Contraction &c, const void *img, const void *img_half, const FxScale *fxA,
-                                 const int *fxF, const unsigned long long *fxG, FxScale *fxC, cudaStream_t st) {
+                                 const int *fxF, const unsigned long long *fxG, FxScale *fxC, FxScale *reset_next,
+                                 cudaStream_t st) {
     if (c.M == 0 || c.N == 0) return cudaSuccess;
     TcJob J = make_job(kFX32, c, img);
     const int tiles = J.tiles_m * J.tiles_n;
@@ -1165,7 +1187,7 @@ cudaError_t tcp_contract_fx_tail(const Contraction &c, const void *img, const vo
     const int64_t R1 = (int64_t)(tiles - tail) * kBM;
     const bool split = img_half != nullptr && J.tiles_n == 1 && J.BN % 32 == 0 && tiles > grid && tail > 0 &&
                        2 * tail <= grid && !c.A_f64 && shifts_at(c.rowA, R1, c.M) && shifts_at(c.rowC, R1, c.M);
-    if (!split) return tcp_contract_fx(c, img, fxA, fxF, fxG, fxC, st);
+    if (!split) return tcp_contract_fx(c, img, fxA, fxF, fxG, fxC, st, reset_next);
     // job 0: the full rounds
     J.M = R1;
     J.tiles_m = tiles - tail;
@@ -1195,7 +1217,8 @@ cudaError_t tcp_contract_fx_tail(const Contraction &c, const void *img, const vo
     setup_tma(kFX32, H, cb);
     setup_tmc(H, cb);
     TcJob jobs[2] = {J, H};
-    return tcp_launch(kFX32, jobs, 2, H.tile_begin + H.tiles_m * H.tiles_n, J.BN, J.nkb, nullptr, nullptr, st);
+    return tcp_launch(kFX32, jobs, 2, H.tile_begin + H.tiles_m * H.tiles_n, J.BN, J.nkb, nullptr, nullptr, st,
+                      reset_next);
 }
 
 // One contraction with the B side from an image built by tc_build_bimage.
