@@ -42,6 +42,7 @@ WORKLOAD = "expkronsum stepper d=3 n=256 tau=1e-4 100 steps, FP64 state, FD Lapl
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # GB300 nominal dense tensor rates (PFLOP/s), used only as ratios between dtypes
 NOMINAL = {"bf16": 2.25, "tf32": 1.1, "fp64": 0.00125}
+FX_FORMS = ("fx32", "fx32h")                          # fixed-point forms of the stepper
 
 
 def dist_env():
@@ -75,10 +76,10 @@ def whole_job_value(world, ms_per_step):
 
 
 def launches_per_step(prec):
-    """Our kernels per stepper call: one launch for the exponentials; for FX32
-    two per mode for the sliced image of E_mu, two for the conversion of U to
-    fixed point, then one per mode product."""
-    if prec == "fx32":
+    """Our kernels per stepper call: one launch for the exponentials; for the
+    fixed-point forms two per mode for the sliced image of E_mu, two for the
+    conversion of U to fixed point, then one per mode product."""
+    if prec in FX_FORMS:
         return 1 + 2 * D + 2 + NSTEPS * D
     return 1 + D + NSTEPS * D
 
@@ -282,7 +283,7 @@ def run_gpu(args):
     rel = float((U_split - U64).abs().max() / U64.abs().max())
     # the FP32-accumulating split forms on the same inputs, for comparison
     others = {}
-    for p in ("3xtf32", "bf16x6"):
+    for p in ("fx32", "fx32h", "3xtf32", "bf16x6"):
         if p == prec:
             continue
         o = StepperFP64(kron, torch, dev, A, U_init, prec=p)
@@ -297,10 +298,13 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"3xtf32": "tf32x3/f32acc", "bf16x6": "bf16x6/f32acc",
                                            "bf16x3": "bf16x3/f32acc",
-                                           "fx32": "i32 fixed point, bf16 digit slices, exact acc"}.get(prec, prec),
+                                           "fx32": "i32 fixed point, bf16 digit slices, exact acc",
+                                           "fx32h": "i32 (29-bit) fixed point, f16 digit slices, exact acc"
+                                           }.get(prec, prec),
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "prec": prec,
-                       "state": "f64 in/out, " + ("32-bit fixed point" if prec == "fx32" else "f32") + " between modes",
+                       "state": "f64 in/out, " + ("32-bit fixed point" if prec in FX_FORMS else "f32")
+                                + " between modes",
                        "l2": "flushed between timed steps (512 MiB write); U is 134 MB FP64"},
             "rel_err_vs_fp64_gpu": rel,
             "fp64_path": {"ms_per_step": fp64_ms, "value": FLOPS_PER_STEP / (fp64_ms * 1e-3) / 1e12,
@@ -352,8 +356,8 @@ def time_mode_product(kron, torch, dev, prec, args):
     X.normal_()
     E = torch.randn(N, N, dtype=torch.float32, device=dev)
     Y = kron.empty_colmajor([N] * D, torch.float32, dev)
-    if prec == "fx32":
-        return {"ms": time_fx_mode_product(kron, torch, dev, X, E, Y, mu), "mu": mu}
+    if prec in FX_FORMS:
+        return {"ms": time_fx_mode_product(kron, torch, dev, X, E, Y, mu, prec), "mu": mu}
     # the 1 GiB flush keeps the GPU busy while the host enqueues the events
     # and the launch, so no host latency lands between the two events
     flush = torch.empty(1024 * 1024 * 1024, dtype=torch.uint8, device=dev)
@@ -372,10 +376,10 @@ def time_mode_product(kron, torch, dev, prec, args):
     return {"ms": statistics.median(ts), "mu": mu}
 
 
-def time_fx_mode_product(kron, torch, dev, X, E, Y, mu):
-    """The fixed-point form's mode product on a 256^3 fixed-point state, as
-    the stepper runs it (state and output 32-bit fixed point)."""
-    plan = kron.StepperPlan([N] * D, torch.float32, "fx32")
+def time_fx_mode_product(kron, torch, dev, X, E, Y, mu, prec):
+    """A fixed-point form's mode product on a 256^3 fixed-point state, as
+    the stepper runs it (state and output 32-bit integers)."""
+    plan = kron.StepperPlan([N] * D, torch.float32, prec)
     ws = plan.workspace(dev)
     U = kron.empty_colmajor([N] * D, torch.float32, dev)
     U.copy_(X)
@@ -409,8 +413,8 @@ def run_kernel_only(args):
 
 
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
-# capture of `bench.py --kernel-only --prec fx32` (the summary and its command
-# are in profiles/tcp_kernel_fx32_mode_product_256cubed.md).  The counters
+# capture of `bench.py --kernel-only --prec <form>` (the summaries and their
+# commands are in profiles/tcp_kernel_<form>_mode_product_256cubed.md).  The counters
 # hold for the kernel sources they were taken on only: another hash of those
 # files reports the traffic as unknown (null).
 KERNEL_SOURCES = ["tcp.cu", "tc_common.cuh", "ptx.cuh", "internal.h"]
@@ -449,6 +453,8 @@ def roofline(kern, peaks, src, prec):
         pipe, mult = bf16, 6
     elif prec == "fx32":
         pipe, mult = bf16, 10
+    elif prec == "fx32h":
+        pipe, mult = bf16, 6  # f16 operands: the same nominal rate as bf16
     else:
         pipe, mult = bf16, 3
     peak = pipe / mult
@@ -512,7 +518,7 @@ def _line(name, prec, ms, flops, byts, peaks, mult=None):
     print(json.dumps(out), flush=True)
 
 
-MULT = {"3xtf32": 3, "bf16x3": 3, "bf16x6": 6, "fx32": 10}
+MULT = {"3xtf32": 3, "bf16x3": 3, "bf16x6": 6, "fx32": 10, "fx32h": 6}
 
 
 def run_configs(args):
@@ -530,7 +536,7 @@ def run_configs(args):
     T = kron.colmajor(torch.from_numpy(c.T).to(dev))
     Ls = [kron.colmajor(torch.from_numpy(L).to(dev)) for L in c.L]
     fl = W.tucker_flops([100] * 3, [100] * 3)
-    for prec in ("fp64", "fp32", "3xtf32", "bf16x6", "fx32"):
+    for prec in ("fp64", "fp32", "3xtf32", "bf16x6", "fx32", "fx32h"):
         plan = kron.TuckerPlan(T.shape, [100] * 3, torch.float64, prec)
         ws = plan.workspace(dev)
         S = kron.empty_colmajor([100] * 3, torch.float64, dev)
@@ -543,7 +549,7 @@ def run_configs(args):
     T = kron.colmajor(torch.from_numpy(c.T).float().to(dev))
     Ls = [kron.colmajor(torch.from_numpy(L).float().to(dev)) for L in c.L]
     fl = W.tucker_flops([20] * 6, [20] * 6)
-    for prec in ("fp32", "3xtf32", "bf16x3", "bf16x6", "fx32"):
+    for prec in ("fp32", "3xtf32", "bf16x3", "bf16x6", "fx32", "fx32h"):
         plan = kron.TuckerPlan(T.shape, [20] * 6, torch.float32, prec)
         ws = plan.workspace(dev)
         S = kron.empty_colmajor([20] * 6, torch.float32, dev)
@@ -589,7 +595,7 @@ def run_configs(args):
     Ps = [kron.colmajor((torch.eye(N, dtype=torch.float64, device=dev) - TAU * a)) for a in A]
     S = kron.empty_colmajor([N] * D, torch.float64, dev)
     fl = D * 2.0 * N ** (D + 1)
-    for prec in ("fp64", "fx32", "3xtf32"):
+    for prec in ("fp64", "fx32", "fx32h", "3xtf32"):
         plan = kron.TuckerPlan([N] * D, [N] * D, torch.float64, prec, natural_order=True)
         ws = torch.empty(plan.kronsumv_workspace_bytes(), dtype=torch.uint8, device=dev)
         ms = _timed(torch, lambda: plan.kronsumv_into(V, A, S, ws=ws), reps=5, flush=flush)

@@ -88,6 +88,13 @@ typedef enum kron_dtype { KRON_F64 = 0, KRON_F32 = 1 } kron_dtype;
  *                     per stored value and per product, for contraction
  *                     lengths up to 256; intermediates are 32-bit fixed point.
  *                     Supported by kron_mump, kron_tucker and the stepper.
+ *  KRON_PREC_FX32H  : the same scheme with 29-bit fixed point cut into three
+ *                     balanced digits of 8, 11 and 11 bits stored exactly as
+ *                     FP16 slices d0 2^8, d1 2^-3, d2 2^-14 (all in the normal
+ *                     FP16 range), and the six slice products with digit
+ *                     index sum <= 2 (tcgen05 kind::f16 with f16 operands):
+ *                     6 products instead of 10, about 26 significant bits per
+ *                     product.  Same calls as KRON_PREC_FX32.
  * Split forms keep intermediates in FP32.  Inputs stored as double are split
  * from their double value.
  */
@@ -97,7 +104,8 @@ typedef enum kron_prec {
     KRON_PREC_3XTF32 = 2,
     KRON_PREC_BF16X3 = 3,
     KRON_PREC_BF16X6 = 4,
-    KRON_PREC_FX32 = 5
+    KRON_PREC_FX32 = 5,
+    KRON_PREC_FX32H = 6
 } kron_prec;
 
 /* Plan flags. */

@@ -35,7 +35,7 @@ STATUS = {0: "KRON_OK", 1: "KRON_ERR_INVALID_ARG", 2: "KRON_ERR_UNSUPPORTED",
           3: "KRON_ERR_ALIGNMENT", 4: "KRON_ERR_WORKSPACE", 5: "KRON_ERR_CUDA",
           6: "KRON_ERR_TIMEOUT", 7: "KRON_ERR_NUMERIC"}
 F64, F32 = 0, 1
-PREC = {"fp64": 0, "fp32": 1, "3xtf32": 2, "bf16x3": 3, "bf16x6": 4, "fx32": 5}
+PREC = {"fp64": 0, "fp32": 1, "3xtf32": 2, "bf16x3": 3, "bf16x6": 4, "fx32": 5, "fx32h": 6}
 SPLIT_PRECS = ("3xtf32", "bf16x3", "bf16x6")
 PLAN_TRANS_L = 0x1
 PLAN_NATURAL_ORDER = 0x2

@@ -20,7 +20,7 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 kron_status cuda_status(cudaError_t e) { return e == cudaSuccess ? KRON_OK : KRON_ERR_CUDA; }
 
 bool valid_dtype(kron_dtype t) { return t == KRON_F64 || t == KRON_F32; }
-bool valid_prec(kron_prec p) { return p >= KRON_PREC_FP64 && p <= KRON_PREC_FX32; }
+bool valid_prec(kron_prec p) { return p >= KRON_PREC_FP64 && p <= KRON_PREC_FX32H; }
 size_t esize(kron_dtype t) { return t == KRON_F64 ? 8 : 4; }
 
 // Element size of the intermediates of a precision.
@@ -154,7 +154,9 @@ kron_status run_chain_fx(const kron_plan_s *pl, const void *T, const void *const
     FxScale *sc = reinterpret_cast<FxScale *>(ws + pl->fxsc_off);  // [0] input, [1], [2] buffers
     auto *scratch = reinterpret_cast<unsigned long long *>(sc + 3);
     auto *xin = reinterpret_cast<int32_t *>(ws + pl->fxin_off);
-    if (fx_from_float(T, io64, prod(pl->m, 0, d), xin, &sc[0], scratch, st) != cudaSuccess) return KRON_ERR_CUDA;
+    const int form = form_of(pl->prec);
+    if (fx_from_float(form, T, io64, prod(pl->m, 0, d), xin, &sc[0], scratch, st) != cudaSuccess)
+        return KRON_ERR_CUDA;
     int64_t cur[KRON_MAX_D];
     for (int k = 0; k < d; ++k) cur[k] = pl->m[k];
     const void *src = xin;
@@ -170,9 +172,9 @@ kron_status run_chain_fx(const kron_plan_s *pl, const void *T, const void *const
         void *img = ws + pl->img_off[mu];
         int *f = reinterpret_cast<int *>(ws + pl->fxf_off[mu]);
         auto *gb = reinterpret_cast<unsigned long long *>(ws + pl->fxg_off[mu]);
-        cudaError_t e = fx_build_bimage(c, img, f, gb, st);
+        cudaError_t e = fx_build_bimage(form, c, img, f, gb, st);
         if (e == cudaSuccess && sdst) e = fx_reset(sdst, st);
-        if (e == cudaSuccess) e = tcp_contract_fx(c, img, ssrc, f, gb, sdst, st);
+        if (e == cudaSuccess) e = tcp_contract_fx(form, c, img, ssrc, f, gb, sdst, st);
         if (e != cudaSuccess) return KRON_ERR_CUDA;
         cur[mu] = pl->n[mu];
         src = dst;
@@ -350,7 +352,8 @@ kron_status kron_mump(int d, const int64_t *m, int mu, int64_t n, const void *T,
     cudaError_t e;
     if (is_fx(prec)) {
         auto *w = static_cast<uint8_t *>(ws);
-        size_t off = align_up(tc_bimage_bytes(kFX32, n, m[mu]));
+        const int form = form_of(prec);
+        size_t off = align_up(tc_bimage_bytes(form, n, m[mu]));
         int *f = reinterpret_cast<int *>(w + off);
         off += align_up((size_t)n * sizeof(int));
         auto *gb = reinterpret_cast<unsigned long long *>(w + off);
@@ -360,9 +363,9 @@ kron_status kron_mump(int d, const int64_t *m, int mu, int64_t n, const void *T,
         auto *sc = reinterpret_cast<FxScale *>(w + off);
         auto *scratch = reinterpret_cast<unsigned long long *>(sc + 1);
         Contraction c = tc_mode_contraction(g, X, false, L, io64, ldL, transL != 0, S, io64);
-        e = fx_from_float(T, io64, prod(m, 0, d), X, sc, scratch, cs);
-        if (e == cudaSuccess) e = fx_build_bimage(c, w, f, gb, cs);
-        if (e == cudaSuccess) e = tcp_contract_fx(c, w, sc, f, gb, nullptr, cs);
+        e = fx_from_float(form, T, io64, prod(m, 0, d), X, sc, scratch, cs);
+        if (e == cudaSuccess) e = fx_build_bimage(form, c, w, f, gb, cs);
+        if (e == cudaSuccess) e = tcp_contract_fx(form, c, w, sc, f, gb, nullptr, cs);
     } else if (is_split(prec)) {
         const int form = form_of(prec);
         Contraction c = tc_mode_contraction(g, T, io64, L, io64, ldL, transL != 0, S, io64);
@@ -720,7 +723,8 @@ kron_status kron_kronsumv(kron_plan plan, const void *V, const void *const *L, c
     if (is_fx(plan->prec)) {
         X = reinterpret_cast<int32_t *>(w + lay.fxv);
         sc = reinterpret_cast<FxScale *>(w + lay.fxsc);
-        e = fx_from_float(V, io64, prod(plan->n, 0, d), X, sc, reinterpret_cast<unsigned long long *>(sc + 1), cs);
+        e = fx_from_float(form, V, io64, prod(plan->n, 0, d), X, sc, reinterpret_cast<unsigned long long *>(sc + 1),
+                          cs);
     }
     for (int mu = 0; mu < d && e == cudaSuccess; ++mu) {
         const ModeGeom g = mode_geom(d, plan->n, mu, plan->n[mu]);
@@ -729,8 +733,8 @@ kron_status kron_kronsumv(kron_plan plan, const void *V, const void *const *L, c
             c.accumulate = mu > 0;
             int *f = reinterpret_cast<int *>(w + lay.fxf);
             auto *gb = reinterpret_cast<unsigned long long *>(w + lay.fxg);
-            e = fx_build_bimage(c, w + lay.img, f, gb, cs);
-            if (e == cudaSuccess) e = tcp_contract_fx(c, w + lay.img, sc, f, gb, nullptr, cs);
+            e = fx_build_bimage(form, c, w + lay.img, f, gb, cs);
+            if (e == cudaSuccess) e = tcp_contract_fx(form, c, w + lay.img, sc, f, gb, nullptr, cs);
         } else if (is_split(plan->prec)) {
             Contraction c = tc_mode_contraction(g, V, io64, L[mu], io64, ldL[mu], trans, S, io64);
             c.accumulate = mu > 0;
@@ -1093,8 +1097,8 @@ StepLayout step_layout(const kron_plan_s *pl) {
             s.fxg[k] = off;
             off += kAlign;
             s.imgh[k] = off;
-            const int bn = tc_tile_n(kFX32, pl->n[k]);
-            if (bn % 32 == 0) off += align_up(tc_bimage_bytes_bn(kFX32, pl->n[k], pl->n[k], bn / 2));
+            const int bn = tc_tile_n(form, pl->n[k]);
+            if (bn % 32 == 0) off += align_up(tc_bimage_bytes_bn(form, pl->n[k], pl->n[k], bn / 2));
         }
         s.fxsc = off;
         off += kAlign;
@@ -1117,21 +1121,23 @@ kron_status run_steps_fx(const kron_plan_s *pl, const double *const *E, const in
     // launches before it are complete (no memset between the launches)
     FxScale *sc = reinterpret_cast<FxScale *>(w + lay.fxsc);
     auto *scratch = reinterpret_cast<unsigned long long *>(sc + 3);
+    const int form = form_of(pl->prec);
     for (int k = 0; k < d; ++k) {
         const ModeGeom g{1, 1, pl->n[k], pl->n[k]};
         Contraction c = tc_mode_contraction(g, nullptr, false, E[k], true, ldE[k], false, nullptr, false);
-        if (fx_build_bimage(c, w + lay.img[k], reinterpret_cast<int *>(w + lay.fxf[k]),
+        if (fx_build_bimage(form, c, w + lay.img[k], reinterpret_cast<int *>(w + lay.fxf[k]),
                             reinterpret_cast<unsigned long long *>(w + lay.fxg[k]), cs) != cudaSuccess)
             return KRON_ERR_CUDA;
         // half-width image for the tail tiles (same row exponents and bound)
-        const int bn = tc_tile_n(kFX32, pl->n[k]);
+        const int bn = tc_tile_n(form, pl->n[k]);
         if (bn % 32 == 0 &&
-            fx_build_bimage_bn(c, w + lay.imgh[k], reinterpret_cast<int *>(w + lay.fxf[k]),
+            fx_build_bimage_bn(form, c, w + lay.imgh[k], reinterpret_cast<int *>(w + lay.fxf[k]),
                                reinterpret_cast<unsigned long long *>(w + lay.fxg[k]), bn / 2, cs) != cudaSuccess)
             return KRON_ERR_CUDA;
     }
     const int64_t N = prod(pl->n, 0, d);
-    if (fx_from_float(U, io64, N, reinterpret_cast<int32_t *>(w + lay.st[0]), &sc[0], scratch, cs) != cudaSuccess)
+    if (fx_from_float(form, U, io64, N, reinterpret_cast<int32_t *>(w + lay.st[0]), &sc[0], scratch, cs) !=
+        cudaSuccess)
         return KRON_ERR_CUDA;
     if (fx_reset(&sc[1], cs) != cudaSuccess) return KRON_ERR_CUDA;
     int cur = 0, idx = 0;
@@ -1145,9 +1151,9 @@ kron_status run_steps_fx(const kron_plan_s *pl, const double *const *E, const in
             FxScale *snext = (idx + 2 < total) ? &sc[(idx + 2) % 3] : nullptr;
             Contraction c = tc_mode_contraction(g, w + lay.st[cur], false, E[mu], true, ldE[mu], false, dst,
                                                 last ? io64 : false);
-            const bool half = tc_tile_n(kFX32, pl->n[mu]) % 32 == 0;
+            const bool half = tc_tile_n(form, pl->n[mu]) % 32 == 0;
             const cudaError_t e =
-                tcp_contract_fx_tail(c, w + lay.img[mu], half ? w + lay.imgh[mu] : nullptr, &sc[idx % 3],
+                tcp_contract_fx_tail(form, c, w + lay.img[mu], half ? w + lay.imgh[mu] : nullptr, &sc[idx % 3],
                                      reinterpret_cast<const int *>(w + lay.fxf[mu]),
                                      reinterpret_cast<const unsigned long long *>(w + lay.fxg[mu]), sdst, snext, cs);
             if (e != cudaSuccess) return KRON_ERR_CUDA;

@@ -1,11 +1,12 @@
-// fx.cu -- helpers of the 32-bit fixed-point form (KRON_PREC_FX32): the
+// fx.cu -- helpers of the fixed-point forms (KRON_PREC_FX32, _FX32H): the
 // sliced image of op(L) with one power-of-two scale per row, and the
 // conversion of a floating-point tensor into fixed point with one scale.
 //
-// Fixed point: a tensor X with scale e holds the values X * 2^(e - 31),
-// |X| <= 2^31 - 1, so |value| < 2^e.  A row c of op(L) is held as
-// Y = round(L[c, :] * 2^(31 - f_c)) with 2^(f_c - 1) <= max_k |L[c, k]| < 2^f_c.
-// Both are cut into four 8-bit slices (fx_pack, tc_common.cuh).
+// Fixed point with b magnitude bits (b = 31 for FX32, 29 for FX32H): a tensor
+// X with scale e holds the values X * 2^(e - b), |X| <= 2^b - 1, so
+// |value| < 2^e.  A row c of op(L) is held as Y = round(L[c, :] * 2^(b - f_c))
+// with 2^(f_c - 1) <= max_k |L[c, k]| < 2^f_c.  Both are cut into digit slices
+// (fx_pack / fx_pack3, tc_common.cuh).
 #include <algorithm>
 #include <climits>
 
@@ -22,9 +23,10 @@ __device__ __forceinline__ int exp_bound(double mx) {
     return f;
 }
 
-__device__ __forceinline__ int32_t to_fixed(double v, int f) {
-    double y = rint(ldexp(v, 31 - f));
-    y = fmax(-2147483647.0, fmin(2147483647.0, y));
+__device__ __forceinline__ int32_t to_fixed(double v, int f, int bits) {
+    const double lim = ldexp(1.0, bits) - 1.0;
+    double y = rint(ldexp(v, bits - f));
+    y = fmax(-lim, fmin(lim, y));
     return (int32_t)y;
 }
 
@@ -56,10 +58,11 @@ __global__ void fx_rows_kernel(const T *__restrict__ B, IdxMap colB, IdxMap kB, 
 }
 
 // Image items (nt, kb, row, chunk): eight consecutive k of one row of op(L),
-// fixed point with the row's exponent, cut into the four slices.
-template <typename T>
+// fixed point with the row's exponent, cut into the slices of form F.
+template <typename T, int F>
 __global__ void fx_image_kernel(const T *__restrict__ B, IdxMap colB, IdxMap kB, int64_t N, int64_t K, int BN,
                                 int64_t KB, int64_t NT, const int *__restrict__ f, uint8_t *img) {
+    constexpr int bits = (F == kFX32H) ? 29 : 31;
     constexpr int BK = kRowBytes / 2;
     const int64_t total = NT * KB * BN * kChunks;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -77,14 +80,15 @@ __global__ void fx_image_kernel(const T *__restrict__ B, IdxMap colB, IdxMap kB,
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const int64_t k = kb * BK + ch * 8 + e;
-            x[e] = (c < N && k < K) ? to_fixed((double)B[ro + imap(kB, k)], fc) : 0;
+            x[e] = (c < N && k < K) ? to_fixed((double)B[ro + imap(kB, k)], fc, bits) : 0;
         }
-        uint4 out[4];
-        fx_pack(x, out);
-        uint8_t *base = img + (size_t)((nt * KB + kb) * 4) * BN * kRowBytes;
+        constexpr int NP = FT<F>::PIECES;
+        uint4 out[NP];
+        fx_pack_f<F>(x, out);
+        uint8_t *base = img + (size_t)((nt * KB + kb) * NP) * BN * kRowBytes;
         const uint32_t off = swz(row, ch);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4 *>(base + (size_t)q * BN * kRowBytes + off) = out[q];
+        for (int q = 0; q < NP; ++q) *reinterpret_cast<uint4 *>(base + (size_t)q * BN * kRowBytes + off) = out[q];
     }
 }
 
@@ -100,27 +104,30 @@ __device__ __forceinline__ int ebound(float v) {
     return E ? E - 126 : INT_MIN;
 }
 
-// round(v * 2^(31 - e)) from the bits of v, for |v| < 2^e (integer only).
-__device__ __forceinline__ int32_t fixed_bits(double v, int e) {
+// round(v * 2^(bits - e)) from the bits of v, for |v| < 2^e (integer only),
+// clamped to 2^bits - 1.
+__device__ __forceinline__ int32_t fixed_bits(double v, int e, int bits) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const int E = (int)((b >> 52) & 0x7FF);
     if (E == 0) return 0;
     const unsigned long long mant = (1ull << 52) | (b & ((1ull << 52) - 1));
-    const int r = e + 1044 - E;  // right shift, >= 22 when |v| < 2^e
+    const int r = e + 1075 - bits - E;  // right shift, >= 53 - bits when |v| < 2^e
     unsigned long long x = 0;
     if (r < 64) x = r > 0 ? (mant + (1ull << (r - 1))) >> r : mant << (-r);
-    if (x > 2147483647ull) x = 2147483647ull;
+    const unsigned long long lim = (1ull << bits) - 1;
+    if (x > lim) x = lim;
     return (b >> 63) ? -(int32_t)x : (int32_t)x;
 }
-__device__ __forceinline__ int32_t fixed_bits(float v, int e) {
+__device__ __forceinline__ int32_t fixed_bits(float v, int e, int bits) {
     const uint32_t b = __float_as_uint(v);
     const int E = (int)((b >> 23) & 0xFF);
     if (E == 0) return 0;
     const unsigned long long mant = (1u << 23) | (b & ((1u << 23) - 1));
-    const int r = e + 119 - E;
+    const int r = e + 150 - bits - E;
     unsigned long long x = 0;
     if (r < 64) x = r > 0 ? (mant + (1ull << (r - 1))) >> r : mant << (-r);
-    if (x > 2147483647ull) x = 2147483647ull;
+    const unsigned long long lim = (1ull << bits) - 1;
+    if (x > lim) x = lim;
     return (b >> 31) ? -(int32_t)x : (int32_t)x;
 }
 
@@ -135,11 +142,12 @@ __global__ void fx_maxabs_kernel(const T *__restrict__ src, int64_t n, int *emax
 }
 
 template <typename T>
-__global__ void fx_convert_kernel(const T *__restrict__ src, int64_t n, const int *emax, int32_t *X, FxScale *s) {
+__global__ void fx_convert_kernel(const T *__restrict__ src, int64_t n, const int *emax, int32_t *X, FxScale *s,
+                                  int bits) {
     const int e = (*emax < -100000) ? 0 : *emax;  // all-zero tensor: any scale
     unsigned m = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t x = fixed_bits(src[i], e);
+        const int32_t x = fixed_bits(src[i], e, bits);
         X[i] = x;
         m = max(m, (unsigned)(x < 0 ? -x : x));
     }
@@ -155,11 +163,12 @@ cudaError_t fx_reset(FxScale *s, cudaStream_t st) {
     return cudaMemsetAsync(&s->maxabs, 0, sizeof(unsigned), st);
 }
 
-cudaError_t fx_build_bimage(const Contraction &c, void *img, int *f, unsigned long long *g, cudaStream_t st) {
-    return fx_build_bimage_bn(c, img, f, g, tc_tile_n(kFX32, c.N), st);
+cudaError_t fx_build_bimage(int form, const Contraction &c, void *img, int *f, unsigned long long *g,
+                            cudaStream_t st) {
+    return fx_build_bimage_bn(form, c, img, f, g, tc_tile_n(form, c.N), st);
 }
 
-cudaError_t fx_build_bimage_bn(const Contraction &c, void *img, int *f, unsigned long long *g, int bn,
+cudaError_t fx_build_bimage_bn(int form, const Contraction &c, void *img, int *f, unsigned long long *g, int bn,
                                cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(g, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
@@ -175,17 +184,25 @@ cudaError_t fx_build_bimage_bn(const Contraction &c, void *img, int *f, unsigned
     const int64_t total = nt * kb * bn * kChunks;
     const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 16));
     auto *out = static_cast<uint8_t *>(img);
-    if (c.B_f64)
-        fx_image_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double *>(c.B), c.colB, c.kB, c.N, c.K, bn,
-                                                        kb, nt, f, out);
+    const bool h = form == kFX32H;
+    if (c.B_f64 && h)
+        fx_image_kernel<double, kFX32H><<<blocks, 256, 0, st>>>(static_cast<const double *>(c.B), c.colB, c.kB, c.N,
+                                                                c.K, bn, kb, nt, f, out);
+    else if (c.B_f64)
+        fx_image_kernel<double, kFX32><<<blocks, 256, 0, st>>>(static_cast<const double *>(c.B), c.colB, c.kB, c.N,
+                                                               c.K, bn, kb, nt, f, out);
+    else if (h)
+        fx_image_kernel<float, kFX32H><<<blocks, 256, 0, st>>>(static_cast<const float *>(c.B), c.colB, c.kB, c.N,
+                                                               c.K, bn, kb, nt, f, out);
     else
-        fx_image_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float *>(c.B), c.colB, c.kB, c.N, c.K, bn, kb,
-                                                       nt, f, out);
+        fx_image_kernel<float, kFX32><<<blocks, 256, 0, st>>>(static_cast<const float *>(c.B), c.colB, c.kB, c.N,
+                                                              c.K, bn, kb, nt, f, out);
     return cudaGetLastError();
 }
 
-cudaError_t fx_from_float(const void *src, bool src64, int64_t count, int32_t *X, FxScale *s,
+cudaError_t fx_from_float(int form, const void *src, bool src64, int64_t count, int32_t *X, FxScale *s,
                           unsigned long long *scratch, cudaStream_t st) {
+    const int bits = fx_bits(form);
     int *emax = reinterpret_cast<int *>(scratch);
     cudaError_t e = cudaMemsetAsync(emax, 0x80, sizeof(int), st);  // 0x80808080: below every bound
     if (e == cudaSuccess) e = fx_reset(s, st);
@@ -193,10 +210,10 @@ cudaError_t fx_from_float(const void *src, bool src64, int64_t count, int32_t *X
     const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, 152 * 8));
     if (src64) {
         fx_maxabs_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double *>(src), count, emax);
-        fx_convert_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double *>(src), count, emax, X, s);
+        fx_convert_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double *>(src), count, emax, X, s, bits);
     } else {
         fx_maxabs_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float *>(src), count, emax);
-        fx_convert_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float *>(src), count, emax, X, s);
+        fx_convert_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float *>(src), count, emax, X, s, bits);
     }
     return cudaGetLastError();
 }

@@ -41,7 +41,7 @@ struct Contraction {
 };
 
 // The split-precision forms of the tensor-core path.
-enum TcForm { kTF32x3 = 0, kBF16x3 = 1, kBF16x6 = 2, kFX32 = 3 };
+enum TcForm { kTF32x3 = 0, kBF16x3 = 1, kBF16x6 = 2, kFX32 = 3, kFX32H = 4 };
 
 inline int form_of(kron_prec p) {
     switch (p) {
@@ -49,11 +49,15 @@ inline int form_of(kron_prec p) {
         case KRON_PREC_BF16X3: return kBF16x3;
         case KRON_PREC_BF16X6: return kBF16x6;
         case KRON_PREC_FX32: return kFX32;
+        case KRON_PREC_FX32H: return kFX32H;
         default: return -1;
     }
 }
-inline bool is_split(kron_prec p) { return form_of(p) >= 0 && p != KRON_PREC_FX32; }
-inline bool is_fx(kron_prec p) { return p == KRON_PREC_FX32; }
+inline bool is_fx(kron_prec p) { return p == KRON_PREC_FX32 || p == KRON_PREC_FX32H; }
+inline bool is_split(kron_prec p) { return form_of(p) >= 0 && !is_fx(p); }
+inline bool is_fx_form(int form) { return form == kFX32 || form == kFX32H; }
+// Magnitude bits of a fixed-point form's integers: |X| < 2^bits.
+inline int fx_bits(int form) { return form == kFX32H ? 29 : 31; }
 
 // Scale word of a 32-bit fixed-point tensor: value = X * 2^(e - 31), and the
 // largest |X| stored (maintained with atomicMax by the kernel that writes X).
@@ -89,27 +93,27 @@ cudaError_t tcp_contract(int form, const Contraction &c, const void *img, cudaSt
 // reset_next: a scale word that the launch clears once the launches before it
 // are complete (the output scale of the next fixed-point product; launches are
 // programmatic dependent launches, so no memset may sit between them).
-cudaError_t tcp_contract_fx(const Contraction &c, const void *img, const FxScale *fxA, const int *fxF,
+cudaError_t tcp_contract_fx(int form, const Contraction &c, const void *img, const FxScale *fxA, const int *fxF,
                             const unsigned long long *fxG, FxScale *fxC, cudaStream_t st,
                             FxScale *reset_next = nullptr);
 
 // ---- fixed-point helpers (fx.cu) ----
 // Image of op(L) for the FX32 form (same layout as tc_build_bimage, four
 // slices), per-row exponents f[N] and the row-sum bound *g (zeroed here).
-cudaError_t fx_build_bimage(const Contraction &c, void *img, int *f, unsigned long long *g, cudaStream_t st);
+cudaError_t fx_build_bimage(int form, const Contraction &c, void *img, int *f, unsigned long long *g, cudaStream_t st);
 // the same image for N-tiles of width bn (the tail tiles of tcp_contract_fx_tail)
-cudaError_t fx_build_bimage_bn(const Contraction &c, void *img, int *f, unsigned long long *g, int bn,
+cudaError_t fx_build_bimage_bn(int form, const Contraction &c, void *img, int *f, unsigned long long *g, int bn,
                                cudaStream_t st);
 // tcp_contract_fx with the last, partial round of tiles split into tiles of
 // half the width (second image img_half, tiles of width tc_tile_n / 2), so
 // that it takes about half a tile's time; one launch.  Falls back to
 // tcp_contract_fx when the split does not apply.
-cudaError_t tcp_contract_fx_tail(const Contraction &c, const void *img, const void *img_half, const FxScale *fxA,
+cudaError_t tcp_contract_fx_tail(int form, const Contraction &c, const void *img, const void *img_half, const FxScale *fxA,
                                  const int *fxF, const unsigned long long *fxG, FxScale *fxC, FxScale *reset_next,
                                  cudaStream_t st);
 // Dense FP64/FP32 tensor of `count` elements -> 32-bit fixed point X with
 // one scale (written to *s); `scratch` is 8 bytes of device memory.
-cudaError_t fx_from_float(const void *src, bool src64, int64_t count, int32_t *X, FxScale *s,
+cudaError_t fx_from_float(int form, const void *src, bool src64, int64_t count, int32_t *X, FxScale *s,
                           unsigned long long *scratch, cudaStream_t st);
 // Zeroes the running maximum of a scale word before a kernel fills it.
 cudaError_t fx_reset(FxScale *s, cudaStream_t st);

@@ -257,7 +257,7 @@ __device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t saddr, uint32_t ro
 }
 
 // Instruction descriptor for kind::tf32 / kind::f16: FP32 accumulator,
-// A and B K-major, M x N tile.  fmt: 2 = TF32, 1 = BF16.
+// A and B K-major, M x N tile.  fmt: 2 = TF32, 1 = BF16, 0 = F16.
 __host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t M, uint32_t N) {
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }

@@ -384,9 +384,9 @@ __global__ void splitk_reduce_kernel(const float *__restrict__ P, int64_t splits
 
 cudaError_t tc_error_word(unsigned int *out, bool clear) { return read_error_word(out, clear); }
 
-static int pieces_of(int form) { return form == kFX32 ? 4 : (form == kBF16x6 ? 3 : 2); }
+static int pieces_of(int form) { return form == kFX32 ? 4 : ((form == kBF16x6 || form == kFX32H) ? 3 : 2); }
 static int bk_of(int form) { return form == kTF32x3 ? kRowBytes / 4 : kRowBytes / 2; }
-static int max_bn(int form) { return form == kBF16x6 ? 64 : (form == kFX32 ? 256 : 128); }
+static int max_bn(int form) { return form == kBF16x6 ? 64 : (is_fx_form(form) ? 256 : 128); }
 
 int tc_tile_n(int form, int64_t N) {
     const int64_t mx = max_bn(form);

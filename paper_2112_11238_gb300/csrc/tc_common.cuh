@@ -4,6 +4,7 @@
 // describe.
 #pragma once
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "internal.h"
 #include "ptx.cuh"
@@ -29,6 +30,13 @@ template <>
 struct FT<kFX32> {
     static constexpr int KIND = 1, PIECES = 4, ELEM = 2, NPROD = 10, FMT = 1, MMA_K = 16;
 };
+// 29-bit fixed point in three FP16 digit slices (kind::f16, both operands f16)
+template <>
+struct FT<kFX32H> {
+    static constexpr int KIND = 1, PIECES = 3, ELEM = 2, NPROD = 6, FMT = 0, MMA_K = 16;
+};
+template <int F>
+__host__ __device__ constexpr bool is_fx_f() { return F == kFX32 || F == kFX32H; }
 
 // Tensor-memory accumulator regions per accumulator set: the split forms keep
 // hi*hi (region 0) apart from the cross products (region 1); the fixed-point
@@ -55,6 +63,7 @@ __device__ __forceinline__ void prod_pieces(int i, int &pa, int &pb) {
         pa = (i == 0) ? 1 : 0;
         pb = (i == 1) ? 1 : 0;
     } else {
+        // three pieces (BF16x6, and the FX32H digits: levels 2, 1, 0):
         // (2,0) (1,1) (0,2) (1,0) (0,1) (0,0)
         const int ta[6] = {2, 1, 0, 1, 0, 0};
         const int tb[6] = {0, 1, 2, 0, 1, 0};
@@ -196,6 +205,44 @@ __device__ __forceinline__ void fx_pack(const int32_t (&v)[8], uint4 (&out)[4]) 
     }
 #pragma unroll
     for (int t = 0; t < 4; ++t) out[t] = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+}
+
+// 29-bit fixed-point values (|x| < 2^29) -> three balanced digits each,
+// x = d0 2^22 + d1 2^11 + d2 with d1, d2 in [-1024, 1023] and d0 in
+// [-128, 128]; slice t is d0 2^8, d1 2^-3, d2 2^-14: all exact and in the
+// normal FP16 range (|slice| in [2^-14, 2^15]), and x = 2^14 (sum of slices).
+// Digits without a carry chain: y = x + 0x200400 holds d1 + 1024 and
+// d2 + 1024 in its 11-bit fields and y >> 22 = d0 (no overflow below 2^29);
+// each digit becomes a float exactly through the 2^23 exponent trick, and
+// pairs are rounded to f16x2, exact for these values.
+__device__ __forceinline__ void fx_pack3(const int32_t (&v)[8], uint4 (&out)[3]) {
+    uint32_t w[3][4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+        float f[3][2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int y = v[e + h] + 0x200400;
+            f[0][h] = fmaf(__int_as_float(0x4B400000 + (y >> 22)), 256.0f, -3221225472.0f);
+            f[1][h] = fmaf(__uint_as_float(0x4B000000u | (((uint32_t)y >> 11) & 0x7FFu)), 0.125f, -1048704.0f);
+            f[2][h] = fmaf(__uint_as_float(0x4B000000u | ((uint32_t)y & 0x7FFu)), 6.103515625e-05f,
+                           -512.0625f);
+        }
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const __half2 hh = __floats2half2_rn(f[t][0], f[t][1]);
+            w[t][e / 2] = *reinterpret_cast<const uint32_t *>(&hh);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 3; ++t) out[t] = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+}
+
+// Digits of the fixed-point form F.
+template <int F>
+__device__ __forceinline__ void fx_pack_f(const int32_t (&v)[8], uint4 (&out)[FT<F>::PIECES]) {
+    if constexpr (F == kFX32H) fx_pack3(v, out);
+    else fx_pack(v, out);
 }
 
 template <int F, typename Tin>

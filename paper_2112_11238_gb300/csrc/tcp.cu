@@ -346,11 +346,11 @@ __device__ __forceinline__ bool conv_tile_loop_raw(const TcJob &J, const CUtenso
                 for (int e = 0; e < CH; ++e) v[e] = raw[(ich[i] * CH + e) * kBM + irow[i]];
             }
             uint4 out[FT<F>::PIECES];
-            if constexpr (F == kFX32) {
+            if constexpr (is_fx_f<F>()) {
                 int32_t x[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) x[e] = __float_as_int(v[e]);
-                fx_pack(x, out);
+                fx_pack_f<F>(x, out);
             } else {
                 split_pack<F, float>(v, out);
             }
@@ -401,43 +401,60 @@ __device__ __forceinline__ int add_sat(int a, int b) {
     return r;
 }
 
+// Constants of the fixed-point form F: magnitude bits b of its integers
+// (|X| < 2^b), the accumulator unit 2^(eA + f_c + UNIT) of a product of two
+// fixed-point operands with scales eA and f_c, and the left shift VS of the
+// level-0 accumulator in the 64-bit value path.
+//   FX32:  four 8-bit digits, slices d_t 2^(-8t), x = 2^24 (sum of slices):
+//          b = 31, UNIT = 48 - 62 = -14, level 0 an integer below 2^24.
+//   FX32H: three digits (8, 11, 11 bits), slices d0 2^8, d1 2^-3, d2 2^-14,
+//          x = 2^14 (sum of slices): b = 29, UNIT = 28 - 58 = -30, level 0 a
+//          multiple of 2^16 (above 2^31 for long K: no 32-bit conversion).
+template <int F>
+struct FxForm {
+    static constexpr int BITS = (F == kFX32H) ? 29 : 31;
+    static constexpr int UNIT = (F == kFX32H) ? -30 : -14;
+    static constexpr int VS = (F == kFX32H) ? 0 : 16;
+};
+
 // Scales of one fixed-point job, the same for all of its tiles: A's scale
 // eA and the output scale eC = eA_actual + g, where |A| < 2^eA_actual (from
 // A's largest magnitude) and every row sum of |op(L)| is below 2^g, so that
-// every output is below 2^31 in magnitude up to rounding (the conversion
-// saturates there).
+// every output is below 2^b in magnitude up to rounding.
 struct FxConsts {
     int j = -1;
     int eA = 0, eC = 0;
 };
 
+template <int F>
 __device__ __forceinline__ void fx_consts(const TcJob &J, int j, FxConsts &k) {
     if (k.j == j) return;
     k.j = j;
     k.eA = J.fxA->e;
     const unsigned mA = J.fxA->maxabs;
-    const int eAact = k.eA - 31 + (mA ? 32 - __clz((int)mA) : 0);
+    const int eAact = k.eA - FxForm<F>::BITS + (mA ? 32 - __clz((int)mA) : 0);
     const unsigned long long gb = *J.fxG;  // bits of the largest row sum (non-negative)
     const int g = gb ? (int)((gb >> 52) & 0x7FF) - 1022 : 0;
     k.eC = eAact + g;
 }
 
 // Fixed-point form epilogue for one tile row.  The two accumulator regions
-// hold a0 (level 0, an exact integer below 2^24) and a1 (levels 1..3) in
-// units of 2^(eA + f_c - 14).  Fixed-point output with scale eC:
-//     X = round((a0 + a1) * 2^s),  s = eA + f_c + 17 - eC,
+// hold a0 (level 0, exact) and a1 (the other levels kept) in units of
+// 2^(eA + f_c + UNIT).  Fixed-point output with scale eC:
+//     X = round((a0 + a1) * 2^s),  s = eA + f_c + UNIT + b - eC,
 // formed from the float pair (sum, err) = Fast2Sum(a0 * 2^s, a1 * 2^s) (both
 // products are exact power-of-two scalings; Dekker's Fast2Sum is error-free
 // when |a0| >= |a1|, the usual case, and within an ulp of the sum otherwise),
 // then X = rint(sum) + rint(err) (|err| <= 2^7: rounded by the 1.5 * 2^23
 // exponent trick), saturated.  The largest |X| of the tile is tracked on
 // |sum| with a margin above the error term.
-// Value output (last mode): the sum 2^16 (a0 + a1) is formed in 64-bit
-// integers and scaled by 2^(eA + f_c - 30).
+// Value output (last mode): the sum 2^VS (a0 + a1) is formed in 64-bit
+// integers (a0 exactly, a1 rounded) and scaled by 2^(eA + f_c + UNIT - VS).
 // The 16-column chunks of the tile are shared by `nparts` warps of the same
 // tensor-memory lane quarter; this one takes chunks part, part + nparts, ...
 // stg: this warp's 4 KB of staging shared memory for TMA stores of C
 // through tmC (null: plain stores); rw0 is the warp's first tile row.
+template <int F>
 __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, uint32_t lane_base, uint32_t ACOLS,
                                             int64_t ro, int64_t n0, int lane, int part, int nparts, uint8_t *stg,
                                             const CUtensorMap *tmC, int64_t rw0) {
@@ -446,7 +463,8 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, u
     const bool unit = (J.colC.R0 == 0 && J.colC.s0 == 1);
     const int64_t cs = J.colC.s0;
     const int step = 16 * nparts;
-    const int base = eA + 17 - eC;
+    using X = FxForm<F>;
+    const int base = eA + X::UNIT + X::BITS - eC;
     unsigned mx = 0;
     float mxf = 0.f;
     int cnt = 0;  // TMA stores issued by this warp
@@ -522,9 +540,11 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, u
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
                 const int f = __shfl_sync(0xffffffffu, fl, e);
-                const long long I0 = (long long)__float2int_rz(__uint_as_float(r0[e]));
-                const long long I1 = f32_round_i64(__uint_as_float(r1[e]) * 65536.0f);
-                v[e] = i64_scaled(I0 * 65536 + I1, eA + f - 30);
+                const float s1 = __uint_as_float(r1[e]) * (float)(1 << X::VS);
+                long long I0;
+                if constexpr (X::VS > 0) I0 = (long long)__float2int_rz(__uint_as_float(r0[e])) << X::VS;
+                else I0 = f32_round_i64(__uint_as_float(r0[e]));
+                v[e] = i64_scaled(I0 + f32_round_i64(s1), eA + f + X::UNIT - X::VS);
             }
             // the accumulate flag is tested outside the stores: no loads of C otherwise
             if (stg) {
@@ -574,7 +594,8 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, u
     }
     __syncwarp();
     if (J.cfix) {
-        // |X| <= |sum| + 2^7 + 1; capped at 2^31
+        // |X| <= |sum| + 2^7 + 1; capped at 2^31 (the rounding bound of
+        // FX32, where the conversion saturates; FX32H stays below 2^29 + 2^8)
         mx = (unsigned)fminf(mxf + 256.0f, 2147483648.0f);
         if (mxf == 0.f) mx = 0;
 #pragma unroll
@@ -587,6 +608,7 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, u
 // waits for its accumulators, drains this warp's column share, releases the
 // accumulators and publishes the tile.  `nbar` threads take part.
 // stg: the warp's staging memory (used when the job stores C by TMA).
+template <int F>
 __device__ __forceinline__ bool fx_epi_tile(const TcLaunch &L, int t, int it, uint32_t tmem, uint32_t ACOLS, int NBUF,
                                             uint64_t *accf, uint64_t *acce, FxConsts &k, int q, int lane, bool lead,
                                             int part, int nparts, int nbar, uint8_t *stg) {
@@ -602,11 +624,11 @@ __device__ __forceinline__ bool fx_epi_tile(const TcLaunch &L, int t, int it, ui
     tc_fence_after();
     const int64_t rg = (int64_t)mt * kBM + q * 32 + lane;
     const int64_t ro = rg < J.M ? imap(J.rowC, rg) : -1;
-    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * Regions<kFX32>::N) * ACOLS;
-    fx_consts(J, j, k);
+    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * Regions<F>::N) * ACOLS;
+    fx_consts<F>(J, j, k);
     if (J.cfix && lead && lane == 0) J.fxC->e = k.eC;
     const bool staged = stg != nullptr && J.tmc != 0;
-    fx_epilogue(J, k, lane_base, ACOLS, ro, (int64_t)nt * J.BN, lane, part, nparts, staged ? stg : nullptr,
+    fx_epilogue<F>(J, k, lane_base, ACOLS, ro, (int64_t)nt * J.BN, lane, part, nparts, staged ? stg : nullptr,
                 &job_at(L, j).tmC, (int64_t)mt * kBM + q * 32);
     tc_fence_before();
     __syncwarp();
@@ -650,7 +672,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
 
     // one accumulator buffer (fixed point, 256-column tiles): the converter
     // warps, idle while the MMA waits for the epilogue, take two thirds of it
-    const bool join = (F == kFX32) && NBUF == 1;
+    const bool join = is_fx_f<F>() && NBUF == 1;
     const int n_epi = kEpi + (join ? kConv : 0);
     // in that mode every A stage is free during the epilogue (the converters
     // fill them only after it): 4 KB of staging per epilogue warp
@@ -758,10 +780,10 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
         // ---------------------------------------------------------- epilogue
         const int q = warp & 3;                // TMEM lane quarter this warp may access
         int it = 0;
-        if constexpr (F == kFX32) {
+        if constexpr (is_fx_f<F>()) {
             FxConsts k;
             for (int t = blockIdx.x; t < L.total_tiles; t += gridDim.x, ++it)
-                if (!fx_epi_tile(L, t, it, tmem, ACOLS, NBUF, accf, acce, k, q, lane, warp == 2, 0, join ? 3 : 1,
+                if (!fx_epi_tile<F>(L, t, it, tmem, ACOLS, NBUF, accf, acce, k, q, lane, warp == 2, 0, join ? 3 : 1,
                                  32 * n_epi, stg))
                     break;
         } else
@@ -835,13 +857,13 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
         const int part = 1 + (warp - kConv0) / 4;
         FxConsts k;
         auto epi_prev = [&]() -> bool {
-            if constexpr (F != kFX32) {
+            if constexpr (!is_fx_f<F>()) {
                 return true;
             } else {
                 if (pend < 0) return true;
                 const int t = pend;
                 pend = -1;
-                if (!fx_epi_tile(L, t, pend_it, tmem, ACOLS, NBUF, accf, acce, k, warp & 3, lane, false, part, 3,
+                if (!fx_epi_tile<F>(L, t, pend_it, tmem, ACOLS, NBUF, accf, acce, k, warp & 3, lane, false, part, 3,
                                  32 * n_epi, stg))
                     return false;
                 // the A stages double as staging memory: wait until every
@@ -877,7 +899,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
                 }
                 named_bar(2, 32 * kConv);
             }
-            if constexpr (F == kFX32) {  // always 32-bit fixed point
+            if constexpr (is_fx_f<F>()) {  // always 32-bit integers
                 ok = conv_tile_loop_raw<F>(J, tm, rfull, rc, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct, epi_prev);
                 if (join) {
                     pend = t;
@@ -903,7 +925,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
 
 // ---------------------------------------------------------------- host side
 
-static int pieces_of_f(int form) { return form == kFX32 ? 4 : (form == kBF16x6 ? 3 : 2); }
+static int pieces_of_f(int form) { return form == kFX32 ? 4 : ((form == kBF16x6 || form == kFX32H) ? 3 : 2); }
 static int bk_of_f(int form) { return form == kTF32x3 ? kRowBytes / 4 : kRowBytes / 2; }
 
 size_t tcp_job_bytes() { return sizeof(TcJob); }
@@ -1071,7 +1093,7 @@ static void pick_config(int form, int bn_max, int nkb_max, int &stages, int &nac
     nbuf = std::min(2, budget);
     nacc = std::max(1, std::min(4, budget / nbuf));
     // the fixed-point form keeps one exact accumulator set per tile
-    if (nkb_max < 2 || form == kFX32) nacc = 1;
+    if (nkb_max < 2 || is_fx_form(form)) nacc = 1;
     const size_t a_st = (size_t)pieces_of_f(form) * kBM * kRowBytes;
     const size_t b_st = (size_t)pieces_of_f(form) * bn_max * kRowBytes;
     const size_t extra = 1024 + (size_t)(2 * 8 + 2 * 4 + 4 + 2) * 8;
@@ -1080,6 +1102,7 @@ static void pick_config(int form, int bn_max, int nkb_max, int &stages, int &nac
         case kTF32x3: raw = (size_t)RawCfg<kTF32x3>::STAGES * RawCfg<kTF32x3>::BYTES; break;
         case kBF16x3: raw = (size_t)RawCfg<kBF16x3>::STAGES * RawCfg<kBF16x3>::BYTES; break;
         case kFX32: raw = (size_t)RawCfg<kFX32>::STAGES * RawCfg<kFX32>::BYTES; break;
+        case kFX32H: raw = (size_t)RawCfg<kFX32H>::STAGES * RawCfg<kFX32H>::BYTES; break;
         default: raw = (size_t)RawCfg<kBF16x6>::STAGES * RawCfg<kBF16x6>::BYTES; break;
     }
     stages = 1;
@@ -1148,17 +1171,18 @@ static cudaError_t tcp_launch(int form, const TcJob *jobs, int njobs, int total_
         case kBF16x3: return launch_f<kBF16x3>(L, grid, smem, st);
         case kBF16x6: return launch_f<kBF16x6>(L, grid, smem, st);
         case kFX32: return launch_f<kFX32>(L, grid, smem, st);
+        case kFX32H: return launch_f<kFX32H>(L, grid, smem, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-// One fixed-point contraction: A is 32-bit fixed point with scale fxA, the
-// image of op(L) comes with its row exponents and row-sum bound; C is fixed
-// point with scale fxC (cfix) or a value tensor.
-cudaError_t tcp_contract_fx(const Contraction &c, const void *img, const FxScale *fxA, const int *fxF,
+// One fixed-point contraction of form `form`: A is fixed point (int32) with
+// scale fxA, the image of op(L) comes with its row exponents and row-sum
+// bound; C is fixed point with scale fxC (cfix) or a value tensor.
+cudaError_t tcp_contract_fx(int form, const Contraction &c, const void *img, const FxScale *fxA, const int *fxF,
                             const unsigned long long *fxG, FxScale *fxC, cudaStream_t st, FxScale *reset_next) {
     if (c.M == 0 || c.N == 0) return cudaSuccess;
-    TcJob J = make_job(kFX32, c, img);
+    TcJob J = make_job(form, c, img);
     J.fxA = fxA;
     J.fxF = fxF;
     J.fxG = fxG;
@@ -1166,28 +1190,28 @@ cudaError_t tcp_contract_fx(const Contraction &c, const void *img, const FxScale
     J.cfix = fxC != nullptr;
     J.a64 = 0;
     J.tile_begin = 0;
-    setup_tma(kFX32, J, c);
+    setup_tma(form, J, c);
     setup_tmc(J, c);
     const int tiles = J.tiles_m * J.tiles_n;
-    return tcp_launch(kFX32, &J, 1, tiles, J.BN, J.nkb, nullptr, nullptr, st, reset_next);
+    return tcp_launch(form, &J, 1, tiles, J.BN, J.nkb, nullptr, nullptr, st, reset_next);
 }
 
 // Rows r0..M-1 of a row map are the same map shifted by imap(m, r0): one
 // level, one slab holding all M rows, or r0 on a slab boundary.
 static bool shifts_at(const IdxMap &m, int64_t r0, int64_t M) { return m.R0 == 0 || M <= m.R0 || r0 % m.R0 == 0; }
 
-cudaError_t tcp_contract_fx_tail(const Contraction &c, const void *img, const void *img_half, const FxScale *fxA,
-                                 const int *fxF, const unsigned long long *fxG, FxScale *fxC, FxScale *reset_next,
-                                 cudaStream_t st) {
+cudaError_t tcp_contract_fx_tail(int form, const Contraction &c, const void *img, const void *img_half,
+                                 const FxScale *fxA, const int *fxF, const unsigned long long *fxG, FxScale *fxC,
+                                 FxScale *reset_next, cudaStream_t st) {
     if (c.M == 0 || c.N == 0) return cudaSuccess;
-    TcJob J = make_job(kFX32, c, img);
+    TcJob J = make_job(form, c, img);
     const int tiles = J.tiles_m * J.tiles_n;
     const int grid = num_sms();
     const int tail = tiles % grid;
     const int64_t R1 = (int64_t)(tiles - tail) * kBM;
     const bool split = img_half != nullptr && J.tiles_n == 1 && J.BN % 32 == 0 && tiles > grid && tail > 0 &&
                        2 * tail <= grid && !c.A_f64 && shifts_at(c.rowA, R1, c.M) && shifts_at(c.rowC, R1, c.M);
-    if (!split) return tcp_contract_fx(c, img, fxA, fxF, fxG, fxC, st, reset_next);
+    if (!split) return tcp_contract_fx(form, c, img, fxA, fxF, fxG, fxC, st, reset_next);
     // job 0: the full rounds
     J.M = R1;
     J.tiles_m = tiles - tail;
@@ -1198,15 +1222,15 @@ cudaError_t tcp_contract_fx_tail(const Contraction &c, const void *img, const vo
     J.cfix = fxC != nullptr;
     J.a64 = 0;
     J.tile_begin = 0;
-    setup_tma(kFX32, J, c);
+    setup_tma(form, J, c);
     setup_tmc(J, c);
     // job 1: the remaining rows in tiles of half the width
     Contraction cb = c;
     cb.M = c.M - R1;
     cb.A = static_cast<const int32_t *>(c.A) + imap(c.rowA, R1);
-    const size_t esC = c.C_f64 ? 8 : 4;  // FX32 output: int32 or a value tensor (FP32 / FP64)
+    const size_t esC = c.C_f64 ? 8 : 4;  // fixed-point output: int32 or a value tensor (FP32 / FP64)
     cb.C = static_cast<uint8_t *>(c.C) + (size_t)imap(c.rowC, R1) * esC;
-    TcJob H = make_job(kFX32, cb, img_half, J.BN / 2);
+    TcJob H = make_job(form, cb, img_half, J.BN / 2);
     H.fxA = fxA;
     H.fxF = fxF;
     H.fxG = fxG;
@@ -1214,10 +1238,10 @@ cudaError_t tcp_contract_fx_tail(const Contraction &c, const void *img, const vo
     H.cfix = fxC != nullptr;
     H.a64 = 0;
     H.tile_begin = J.tiles_m * J.tiles_n;
-    setup_tma(kFX32, H, cb);
+    setup_tma(form, H, cb);
     setup_tmc(H, cb);
     TcJob jobs[2] = {J, H};
-    return tcp_launch(kFX32, jobs, 2, H.tile_begin + H.tiles_m * H.tiles_n, J.BN, J.nkb, nullptr, nullptr, st,
+    return tcp_launch(form, jobs, 2, H.tile_begin + H.tiles_m * H.tiles_n, J.BN, J.nkb, nullptr, nullptr, st,
                       reset_next);
 }
 

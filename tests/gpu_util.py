@@ -14,7 +14,12 @@ import numpy as np
 #           (row's) largest magnitude, so random data with a spread of about
 #           4 between largest and typical values, summed over K terms, lands
 #           near sqrt(K) * 16 * 2^-32 = 4e-8 per product; bound 2e-7.
-TOL = {"fp64": 1e-12, "3xtf32": 2e-6, "bf16x6": 2e-6, "bf16x3": 6e-5, "fp32": 1e-5, "fx32": 2e-7}
+#  fx32h  : 29-bit fixed point (2^-29 of the largest magnitude, four times
+#           coarser than fx32) and three digit slices: the two level-3
+#           products left out are at most 2^-27 of the largest product per
+#           term, with no preferred sign; bound 1e-6.
+TOL = {"fp64": 1e-12, "3xtf32": 2e-6, "bf16x6": 2e-6, "bf16x3": 6e-5, "fp32": 1e-5, "fx32": 2e-7,
+       "fx32h": 1e-6}
 
 
 def tol(prec, ksum):

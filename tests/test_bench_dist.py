@@ -56,3 +56,4 @@ def test_single_rank_needs_no_process_group():
 def test_launch_count_of_the_fixed_point_stepper():
     # expm (one launch), E images (2 per mode), U -> fixed point (2), 300 mode products
     assert bench.launches_per_step("fx32") == 1 + 6 + 2 + 300
+    assert bench.launches_per_step("fx32h") == 1 + 6 + 2 + 300

@@ -35,14 +35,18 @@ def cfg_d3():
     return c, oracle.tucker(c.T, c.L)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "3xtf32", "bf16x3", "bf16x6", "fx32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "3xtf32", "bf16x3", "bf16x6", "fx32", "fx32h"])
 def test_tucker_d3_n100(kron, cfg_d3, prec):
     c, ref = cfg_d3
     S = kron.tucker(to_dev(c.T), [to_dev(L) for L in c.L], prec=prec)
     err = rel_err(to_host(S), ref)
     print(f"tucker d=3 n=100 {prec}: max-norm rel err {err:.3e}")
-    # the workload budget for every split form, the fixed-point one included
-    assert err <= (2e-6 if prec == "fx32" else TOL[prec]), err
+    # the workload budget for every split form, fx32 included.  fx32h: every
+    # intermediate state takes its scale from the row-sum bound of |L_mu|,
+    # which on these Gaussian operators is about 9 times the typical output
+    # (about 3 of its 29 bits unused per mode); measured 1.9e-6, bound 4e-6
+    bound = {"fx32": 2e-6, "fx32h": 4e-6}.get(prec, TOL[prec])
+    assert err <= bound, err
 
 
 @pytest.fixture(scope="module")
@@ -54,11 +58,11 @@ def cfg_d6():
     return c, idx, ref
 
 
-@pytest.mark.parametrize("prec", ["fp64", "3xtf32", "bf16x3", "bf16x6", "fp32", "fx32"])
+@pytest.mark.parametrize("prec", ["fp64", "3xtf32", "bf16x3", "bf16x6", "fp32", "fx32", "fx32h"])
 def test_tucker_d6_n20_sampled(kron, cfg_d6, prec):
     import torch
     c, idx, ref = cfg_d6
-    dtype = torch.float64 if prec in ("fp64", "fx32") else torch.float32
+    dtype = torch.float64 if prec in ("fp64", "fx32", "fx32h") else torch.float32
     S = kron.tucker(to_dev(c.T, dtype), [to_dev(L, dtype) for L in c.L], prec=prec)
     ix = [torch.as_tensor(i, device=S.device) for i in idx]
     sub = S
@@ -86,13 +90,15 @@ def test_stepper_fp64_100_steps(kron, cfg_stepper):
     assert kron.device_error() == 0
 
 
-def test_stepper_fx32_100_steps(kron, cfg_stepper):
-    """The fixed-point form keeps about 31 bits per value and per product, so
-    the 300 chained mode products of the 100 steps stay within 2e-6."""
+@pytest.mark.parametrize("prec", ["fx32", "fx32h"])
+def test_stepper_fx32_100_steps(kron, cfg_stepper, prec):
+    """The fixed-point forms keep about 31 (fx32) or 29 (fx32h) bits per value
+    and per product, so the 300 chained mode products of the 100 steps stay
+    within 2e-6."""
     c, ref = cfg_stepper
-    U = kron.expkronsum_step(to_dev(c.U0), [to_dev(A) for A in c.A], c.tau, c.nsteps, prec="fx32")
+    U = kron.expkronsum_step(to_dev(c.U0), [to_dev(A) for A in c.A], c.tau, c.nsteps, prec=prec)
     err = rel_err(to_host(U), ref)
-    print(f"stepper fx32 100 steps: {err:.3e}")
+    print(f"stepper {prec} 100 steps: {err:.3e}")
     assert err <= 2e-6
     assert kron.device_error() == 0
 

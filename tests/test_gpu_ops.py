@@ -10,7 +10,7 @@ from gpu_util import TOL, rel_err, to_dev, to_host, tol
 pytestmark = pytest.mark.gpu
 
 RNG = np.random.default_rng(2024)
-PRECS = ["fp64", "fp32", "3xtf32", "bf16x3", "bf16x6", "fx32"]
+PRECS = ["fp64", "fp32", "3xtf32", "bf16x3", "bf16x6", "fx32", "fx32h"]
 
 
 def rnd(*s):
@@ -103,7 +103,7 @@ def test_kronsumv_matches_oracle(kron, shape, prec):
     assert kron.device_error() == 0
 
 
-@pytest.mark.parametrize("prec", ["fp64", "3xtf32", "fx32"])
+@pytest.mark.parametrize("prec", ["fp64", "3xtf32", "fx32", "fx32h"])
 def test_kronsumv_transposed_and_float32(kron, prec):
     import torch
     shape = (11, 23, 5)
@@ -141,7 +141,7 @@ def test_itucker_matches_oracle(kron, shape, prec):
     assert kron.device_error() == 0
 
 
-@pytest.mark.parametrize("prec", ["fp32", "3xtf32", "bf16x3", "bf16x6", "fx32"])
+@pytest.mark.parametrize("prec", ["fp32", "3xtf32", "bf16x3", "bf16x6", "fx32", "fx32h"])
 def test_itucker_refinement_reaches_fp64_accuracy(kron, prec):
     """FP64-residual iterative refinement of the low-precision chain."""
     shape = (9, 33, 17)
@@ -153,7 +153,7 @@ def test_itucker_refinement_reaches_fp64_accuracy(kron, prec):
     assert e3 <= 1e-12 and e3 < e0 / 100, (prec, e0, e3)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "3xtf32", "fx32"])
+@pytest.mark.parametrize("prec", ["fp64", "3xtf32", "fx32", "fx32h"])
 def test_itucker_transposed_and_float32(kron, prec):
     import torch
     shape = (11, 23, 5)
@@ -178,7 +178,8 @@ def test_itucker_singular_matrix_sets_the_numeric_flag(kron):
     assert kron.device_error() == 0  # cleared by the read
 
 
-def test_fx32_rows_far_below_the_largest_row_sum(kron):
+@pytest.mark.parametrize("prec", ["fx32", "fx32h"])
+def test_fx32_rows_far_below_the_largest_row_sum(kron, prec):
     """Rows of op(L_mu) whose magnitude is far below the largest row sum: in
     the fixed-point chain their products are scaled down (a negative shift)
     before rounding, and must keep their own scale (Eq. (tuckerop))."""
@@ -188,8 +189,8 @@ def test_fx32_rows_far_below_the_largest_row_sum(kron):
         L[3, :] *= 2.0 ** -20
         L[5, :] *= 2.0 ** -12
     ref = oracle.tucker(T, Ls)
-    S = kron.tucker(to_dev(T), [to_dev(L) for L in Ls], prec="fx32")
-    assert rel_err(to_host(S), ref) <= TOL["fx32"]
+    S = kron.tucker(to_dev(T), [to_dev(L) for L in Ls], prec=prec)
+    assert rel_err(to_host(S), ref) <= TOL[prec]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "3xtf32"])
