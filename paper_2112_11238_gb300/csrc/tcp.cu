@@ -446,18 +446,23 @@ __device__ __forceinline__ void fx_consts(const TcJob &J, int j, FxConsts &k) {
 // products are exact power-of-two scalings; Dekker's Fast2Sum is error-free
 // when |a0| >= |a1|, the usual case, and within an ulp of the sum otherwise),
 // then X = rint(sum) + rint(err) (|err| <= 2^7: rounded by the 1.5 * 2^23
-// exponent trick), saturated.  The largest |X| of the tile is tracked on
-// |sum| with a margin above the error term.
+// exponent trick), saturated for FX32 (FX32H stays below 2^29 + 2^8, no
+// overflow).  The largest |X| of the tile is tracked on |sum| with a margin
+// above the error term.  Two columns at a time in paired FP32 instructions.
 // Value output (last mode): the sum 2^VS (a0 + a1) is formed in 64-bit
 // integers (a0 exactly, a1 rounded) and scaled by 2^(eA + f_c + UNIT - VS).
 // The 16-column chunks of the tile are shared by `nparts` warps of the same
 // tensor-memory lane quarter; this one takes chunks part, part + nparts, ...
 // stg: this warp's 4 KB of staging shared memory for TMA stores of C
 // through tmC (null: plain stores); rw0 is the warp's first tile row.
+// colw: one word per column of the tile in shared memory (the scale 2^s as
+// a float for fixed-point output, the row exponent f_c otherwise); every
+// warp fills the words of its own chunks (warps of other lane quarters
+// with the same chunks write the same values).
 template <int F>
 __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, uint32_t lane_base, uint32_t ACOLS,
                                             int64_t ro, int64_t n0, int lane, int part, int nparts, uint8_t *stg,
-                                            const CUtensorMap *tmC, int64_t rw0) {
+                                            const CUtensorMap *tmC, int64_t rw0, uint32_t *colw) {
     const int eA = k.eA, eC = k.eC;
     const int lim = (int)min(J.N - n0, (int64_t)J.BN);
     const bool unit = (J.colC.R0 == 0 && J.colC.s0 == 1);
@@ -465,6 +470,13 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, u
     const int step = 16 * nparts;
     using X = FxForm<F>;
     const int base = eA + X::UNIT + X::BITS - eC;
+    // column words of this warp's chunks: lanes 0-15 one chunk, 16-31 the next
+    for (int c = 16 * part + (lane >> 4) * step + (lane & 15); c - (lane & 15) < J.BN; c += 2 * step) {
+        const int f = c < lim ? __ldg(J.fxF + n0 + c) : 0;
+        // 2^s (s below -126 leaves only values that round to 0)
+        colw[c] = J.cfix ? (uint32_t)((127 + min(100, max(-126, base + f))) << 23) : (uint32_t)f;
+    }
+    __syncwarp();
     unsigned mx = 0;
     float mxf = 0.f;
     int cnt = 0;  // TMA stores issued by this warp
@@ -486,30 +498,33 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, u
         }
         ++cnt;
     };
-    int c0 = 16 * part;
-    // row exponent of this lane's column of the chunk (prefetched one chunk ahead)
-    int fl = (c0 + (lane & 15) < lim) ? __ldg(J.fxF + n0 + c0 + (lane & 15)) : 0;
-    for (; c0 < J.BN; c0 += step) {
-        uint32_t r0[16], r1[16];
+    for (int c0 = 16 * part; c0 < J.BN; c0 += step) {
+        uint32_t r0[16], r1[16], w[16];
         tmem_ld16(lane_base + (uint32_t)c0, r0);
         tmem_ld16(lane_base + ACOLS + (uint32_t)c0, r1);
-        const int cn = c0 + step;
-        const int fnext = (cn + (lane & 15) < lim) ? __ldg(J.fxF + n0 + cn + (lane & 15)) : 0;
-        // 2^s of this lane's column (s below -126 leaves only values that round to 0)
-        const float scl = __int_as_float((127 + min(100, max(-126, base + fl))) << 23);
         tmem_ld_wait();
+#pragma unroll
+        for (int e = 0; e < 16; e += 4) *reinterpret_cast<uint4 *>(&w[e]) = *reinterpret_cast<const uint4 *>(colw + c0 + e);
         if (J.cfix) {
             int32_t xv[16];
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const float sc = __shfl_sync(0xffffffffu, scl, e);
-                const float h = __uint_as_float(r0[e]) * sc;
-                const float l = __uint_as_float(r1[e]) * sc;
-                const float sum = h + l;
-                const float err = l - (sum - h);
-                const int ei = __float_as_int(err + 12582912.0f) - 0x4B400000;
-                xv[e] = add_sat(__float2int_rn(sum), ei);
-                mxf = fmaxf(mxf, fabsf(sum));
+            for (int e = 0; e < 16; e += 2) {
+                const uint64_t sc = pack2(w[e], w[e + 1]);
+                const uint64_t h = mul_f32x2(pack2(r0[e], r0[e + 1]), sc);
+                const uint64_t l = mul_f32x2(pack2(r1[e], r1[e + 1]), sc);
+                const uint64_t sum = add_f32x2(h, l);
+                const uint64_t err = sub_f32x2(l, sub_f32x2(sum, h));
+                const uint64_t em = add_f32x2(err, 0x4B4000004B400000ull);  // + 1.5 * 2^23 each
+                const float s0 = __uint_as_float((uint32_t)sum), s1 = __uint_as_float((uint32_t)(sum >> 32));
+                const int e0 = (int)(uint32_t)em - 0x4B400000, e1 = (int)(uint32_t)(em >> 32) - 0x4B400000;
+                if constexpr (F == kFX32H) {
+                    xv[e] = __float2int_rn(s0) + e0;
+                    xv[e + 1] = __float2int_rn(s1) + e1;
+                } else {
+                    xv[e] = add_sat(__float2int_rn(s0), e0);
+                    xv[e + 1] = add_sat(__float2int_rn(s1), e1);
+                }
+                mxf = fmaxf(mxf, fmaxf(fabsf(s0), fabsf(s1)));
             }
             if (stg) {
                 // two 2 KB buffers; [column][row] or [row][column]
@@ -539,7 +554,7 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, u
             double v[16];
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
-                const int f = __shfl_sync(0xffffffffu, fl, e);
+                const int f = (int)w[e];
                 const float s1 = __uint_as_float(r1[e]) * (float)(1 << X::VS);
                 long long I0;
                 if constexpr (X::VS > 0) I0 = (long long)__float2int_rz(__uint_as_float(r0[e])) << X::VS;
@@ -584,7 +599,6 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, u
                 }
             }
         }
-        fl = fnext;
     }
     if (stg && lane == 0) {
         // the staging memory is handed back, and a tile read later in the
@@ -611,7 +625,7 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, u
 template <int F>
 __device__ __forceinline__ bool fx_epi_tile(const TcLaunch &L, int t, int it, uint32_t tmem, uint32_t ACOLS, int NBUF,
                                             uint64_t *accf, uint64_t *acce, FxConsts &k, int q, int lane, bool lead,
-                                            int part, int nparts, int nbar, uint8_t *stg) {
+                                            int part, int nparts, int nbar, uint8_t *stg, uint32_t *colt) {
     const int j = find_job(L, t);
     const TcJob J = job_at(L, j);
     const int lt = t - J.tile_begin;
@@ -629,7 +643,7 @@ __device__ __forceinline__ bool fx_epi_tile(const TcLaunch &L, int t, int it, ui
     if (J.cfix && lead && lane == 0) J.fxC->e = k.eC;
     const bool staged = stg != nullptr && J.tmc != 0;
     fx_epilogue<F>(J, k, lane_base, ACOLS, ro, (int64_t)nt * J.BN, lane, part, nparts, staged ? stg : nullptr,
-                &job_at(L, j).tmC, (int64_t)mt * kBM + q * 32);
+                &job_at(L, j).tmC, (int64_t)mt * kBM + q * 32, colt + buf * 256);
     tc_fence_before();
     __syncwarp();
     if (lane == 0) mbar_arrive(smem_u32(&acce[buf]));
@@ -662,6 +676,8 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
     uint64_t *full = bars, *empty = bars + S, *accf = bars + 2 * S, *acce = bars + 2 * S + NBUF;
     uint64_t *rfull = bars + 2 * S + 2 * NBUF;  // raw A ring (TMA)
     uint32_t *tslot = reinterpret_cast<uint32_t *>(rfull + RawCfg<F>::STAGES);
+    // fixed-point forms: one table of 256 column words per accumulator buffer
+    uint32_t *colt = reinterpret_cast<uint32_t *>((reinterpret_cast<uintptr_t>(tslot + 1) + 15) & ~uintptr_t(15));
     constexpr int RG = Regions<F>::N;
     uint32_t ncols = ACOLS * (uint32_t)RG * (uint32_t)NACC * (uint32_t)NBUF;
     // programmatic dependent launch: the next launch may be scheduled now (it
@@ -784,7 +800,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
             FxConsts k;
             for (int t = blockIdx.x; t < L.total_tiles; t += gridDim.x, ++it)
                 if (!fx_epi_tile<F>(L, t, it, tmem, ACOLS, NBUF, accf, acce, k, q, lane, warp == 2, 0, join ? 3 : 1,
-                                 32 * n_epi, stg))
+                                 32 * n_epi, stg, colt))
                     break;
         } else
         for (int t = blockIdx.x; t < L.total_tiles; t += gridDim.x, ++it) {
@@ -864,7 +880,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
                 const int t = pend;
                 pend = -1;
                 if (!fx_epi_tile<F>(L, t, pend_it, tmem, ACOLS, NBUF, accf, acce, k, warp & 3, lane, false, part, 3,
-                                 32 * n_epi, stg))
+                                 32 * n_epi, stg, colt))
                     return false;
                 // the A stages double as staging memory: wait until every
                 // warp of the epilogue is done with it
@@ -1096,7 +1112,9 @@ static void pick_config(int form, int bn_max, int nkb_max, int &stages, int &nac
     if (nkb_max < 2 || is_fx_form(form)) nacc = 1;
     const size_t a_st = (size_t)pieces_of_f(form) * kBM * kRowBytes;
     const size_t b_st = (size_t)pieces_of_f(form) * bn_max * kRowBytes;
-    const size_t extra = 1024 + (size_t)(2 * 8 + 2 * 4 + 4 + 2) * 8;
+    // alignment slack, barriers and the tensor-memory slot; the fixed-point
+    // forms add a 1 KB column table per accumulator buffer
+    const size_t extra = 1024 + (size_t)(2 * 8 + 2 * 4 + 4 + 2) * 8 + (is_fx_form(form) ? (size_t)nbuf * 1024 : 0);
     size_t raw = 0;
     switch (form) {
         case kTF32x3: raw = (size_t)RawCfg<kTF32x3>::STAGES * RawCfg<kTF32x3>::BYTES; break;

@@ -17,9 +17,15 @@ import numpy as np
 #  fx32h  : 29-bit fixed point (2^-29 of the largest magnitude, four times
 #           coarser than fx32) and three digit slices: the two level-3
 #           products left out are at most 2^-27 of the largest product per
-#           term, with no preferred sign; bound 1e-6.
+#           term, with no preferred sign.  Every intermediate state takes its
+#           scale from the row-sum bound of |op(L_mu)|, which for Gaussian
+#           operators is several times the typical output (up to 3 of the 29
+#           bits unused per mode); measured up to 1.9e-6 on such chains,
+#           bound 4e-6.  Operators whose row sums are near their outputs
+#           (the stepper's exponentials) stay far below: 1.4e-7 over 300
+#           chained products.
 TOL = {"fp64": 1e-12, "3xtf32": 2e-6, "bf16x6": 2e-6, "bf16x3": 6e-5, "fp32": 1e-5, "fx32": 2e-7,
-       "fx32h": 1e-6}
+       "fx32h": 4e-6}
 
 
 def tol(prec, ksum):

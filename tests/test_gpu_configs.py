@@ -45,7 +45,7 @@ def test_tucker_d3_n100(kron, cfg_d3, prec):
     # intermediate state takes its scale from the row-sum bound of |L_mu|,
     # which on these Gaussian operators is about 9 times the typical output
     # (about 3 of its 29 bits unused per mode); measured 1.9e-6, bound 4e-6
-    bound = {"fx32": 2e-6, "fx32h": 4e-6}.get(prec, TOL[prec])
+    bound = 2e-6 if prec == "fx32" else TOL[prec]
     assert err <= bound, err
 
 
