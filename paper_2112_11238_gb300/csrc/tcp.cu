@@ -479,26 +479,36 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, u
     __syncwarp();
     unsigned mx = 0;
     float mxf = 0.f;
-    int cnt = 0;  // TMA stores issued by this warp
-    // one 16-column box: wait until its buffer is free, then write it (fill
-    // writes this lane's row), hand it to the TMA unit
-    auto stage = [&](int nb, uint8_t *buf, int64_t col, auto &&fill) {
-        if (lane == 0 && cnt >= nb) {
-            if (nb == 2) bulk_wait_read<1>();
-            else bulk_wait_read<0>();
-        }
+    int cnt = 0;       // boxes staged by this warp
+    int64_t pcol = 0;  // column of the first box of the pending group
+    // 16-column boxes in groups of nb (nb buffers of bbytes each): the first
+    // box of a group waits until the previous group has been read, fill
+    // writes this lane's row; a full group (or the last box) is fenced once
+    // and handed to the TMA unit
+    auto stage = [&](int nb, int bbytes, int64_t col, bool last, auto &&fill) {
+        const int b = cnt % nb;
+        if (b == 0 && cnt >= nb && lane == 0) bulk_wait_read<0>();
         __syncwarp();
-        fill(buf);
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0 && rw0 < J.M) {  // boxes wholly past the last row are not stored
-            if (J.tmc == 3) tma_store_3d(tmC, smem_u32(buf), (int)(rw0 % J.tmcP), (int)col, (int)(rw0 / J.tmcP));
-            else tma_store_2d(tmC, smem_u32(buf), (int)col, (int)rw0);
-            bulk_commit();
-        }
+        fill(stg + b * bbytes);
+        if (b == 0) pcol = col;
         ++cnt;
+        if (b == nb - 1 || last) {
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0 && rw0 < J.M) {  // boxes wholly past the last row are not stored
+                for (int i = 0; i <= b; ++i) {
+                    const uint32_t src = smem_u32(stg + i * bbytes);
+                    // boxes of a group are `step` columns apart
+                    const int cb = (int)(pcol + (int64_t)i * step);
+                    if (J.tmc == 3) tma_store_3d(tmC, src, (int)(rw0 % J.tmcP), cb, (int)(rw0 / J.tmcP));
+                    else tma_store_2d(tmC, src, cb, (int)rw0);
+                }
+                bulk_commit();
+            }
+        }
     };
     for (int c0 = 16 * part; c0 < J.BN; c0 += step) {
+        const bool last = c0 + step >= J.BN;
         uint32_t r0[16], r1[16], w[16];
         tmem_ld16(lane_base + (uint32_t)c0, r0);
         tmem_ld16(lane_base + ACOLS + (uint32_t)c0, r1);
@@ -527,8 +537,8 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, u
                 mxf = fmaxf(mxf, fmaxf(fabsf(s0), fabsf(s1)));
             }
             if (stg) {
-                // two 2 KB buffers; [column][row] or [row][column]
-                stage(2, stg + (cnt & 1) * 2048, n0 + c0, [&](uint8_t *buf) {
+                // groups of two 2 KB boxes; [column][row] or [row][column]
+                stage(2, 2048, n0 + c0, last, [&](uint8_t *buf) {
                     if (J.tmc == 3) {
 #pragma unroll
                         for (int e = 0; e < 16; ++e) reinterpret_cast<int32_t *>(buf)[e * 32 + lane] = xv[e];
@@ -564,7 +574,7 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, u
             // the accumulate flag is tested outside the stores: no loads of C otherwise
             if (stg) {
                 // one 4 KB buffer of doubles (value output is FP64 when staged)
-                stage(1, stg, n0 + c0, [&](uint8_t *buf) {
+                stage(1, 4096, n0 + c0, last, [&](uint8_t *buf) {
                     if (J.tmc == 3) {
 #pragma unroll
                         for (int e = 0; e < 16; ++e) reinterpret_cast<double *>(buf)[e * 32 + lane] = v[e];
