@@ -87,7 +87,8 @@ typedef enum kron_dtype { KRON_F64 = 0, KRON_F32 = 1 } kron_dtype;
  *                     64-bit integer arithmetic.  About 31 significant bits
  *                     per stored value and per product, for contraction
  *                     lengths up to 256; intermediates are 32-bit fixed point.
- *                     Supported by kron_mump, kron_tucker and the stepper.
+ *                     Supported by kron_mump, kron_tucker, kron_kronsumv,
+ *                     kron_itucker and the stepper (not by the adjoint).
  *  KRON_PREC_FX32H  : the same scheme with 29-bit fixed point cut into three
  *                     balanced digits of 8, 11 and 11 bits stored exactly as
  *                     FP16 slices d0 2^8, d1 2^-3, d2 2^-14 (all in the normal
