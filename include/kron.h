@@ -212,6 +212,34 @@ KRON_API kron_status kron_tucker_adjoint(kron_plan plan, const void *T, const vo
                                 kron_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Complex Tucker operator: Eq. (tuckerop) over C; conjugate transposes as   */
+/* in the remark after Eq. (tensinterp) (the paper's cttucker)               */
+/* ------------------------------------------------------------------------ */
+/*
+ * S = T x_1 op(L_1) x_2 ... x_d op(L_d) for complex T, L_mu and S, with
+ *   op(L) = L     (L is n_mu x m_mu)          plan without KRON_PLAN_TRANS_L,
+ *   op(L) = L^T   (L is m_mu x n_mu)          plan with KRON_PLAN_TRANS_L, conj = 0,
+ *   op(L) = L^*   (conjugate transpose)       plan with KRON_PLAN_TRANS_L, conj = 1,
+ * the last being the paper's cttucker: the evaluation of a pseudospectral
+ * decomposition at the quadrature points with Phi_mu = Psi_mu^* without
+ * forming Phi_mu.  conj = 1 without KRON_PLAN_TRANS_L gives op(L) = conj(L).
+ * Storage: complex values as interleaved (real, imaginary) pairs of the
+ * plan's dtype (KRON_F64: complex double, KRON_F32: complex float);
+ * tensors column-major with the plan's sizes m (T) and n (S) counted in
+ * complex elements; ldL[mu] in complex elements.  Pointers aligned to one
+ * complex element.  Each complex mu-mode product runs as one real
+ * contraction of twice the length over the (real, imaginary) view of the
+ * tensor, with the real 2n_mu x 2m_mu matrix [[Re G, -Im G], [Im G, Re G]]
+ * (G = op(L_mu), entries interleaved as the tensor's) built in the
+ * workspace.  Precisions: KRON_PREC_FP64, FP32, 3XTF32, BF16X3, BF16X6
+ * (the fixed-point forms return KRON_ERR_UNSUPPORTED).  T and S must not
+ * alias.
+ */
+KRON_API kron_status kron_ctucker_workspace_size(kron_plan plan, size_t *bytes);
+KRON_API kron_status kron_ctucker(kron_plan plan, const void *T, const void *const *L, const int64_t *ldL,
+                                  int conj, void *S, void *ws, size_t ws_bytes, kron_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Action of a Kronecker sum: Section 2, Eq. (actkron)                       */
 /* ------------------------------------------------------------------------ */
 /*

@@ -210,6 +210,48 @@ def kronsumv(V, Ls) -> np.ndarray:
     return S
 
 
+def ctucker(T, Ls, transL: bool = False, conj: bool = False) -> np.ndarray:
+    """Complex Tucker operator T x_1 op(L_1) ... x_d op(L_d) (Eq. (tuckerop) over C),
+    op(L) = L, L^T (transL) or the conjugate of either (conj); transL with conj
+    is the conjugate transpose of the remark after Eq. (tensinterp) (cttucker).
+
+    Mode by mode in the order 1..d, each mu-mode product by its definition
+    S^{(mu)} = op(L_mu) X^{(mu)} (Eq. (mmp)) on the mu-unfolding, in complex128
+    (numpy.tensordot as the matrix product)."""
+    X = np.array(T, dtype=np.complex128)
+    for mu in range(X.ndim):
+        G = np.asarray(Ls[mu], dtype=np.complex128)
+        if transL:
+            G = G.T
+        if conj:
+            G = G.conj()
+        X = np.moveaxis(np.tensordot(G, X, axes=([1], [mu])), 0, mu)
+    return np.asfortranarray(X)
+
+
+def ctucker_nested(T, Ls, transL: bool = False, conj: bool = False) -> np.ndarray:
+    """Brute-force element-wise sum of Eq. (nestedmumode) over C (tiny inputs):
+    S[l_1..l_d] = sum_{i_1..i_d} T[i_1..i_d] prod_mu op(L_mu)[l_mu, i_mu]."""
+    import itertools
+    T = np.asarray(T, dtype=np.complex128)
+    Gs = []
+    for L in Ls:
+        G = np.asarray(L, dtype=np.complex128)
+        G = G.T if transL else G
+        Gs.append(G.conj() if conj else G)
+    n = [G.shape[0] for G in Gs]
+    S = np.zeros(n, dtype=np.complex128)
+    for l in itertools.product(*[range(v) for v in n]):
+        acc = 0j
+        for i in itertools.product(*[range(v) for v in T.shape]):
+            w = T[i]
+            for mu in range(T.ndim):
+                w = w * Gs[mu][l[mu], i[mu]]
+            acc += w
+        S[l] = acc
+    return S
+
+
 def itucker(V, Ps, transL: bool = False) -> np.ndarray:
     """V x_1 op(P_1)^{-1} x_2 ... x_d op(P_d)^{-1} (Section 3.4, Eq. (preconnd)).
 

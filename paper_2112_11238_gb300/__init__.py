@@ -66,6 +66,8 @@ _sig("kron_plan_workspace_size", [_vp, ctypes.POINTER(_sz)])
 _sig("kron_plan_order", [_vp, ctypes.POINTER(_ci)])
 _sig("kron_plan_flops", [_vp], ctypes.c_double)
 _sig("kron_tucker", [_vp, _vp, ctypes.POINTER(_vp), _i64p, _vp, _vp, _sz, _vp])
+_sig("kron_ctucker_workspace_size", [_vp, ctypes.POINTER(_sz)])
+_sig("kron_ctucker", [_vp, _vp, ctypes.POINTER(_vp), _i64p, _ci, _vp, _vp, _sz, _vp])
 _sig("kron_kronsumv_workspace_size", [_vp, ctypes.POINTER(_sz)])
 _sig("kron_kronsumv", [_vp, _vp, ctypes.POINTER(_vp), _i64p, _vp, _vp, _sz, _vp])
 _sig("kron_itucker_workspace_size", [_vp, _ci, ctypes.POINTER(_sz)])
@@ -90,7 +92,7 @@ _sig("kron_batched_run", [_vp, _vp, _sz, _vp])
 EXPORTS = [
     "kron_status_string", "kron_version", "kron_get_device_error", "kron_mump_workspace_size",
     "kron_mump", "kron_mump_noalloc", "kron_plan_create", "kron_plan_destroy", "kron_plan_workspace_size",
-    "kron_plan_order", "kron_plan_flops", "kron_tucker", "kron_kronsumv_workspace_size", "kron_kronsumv", "kron_itucker_workspace_size", "kron_itucker", "kron_kronsum_pcg_workspace_size", "kron_kronsum_pcg", "kron_adjoint_workspace_size",
+    "kron_plan_order", "kron_plan_flops", "kron_tucker", "kron_ctucker_workspace_size", "kron_ctucker", "kron_kronsumv_workspace_size", "kron_kronsumv", "kron_itucker_workspace_size", "kron_itucker", "kron_kronsum_pcg_workspace_size", "kron_kronsum_pcg", "kron_adjoint_workspace_size",
     "kron_tucker_adjoint", "kron_expm_workspace_size", "kron_expm",
     "kron_expkronsum_workspace_size", "kron_expkronsum_step", "kron_expkronsum_apply",
     "kron_batched_plan_create", "kron_batched_plan_destroy", "kron_batched_workspace_size",
@@ -250,7 +252,8 @@ class TuckerPlan:
         self.trans = trans
         flags = (PLAN_TRANS_L if trans else 0) | (PLAN_NATURAL_ORDER if natural_order else 0)
         h = ctypes.c_void_p()
-        dt = F64 if dtype == torch.float64 else F32
+        # complex plans take the dtype of the real and imaginary parts
+        dt = F64 if dtype in (torch.float64, torch.complex128) else F32
         _check(_lib.kron_plan_create(ctypes.byref(h), self.d, _i64(self.m), _i64(self.n), dt, _prec(prec), flags),
                "kron_plan_create")
         self._h = h
@@ -299,6 +302,26 @@ class TuckerPlan:
             ws = self.workspace(T.device)
         _check(_lib.kron_tucker(self._h, T.data_ptr(), _ptrs([L for L, _ in mats]), _i64([ld for _, ld in mats]),
                                 S.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)), "kron_tucker")
+        return S
+
+    def ctucker_workspace_bytes(self) -> int:
+        b = ctypes.c_size_t(0)
+        _check(_lib.kron_ctucker_workspace_size(self._h, ctypes.byref(b)), "kron_ctucker_workspace_size")
+        return b.value
+
+    def ctucker_into(self, T, Ls, S, conj: bool = False, ws=None, stream=None):
+        """Complex Tucker operator S = T x_1 op(L_1) ... x_d op(L_d) with op(L) = L, L^T
+        (trans plan) and their conjugates (conj); the paper's cttucker is a trans plan
+        with conj.  T, L_mu, S complex (complex128 / complex64), column-major."""
+        _require_cuda(T, S, *Ls)
+        if not (T.is_complex() and S.is_complex() and all(L.is_complex() for L in Ls)):
+            raise ValueError("ctucker takes complex tensors")
+        mats = [_mat(L) for L in Ls]
+        if ws is None:
+            ws = _workspace(self.ctucker_workspace_bytes(), T.device)
+        _check(_lib.kron_ctucker(self._h, T.data_ptr(), _ptrs([L for L, _ in mats]), _i64([ld for _, ld in mats]),
+                                 int(bool(conj)), S.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)),
+               "kron_ctucker")
         return S
 
     def kronsumv_workspace_bytes(self) -> int:
@@ -378,6 +401,26 @@ def tucker(T: torch.Tensor, Ls, prec="fp64", trans: bool = False, natural_order:
     plan = TuckerPlan(T.shape, n, T.dtype, prec, trans, natural_order)
     S = empty_colmajor(n, T.dtype, T.device)
     return plan.tucker_into(T, Ls, S, stream=stream)
+
+
+def ctucker(T: torch.Tensor, Ls, prec="fp64", trans: bool = False, conj: bool = False,
+            natural_order: bool = False, stream=None) -> torch.Tensor:
+    """Complex Tucker operator T x_1 op(L_1) ... x_d op(L_d) (Eq. (tuckerop) over C),
+    op(L) = L, L^T (trans) or their conjugates (conj)."""
+    T = colmajor(T)
+    if not T.is_complex():
+        raise ValueError("ctucker takes a complex tensor")
+    Ls = [L.to(T.dtype) for L in Ls]
+    n = [(L.shape[1] if trans else L.shape[0]) for L in Ls]
+    plan = TuckerPlan(T.shape, n, T.dtype, prec, trans, natural_order)
+    S = empty_colmajor(n, T.dtype, T.device)
+    return plan.ctucker_into(T, Ls, S, conj=conj, stream=stream)
+
+
+def cttucker(T: torch.Tensor, Psis, prec="fp64", stream=None) -> torch.Tensor:
+    """T x_1 Psi_1^* x_2 ... x_d Psi_d^* (conjugate transposes; the remark after
+    Eq. (tensinterp)): evaluation at the quadrature points without forming Psi_mu^*."""
+    return ctucker(T, Psis, prec=prec, trans=True, conj=True, stream=stream)
 
 
 def kronsumv(V: torch.Tensor, Ls, prec="fp64", trans: bool = False, stream=None) -> torch.Tensor:

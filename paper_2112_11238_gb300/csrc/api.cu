@@ -466,6 +466,146 @@ kron_status kron_tucker(kron_plan plan, const void *T, const void *const *L, con
                      reinterpret_cast<cudaStream_t>(stream), trans);
 }
 
+// ------------------------------------------------------ complex Tucker
+//
+// Workspace: [M_mu x d: real 2n x 2m matrices][images x d][X0][X1]
+namespace {
+
+struct CtLayout {
+    size_t M[KRON_MAX_D], img[KRON_MAX_D], buf[2], total;
+};
+
+CtLayout ct_layout(const kron_plan_s *pl) {
+    CtLayout s{};
+    const int d = pl->d;
+    const int form = form_of(pl->prec);
+    const size_t es = esize(pl->dtype);
+    size_t off = 0;
+    for (int k = 0; k < d; ++k) {
+        s.M[k] = off;
+        off += align_up((size_t)(4 * pl->n[k] * pl->m[k]) * es);
+    }
+    for (int k = 0; k < d; ++k) {
+        s.img[k] = off;
+        off += align_up(form >= 0 ? tc_bimage_bytes(form, 2 * pl->n[k], 2 * pl->m[k]) : 0);
+    }
+    int64_t cur[KRON_MAX_D];
+    for (int k = 0; k < d; ++k) cur[k] = pl->m[k];
+    int64_t mx = 0;
+    for (int st = 0; st < d - 1; ++st) {
+        cur[pl->order[st]] = pl->n[pl->order[st]];
+        mx = std::max(mx, prod(cur, 0, d));
+    }
+    const size_t bb = align_up((size_t)(2 * mx) * inter_size(pl->prec));
+    s.buf[0] = off;
+    s.buf[1] = off + bb;
+    off += 2 * bb;
+    s.total = std::max<size_t>(off, kAlign);
+    return s;
+}
+
+// A complex mu-mode product as one real contraction over the (real,
+// imaginary) view of the tensors: rows are the fibres (p, q) (real offset
+// 2p + 2Pmq), the contracted index c + 2k runs over the part c and the mode
+// index k (real offset c + 2Pk), the output column c' + 2j likewise; the B
+// operand is the real 2n x 2m matrix made by complex_expand.  For P == 1
+// the (part, index) pairs are contiguous and the maps have one level.
+Contraction c_mode_contraction(const ModeGeom &g, const void *src, bool src64, const void *M, bool M64, void *dst,
+                               bool dst64) {
+    Contraction c;
+    c.M = g.P * g.Q;
+    c.N = 2 * g.n;
+    c.K = 2 * g.m;
+    c.A = src;
+    c.A_f64 = src64;
+    if (g.P == 1) {
+        c.rowA = IdxMap{0, 2 * g.m, 0};
+        c.rowC = IdxMap{0, 2 * g.n, 0};
+        c.kA = IdxMap{0, 1, 0};
+        c.colC = IdxMap{0, 1, 0};
+    } else {
+        c.rowA = IdxMap{g.P, 2, 2 * g.P * g.m};
+        c.rowC = IdxMap{g.P, 2, 2 * g.P * g.n};
+        c.kA = IdxMap{2, 1, 2 * g.P};
+        c.colC = IdxMap{2, 1, 2 * g.P};
+    }
+    c.B = M;
+    c.B_f64 = M64;
+    c.colB = IdxMap{0, 1, 0};
+    c.kB = IdxMap{0, 2 * g.n, 0};
+    c.C = dst;
+    c.C_f64 = dst64;
+    return c;
+}
+
+kron_status run_chain_c(const kron_plan_s *pl, const void *T, void *S, uint8_t *ws, const CtLayout &lay,
+                        cudaStream_t st) {
+    const int d = pl->d;
+    const bool io64 = pl->dtype == KRON_F64;
+    const bool split = is_split(pl->prec);
+    const int form = form_of(pl->prec);
+    const bool i64 = pl->prec == KRON_PREC_FP64;
+    int64_t cur[KRON_MAX_D];
+    for (int k = 0; k < d; ++k) cur[k] = pl->m[k];
+    const void *src = T;
+    bool src64 = io64;
+    for (int s = 0; s < d; ++s) {
+        const int mu = pl->order[s];
+        const ModeGeom g = mode_geom(d, cur, mu, pl->n[mu]);
+        const bool last = (s == d - 1);
+        void *dst = last ? S : (void *)(ws + lay.buf[s & 1]);
+        const bool dst64 = last ? io64 : (split ? false : i64);
+        Contraction c = c_mode_contraction(g, src, src64, ws + lay.M[mu], io64, dst, dst64);
+        cudaError_t e;
+        if (split) {
+            void *img = ws + lay.img[mu];
+            e = tc_build_bimage(form, c, img, st);
+            if (e == cudaSuccess) e = tcp_contract(form, c, img, st);
+        } else {
+            e = simt_contract(i64, c, st);
+        }
+        if (e != cudaSuccess) return KRON_ERR_CUDA;
+        cur[mu] = pl->n[mu];
+        src = dst;
+        src64 = dst64;
+    }
+    return KRON_OK;
+}
+
+}  // namespace
+
+kron_status kron_ctucker_workspace_size(kron_plan plan, size_t *bytes) {
+    if (!plan || !bytes) return KRON_ERR_INVALID_ARG;
+    if (is_fx(plan->prec)) return KRON_ERR_UNSUPPORTED;
+    *bytes = ct_layout(plan).total;
+    return KRON_OK;
+}
+
+kron_status kron_ctucker(kron_plan plan, const void *T, const void *const *L, const int64_t *ldL, int conj, void *S,
+                         void *ws, size_t ws_bytes, kron_stream_t stream) {
+    if (!plan || !T || !S || !L || !ldL || (conj != 0 && conj != 1)) return KRON_ERR_INVALID_ARG;
+    if (is_fx(plan->prec)) return KRON_ERR_UNSUPPORTED;
+    const bool trans = (plan->flags & KRON_PLAN_TRANS_L) != 0;
+    const size_t es2 = 2 * esize(plan->dtype);  // one complex element
+    if (!aligned(T, es2) || !aligned(S, es2)) return KRON_ERR_ALIGNMENT;
+    for (int k = 0; k < plan->d; ++k) {
+        if (!L[k]) return KRON_ERR_INVALID_ARG;
+        if (!aligned(L[k], es2)) return KRON_ERR_ALIGNMENT;
+        if (trans ? ldL[k] < plan->m[k] : ldL[k] < plan->n[k]) return KRON_ERR_INVALID_ARG;
+    }
+    const CtLayout lay = ct_layout(plan);
+    kron_status st = check_ws(ws, ws_bytes, lay.total);
+    if (st != KRON_OK) return st;
+    auto *w = static_cast<uint8_t *>(ws);
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    const bool io64 = plan->dtype == KRON_F64;
+    for (int k = 0; k < plan->d; ++k)
+        if (complex_expand(L[k], io64, ldL[k], plan->n[k], plan->m[k], trans, conj != 0, w + lay.M[k], cs) !=
+            cudaSuccess)
+            return KRON_ERR_CUDA;
+    return run_chain_c(plan, T, S, w, lay, cs);
+}
+
 // ----------------------------------------------------------------- adjoint
 //
 // Workspace: [img fwd x d][img trans x d][X0][X1][G0][G1][partial]

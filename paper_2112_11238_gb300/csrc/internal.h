@@ -137,6 +137,13 @@ cudaError_t tcp_jobs_run(const TcpJobs &jobs, const void *table, int *done, cuda
 // ---- CUDA-core path (simt.cu) ----
 // FP64 (f64 = true) or FP32 fused multiply-add.
 cudaError_t simt_contract(bool f64, const Contraction &c, cudaStream_t st);
+
+// The real 2n x 2m matrix of a complex mu-mode product with G = op(L)
+// (complex.cu): L complex (interleaved, FP64 or FP32 parts), ldL in complex
+// elements; op = L, L^T (trans) or conj of either (conj).  M column-major,
+// ld 2n, same part type as L.
+cudaError_t complex_expand(const void *L, bool f64, int64_t ldL, int64_t n, int64_t m, bool trans, bool conj,
+                           void *M, cudaStream_t st);
 // Split-K variant for a long contracted index (the adjoint's dL): partials
 // (FP64 or FP32, splits * M * N) summed in a fixed order into C.
 size_t simt_splitk_partial_bytes(bool f64, int64_t M, int64_t N, int64_t K);

@@ -58,6 +58,10 @@ def to_host(t):
 
 
 def rel_err(x, ref):
-    x = np.asarray(x, dtype=np.float64)
-    ref = np.asarray(ref, dtype=np.float64)
+    """Max-norm relative error; complex arrays are compared as complex
+    numbers (modulus of the difference), not through their real parts."""
+    cplx = np.iscomplexobj(x) or np.iscomplexobj(ref)
+    dt = np.complex128 if cplx else np.float64
+    x = np.asarray(x, dtype=dt)
+    ref = np.asarray(ref, dtype=dt)
     return float(np.max(np.abs(x - ref)) / max(np.max(np.abs(ref)), 1e-300))

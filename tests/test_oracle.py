@@ -406,3 +406,62 @@ def test_semilinear_final_error_matches_the_paper():
     err = np.abs(u - ex).max() / np.abs(ex).max()
     assert abs(err - printed) <= 0.1e-3, err
     assert err == pytest.approx(9.7576e-3, rel=1e-3)
+
+
+# ------------------------------------------------------------------ complex
+
+def _crand(*shape, seed=0):
+    g = np.random.default_rng(2112 + seed)
+    return np.asfortranarray(g.standard_normal(shape) + 1j * g.standard_normal(shape))
+
+
+def test_ctucker_on_real_inputs_equals_the_real_oracle():
+    """Over real data the complex operator is the real one (C oracle, Eq. (tuckerop))."""
+    g = np.random.default_rng(5)
+    T = g.standard_normal((4, 5, 3))
+    Ls = [g.standard_normal((6, 4)), g.standard_normal((2, 5)), g.standard_normal((3, 3))]
+    S = oracle.ctucker(T, Ls)
+    assert np.max(np.abs(S.imag)) == 0.0
+    assert np.allclose(S.real, oracle.tucker(T, Ls), rtol=0, atol=1e-13)
+    Lt = [np.asfortranarray(L.T) for L in Ls]
+    assert np.allclose(oracle.ctucker(T, Lt, transL=True).real, oracle.tucker(T, Lt, transL=True),
+                       rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("transL,conj", [(False, False), (True, False), (True, True), (False, True)])
+def test_ctucker_equals_nested_sum(transL, conj):
+    """Brute force over C of Eq. (nestedmumode)."""
+    T = _crand(3, 2, 4, seed=1)
+    shapes = [(2, 3), (3, 2), (4, 4)]
+    Ls = [_crand(*(s[::-1] if transL else s), seed=2 + k) for k, s in enumerate(shapes)]
+    ref = oracle.ctucker_nested(T, Ls, transL, conj)
+    assert np.allclose(oracle.ctucker(T, Ls, transL, conj), ref, rtol=0, atol=1e-12)
+
+
+def test_cttucker_with_dft_matrices_is_the_inverse_fft():
+    """Psi_mu = F (the DFT matrix, F[j, k] = exp(-2 pi i j k / m)): T x_mu F is
+    numpy.fft.fftn, and the conjugate transposes (cttucker) give m_1...m_d
+    times numpy.fft.ifftn (a library routine, independent of the oracle)."""
+    T = _crand(8, 5, 6, seed=7)
+    Fs = [np.exp(-2j * np.pi * np.outer(np.arange(m), np.arange(m)) / m) for m in T.shape]
+    assert np.allclose(oracle.ctucker(T, Fs), np.fft.fftn(T), rtol=0, atol=1e-10)
+    assert np.allclose(oracle.ctucker(T, Fs, transL=True, conj=True), np.fft.ifftn(T) * T.size, rtol=0, atol=1e-10)
+
+
+def test_cttucker_with_unitary_matrices_keeps_the_norm():
+    """Unitary Psi_mu: the operator with the conjugate transposes is the inverse
+    of the one with Psi_mu, and both keep the Frobenius norm."""
+    T = _crand(5, 4, 6, seed=9)
+    Us = [np.linalg.qr(_crand(m, m, seed=20 + m))[0] for m in T.shape]
+    S = oracle.ctucker(T, Us, transL=True, conj=True)
+    assert np.isclose(np.linalg.norm(S), np.linalg.norm(T), rtol=1e-13)
+    assert np.allclose(oracle.ctucker(S, Us), T, rtol=0, atol=1e-12)
+
+
+def test_ctucker_conjugation_identity():
+    """conj(T x op(L)^*) = conj(T) x op(L) elementwise (complex conjugation is a ring automorphism)."""
+    T = _crand(3, 4, seed=11)
+    Ls = [_crand(3, 5, seed=12), _crand(4, 2, seed=13)]
+    a = oracle.ctucker(T, Ls, transL=True, conj=True)
+    b = oracle.ctucker(T.conj(), Ls, transL=True, conj=False).conj()
+    assert np.allclose(a, b, rtol=0, atol=1e-13)
