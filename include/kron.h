@@ -240,6 +240,47 @@ KRON_API kron_status kron_ctucker(kron_plan plan, const void *T, const void *con
                                   int conj, void *S, void *ws, size_t ws_bytes, kron_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Hermite--Laguerre--Fourier transform matrices (the HLF decomposition of   */
+/* the paper's pseudospectral example; used through Eq. (tensinterp))        */
+/* ------------------------------------------------------------------------ */
+/*
+ * Quadrature rules (host arrays x, w of length m; FP64; host computation):
+ *   kron_gauss_hermite: nodes x_k = xi_k / beta of the m-point Gauss rule of
+ *     the weight exp(-y^2), and the weights w_k with which
+ *     sum_k w_k f(x_k) H_i(x_k) approximates the coefficient of f on the
+ *     normalized scaled Hermite function H_i (exact when f H_i is a
+ *     product of two such functions of total degree < 2m);
+ *   kron_gauss_laguerre: the same for the generalized Laguerre weight
+ *     y^alpha exp(-y) (alpha > -1) and the functions L_i below.
+ * Nodes by Golub--Welsch (eigenvalues of the Jacobi matrix, implicit QL),
+ * weights w_k = 1 / sum_{i<m} phi_i(x_k)^2 (reciprocal Christoffel function
+ * of the orthonormal functions).  KRON_ERR_NUMERIC if the iteration fails to
+ * converge.
+ *
+ * Function matrices (device, FP64; x device array of n points):
+ *   H_i(x) = sqrt(beta / (sqrt(pi) 2^i i!)) H_i^phys(beta x) exp(-beta^2 x^2 / 2),
+ *   L_i(x) = sqrt(beta i! / Gamma(i + alpha + 1)) L_i^alpha(beta x)
+ *            (beta x)^(alpha / 2) exp(-beta x / 2)     (x >= 0),
+ * i = 0 .. m-1 (the paper's i_mu - 1), orthonormal in L^2(R) / L^2(R+).
+ * trans = 0: F[l + ldF i] = phi_i(x_l) (n x m, the evaluation matrix Phi);
+ * trans = 1: F[i + ldF l] (m x n, the transform matrix Psi when x are the
+ * nodes).  Stream-ordered; overflow-free for any m (scaled recurrences).
+ *
+ * kron_fourier_resample: the real n x m matrix F[l, j] of the trigonometric
+ * interpolation of m equispaced samples of a period (at j/m) evaluated at
+ * the n equispaced points l/n (the even-m Nyquist term split symmetrically),
+ * i.e. the resampling of an FFT-based interpolation, as a matrix for a
+ * mu-mode product.
+ */
+KRON_API kron_status kron_gauss_hermite(int64_t m, double beta, double *x, double *w);
+KRON_API kron_status kron_gauss_laguerre(int64_t m, double alpha, double beta, double *x, double *w);
+KRON_API kron_status kron_hermite_functions(int64_t m, double beta, const double *x, int64_t n, double *F,
+                                            int64_t ldF, int trans, kron_stream_t stream);
+KRON_API kron_status kron_laguerre_functions(int64_t m, double alpha, double beta, const double *x, int64_t n,
+                                             double *F, int64_t ldF, int trans, kron_stream_t stream);
+KRON_API kron_status kron_fourier_resample(int64_t m, int64_t n, double *F, int64_t ldF, kron_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Action of a Kronecker sum: Section 2, Eq. (actkron)                       */
 /* ------------------------------------------------------------------------ */
 /*

@@ -252,6 +252,118 @@ def ctucker_nested(T, Ls, transL: bool = False, conj: bool = False) -> np.ndarra
     return S
 
 
+# ------------------------------------------------ Hermite--Laguerre--Fourier
+# The pseudospectral example of Section "Hermite--Laguerre--Fourier function
+# decomposition": the functions are the paper's normalized and scaled ones
+# with 0-based index i (the paper's i_mu - 1).
+
+
+def hermite_functions(m: int, beta: float, x) -> np.ndarray:
+    """n x m matrix of the normalized scaled Hermite functions
+    H_i(x) = sqrt(beta / (sqrt(pi) 2^i i!)) H_i(beta x) exp(-beta^2 x^2 / 2),
+    by the recurrence of the orthonormal functions (plain float64; moderate
+    m and |x| only)."""
+    y = beta * np.asarray(x, dtype=np.float64).ravel()
+    F = np.zeros((y.size, m))
+    F[:, 0] = np.sqrt(beta) * np.pi ** -0.25 * np.exp(-y * y / 2)
+    if m > 1:
+        F[:, 1] = np.sqrt(2.0) * y * F[:, 0]
+    for i in range(2, m):
+        F[:, i] = np.sqrt(2.0 / i) * y * F[:, i - 1] - np.sqrt((i - 1) / i) * F[:, i - 2]
+    return F
+
+
+def laguerre_functions(m: int, alpha: float, beta: float, x) -> np.ndarray:
+    """n x m matrix of the normalized scaled generalized Laguerre functions
+    L_i(x) = sqrt(beta i! / Gamma(i + alpha + 1)) L_i^alpha(beta x) (beta x)^(alpha/2) exp(-beta x / 2),
+    by the recurrence of the orthonormal functions (plain float64)."""
+    import math
+    y = beta * np.asarray(x, dtype=np.float64).ravel()
+    F = np.zeros((y.size, m))
+    F[:, 0] = np.sqrt(beta / math.gamma(alpha + 1)) * y ** (alpha / 2) * np.exp(-y / 2)
+    if m > 1:
+        F[:, 1] = (alpha + 1 - y) / np.sqrt(alpha + 1) * F[:, 0]
+    for i in range(2, m):
+        F[:, i] = ((2 * i - 1 + alpha - y) * F[:, i - 1] - np.sqrt((i - 1) * (i - 1 + alpha)) * F[:, i - 2]) \
+            / np.sqrt(i * (i + alpha))
+    return F
+
+
+def gauss_hermite(m: int, beta: float):
+    """Scaled Gauss--Hermite nodes x = xi / beta and function weights
+    w = lambda exp(xi^2) / beta (lambda the weights of exp(-xi^2));
+    numpy.polynomial.hermite.hermgauss as the rule."""
+    from numpy.polynomial.hermite import hermgauss
+    xi, lam = hermgauss(m)
+    return xi / beta, lam * np.exp(xi * xi) / beta
+
+
+def gauss_laguerre(m: int, alpha: float, beta: float):
+    """Scaled generalized Gauss--Laguerre nodes and function weights
+    w = lambda exp(xi) xi^(-alpha) / beta; scipy.special.roots_genlaguerre as the rule."""
+    import scipy.special
+    xi, lam = scipy.special.roots_genlaguerre(m, alpha)
+    return xi / beta, lam * np.exp(xi) * xi ** (-alpha) / beta
+
+
+def fourier_resample(m: int, n: int) -> np.ndarray:
+    """Real n x m matrix (n >= m) of the FFT resampling of m equispaced samples
+    of one period to n equispaced points: the spectrum of the samples is
+    zero-padded to length n (for n > m the even-m Nyquist coefficient split
+    between +-m/2; for n = m the two are one bin and the spectrum is kept
+    whole) and transformed back, scaled by n / m."""
+    if n < m:
+        raise ValueError("the zero-padding resampling needs n >= m")
+    F = np.zeros((n, m))
+    h = (m + 1) // 2
+    for j in range(m):
+        e = np.zeros(m)
+        e[j] = 1.0
+        a = np.fft.fft(e)
+        b = np.zeros(n, dtype=np.complex128)
+        b[:h] = a[:h]
+        b[n - (m - h):] = a[h:]
+        if m % 2 == 0 and n > m:
+            b[h] = a[h] / 2
+            b[n - h] = a[h] / 2
+        F[:, j] = np.real(np.fft.ifft(b)) * n / m
+    return F
+
+
+def hlf_function(x1, x2, x3):
+    """The trivariate test function of the HLF example."""
+    return x2 ** 2 * np.sin(20 * x1) * np.sin(10 * x2) * np.exp(-x1 ** 2 - 2 * x2) / (np.sin(2 * np.pi * x3) + 2)
+
+
+def hlf_error(m1: int, m2: int, m3: int, alpha: float = 4.0, b1: float = 4.0, b2: float = 11.0,
+              a3: float = -1.0, b3: float = 1.0, n: int = 301) -> float:
+    """Achieved accuracy of the HLF decomposition with (m1, m2, m3) basis
+    functions: coefficients Fhat = FW x_1 Psi_1 x_2 Psi_2 (FW the function at
+    the quadrature points times the weights, Psi_mu the functions at the
+    nodes), evaluation Ftilde = Fhat x_1 Phi_1 x_2 Phi_2 x_3 Phi_3 (Phi_3 the
+    Fourier resampling), both by the Tucker operator (Eq. (tensinterp)), on n
+    equispaced points per direction (left end included, right end excluded);
+    max-norm relative error against f.  beta_1 = sqrt(2 m1 + 1) / b1,
+    beta_2 = (4 m2 + 2 alpha + 2) / b2."""
+    beta1 = np.sqrt(2 * m1 + 1) / b1
+    beta2 = (4 * m2 + 2 * alpha + 2) / b2
+    xi1, w1 = gauss_hermite(m1, beta1)
+    xi2, w2 = gauss_laguerre(m2, alpha, beta2)
+    xi3 = a3 + (b3 - a3) * np.arange(m3) / m3
+    FW = hlf_function(xi1[:, None, None], xi2[None, :, None], xi3[None, None, :]) \
+        * w1[:, None, None] * w2[None, :, None]
+    Psi1 = hermite_functions(m1, beta1, xi1).T
+    Psi2 = laguerre_functions(m2, alpha, beta2, xi2).T
+    Fhat = tucker(FW, [Psi1, Psi2, np.eye(m3)])
+    x1 = -b1 + 2 * b1 * np.arange(n) / n
+    x2 = b2 * np.arange(n) / n
+    x3 = a3 + (b3 - a3) * np.arange(n) / n
+    Ft = tucker(Fhat, [hermite_functions(m1, beta1, x1), laguerre_functions(m2, alpha, beta2, x2),
+                       fourier_resample(m3, n)])
+    F = hlf_function(x1[:, None, None], x2[None, :, None], x3[None, None, :])
+    return float(np.max(np.abs(Ft - F)) / np.max(np.abs(F)))
+
+
 def itucker(V, Ps, transL: bool = False) -> np.ndarray:
     """V x_1 op(P_1)^{-1} x_2 ... x_d op(P_d)^{-1} (Section 3.4, Eq. (preconnd)).
 

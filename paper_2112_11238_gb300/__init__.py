@@ -17,6 +17,8 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
+
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -67,6 +69,12 @@ _sig("kron_plan_order", [_vp, ctypes.POINTER(_ci)])
 _sig("kron_plan_flops", [_vp], ctypes.c_double)
 _sig("kron_tucker", [_vp, _vp, ctypes.POINTER(_vp), _i64p, _vp, _vp, _sz, _vp])
 _sig("kron_ctucker_workspace_size", [_vp, ctypes.POINTER(_sz)])
+_sig("kron_gauss_hermite", [ctypes.c_int64, ctypes.c_double, _vp, _vp])
+_sig("kron_gauss_laguerre", [ctypes.c_int64, ctypes.c_double, ctypes.c_double, _vp, _vp])
+_sig("kron_hermite_functions", [ctypes.c_int64, ctypes.c_double, _vp, ctypes.c_int64, _vp, ctypes.c_int64, _ci, _vp])
+_sig("kron_laguerre_functions", [ctypes.c_int64, ctypes.c_double, ctypes.c_double, _vp, ctypes.c_int64, _vp,
+                                 ctypes.c_int64, _ci, _vp])
+_sig("kron_fourier_resample", [ctypes.c_int64, ctypes.c_int64, _vp, ctypes.c_int64, _vp])
 _sig("kron_ctucker", [_vp, _vp, ctypes.POINTER(_vp), _i64p, _ci, _vp, _vp, _sz, _vp])
 _sig("kron_kronsumv_workspace_size", [_vp, ctypes.POINTER(_sz)])
 _sig("kron_kronsumv", [_vp, _vp, ctypes.POINTER(_vp), _i64p, _vp, _vp, _sz, _vp])
@@ -92,7 +100,9 @@ _sig("kron_batched_run", [_vp, _vp, _sz, _vp])
 EXPORTS = [
     "kron_status_string", "kron_version", "kron_get_device_error", "kron_mump_workspace_size",
     "kron_mump", "kron_mump_noalloc", "kron_plan_create", "kron_plan_destroy", "kron_plan_workspace_size",
-    "kron_plan_order", "kron_plan_flops", "kron_tucker", "kron_ctucker_workspace_size", "kron_ctucker", "kron_kronsumv_workspace_size", "kron_kronsumv", "kron_itucker_workspace_size", "kron_itucker", "kron_kronsum_pcg_workspace_size", "kron_kronsum_pcg", "kron_adjoint_workspace_size",
+    "kron_plan_order", "kron_plan_flops", "kron_tucker", "kron_ctucker_workspace_size", "kron_ctucker",
+    "kron_gauss_hermite", "kron_gauss_laguerre", "kron_hermite_functions", "kron_laguerre_functions",
+    "kron_fourier_resample", "kron_kronsumv_workspace_size", "kron_kronsumv", "kron_itucker_workspace_size", "kron_itucker", "kron_kronsum_pcg_workspace_size", "kron_kronsum_pcg", "kron_adjoint_workspace_size",
     "kron_tucker_adjoint", "kron_expm_workspace_size", "kron_expm",
     "kron_expkronsum_workspace_size", "kron_expkronsum_step", "kron_expkronsum_apply",
     "kron_batched_plan_create", "kron_batched_plan_destroy", "kron_batched_workspace_size",
@@ -421,6 +431,63 @@ def cttucker(T: torch.Tensor, Psis, prec="fp64", stream=None) -> torch.Tensor:
     """T x_1 Psi_1^* x_2 ... x_d Psi_d^* (conjugate transposes; the remark after
     Eq. (tensinterp)): evaluation at the quadrature points without forming Psi_mu^*."""
     return ctucker(T, Psis, prec=prec, trans=True, conj=True, stream=stream)
+
+
+def gauss_hermite(m: int, beta: float):
+    """Scaled Gauss-Hermite nodes and function weights (numpy float64 arrays of length m):
+    sum_k w_k f(x_k) H_i(x_k) approximates the coefficient of f on H_i."""
+    x = np.zeros(int(m))
+    w = np.zeros(int(m))
+    _check(_lib.kron_gauss_hermite(int(m), float(beta), x.ctypes.data, w.ctypes.data), "kron_gauss_hermite")
+    return x, w
+
+
+def gauss_laguerre(m: int, alpha: float, beta: float):
+    """Scaled generalized Gauss-Laguerre nodes and function weights (numpy float64)."""
+    x = np.zeros(int(m))
+    w = np.zeros(int(m))
+    _check(_lib.kron_gauss_laguerre(int(m), float(alpha), float(beta), x.ctypes.data, w.ctypes.data),
+           "kron_gauss_laguerre")
+    return x, w
+
+
+def _points(x, device):
+    if not isinstance(x, torch.Tensor):
+        x = torch.as_tensor(np.asarray(x, dtype=np.float64))
+    return x.to(device=device, dtype=torch.float64).contiguous()
+
+
+def hermite_functions(m: int, beta: float, x, trans: bool = False, device="cuda", stream=None) -> torch.Tensor:
+    """Normalized scaled Hermite functions H_i(x_l), i < m: an n x m column-major
+    matrix (the evaluation matrix Phi), or m x n with trans (the transform matrix Psi)."""
+    x = _points(x, device)
+    n = x.numel()
+    F = empty_colmajor((m, n) if trans else (n, m), torch.float64, x.device)
+    _check(_lib.kron_hermite_functions(int(m), float(beta), x.data_ptr(), n, F.data_ptr(), max(F.shape[0], 1),
+                                       int(bool(trans)), _stream(stream)), "kron_hermite_functions")
+    return F
+
+
+def laguerre_functions(m: int, alpha: float, beta: float, x, trans: bool = False, device="cuda",
+                       stream=None) -> torch.Tensor:
+    """Normalized scaled generalized Laguerre functions L_i(x_l) (x >= 0), layout as
+    hermite_functions."""
+    x = _points(x, device)
+    n = x.numel()
+    F = empty_colmajor((m, n) if trans else (n, m), torch.float64, x.device)
+    _check(_lib.kron_laguerre_functions(int(m), float(alpha), float(beta), x.data_ptr(), n, F.data_ptr(),
+                                        max(F.shape[0], 1), int(bool(trans)), _stream(stream)),
+           "kron_laguerre_functions")
+    return F
+
+
+def fourier_resample(m: int, n: int, device="cuda", stream=None) -> torch.Tensor:
+    """The real n x m matrix of the trigonometric interpolation of m equispaced samples of
+    a period, evaluated at n equispaced points."""
+    F = empty_colmajor((n, m), torch.float64, device)
+    _check(_lib.kron_fourier_resample(int(m), int(n), F.data_ptr(), int(n), _stream(stream)),
+           "kron_fourier_resample")
+    return F
 
 
 def kronsumv(V: torch.Tensor, Ls, prec="fp64", trans: bool = False, stream=None) -> torch.Tensor:

@@ -123,3 +123,42 @@ def test_mump_workspace_query(lib):
     assert lib.kron_mump_workspace_size(3, _i64([5, 6, 7]), 1, 9, 1, 2, ctypes.byref(ws)) == 0
     assert ws.value >= 256
     assert lib.kron_mump_workspace_size(3, _i64([5, 6, 7]), 3, 9, 1, 2, ctypes.byref(ws)) == 1
+
+
+@pytest.mark.parametrize("m", [1, 2, 9, 45, 69, 160])
+def test_gauss_hermite_rule_matches_the_oracle(m):
+    """kron_gauss_hermite (host code of the library: Golub--Welsch by implicit
+    QL, reciprocal Christoffel weights) against numpy's hermgauss."""
+    import numpy as np
+    import oracle
+    import paper_2112_11238_gb300 as kron
+    beta = np.sqrt(2 * m + 1) / 4.0
+    x, w = kron.gauss_hermite(m, beta)
+    xr, wr = oracle.gauss_hermite(m, beta)
+    assert np.max(np.abs(x - xr)) <= 1e-13 * max(1.0, np.max(np.abs(xr)))
+    assert np.max(np.abs(w - wr) / wr) <= 1e-11
+
+
+@pytest.mark.parametrize("m,alpha", [(1, 4.0), (3, 0.0), (31, 4.0), (105, 4.0), (64, -0.5)])
+def test_gauss_laguerre_rule_matches_the_oracle(m, alpha):
+    import numpy as np
+    import oracle
+    import paper_2112_11238_gb300 as kron
+    beta = (4 * m + 2 * alpha + 2) / 11.0
+    x, w = kron.gauss_laguerre(m, alpha, beta)
+    xr, wr = oracle.gauss_laguerre(m, alpha, beta)
+    assert np.max(np.abs(x - xr) / xr) <= 1e-12
+    assert np.max(np.abs(w - wr) / wr) <= 1e-10
+
+
+def test_spectral_argument_validation(lib):
+    import numpy as np
+    x = np.zeros(4)
+    w = np.zeros(4)
+    lib.kron_gauss_hermite.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
+    lib.kron_gauss_laguerre.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                        ctypes.c_void_p]
+    assert lib.kron_gauss_hermite(0, 1.0, x.ctypes.data, w.ctypes.data) == 1
+    assert lib.kron_gauss_hermite(4, 0.0, x.ctypes.data, w.ctypes.data) == 1
+    assert lib.kron_gauss_laguerre(4, -1.0, 1.0, x.ctypes.data, w.ctypes.data) == 1
+    assert lib.kron_gauss_laguerre(4, 1.0, -2.0, x.ctypes.data, w.ctypes.data) == 1

@@ -465,3 +465,79 @@ def test_ctucker_conjugation_identity():
     a = oracle.ctucker(T, Ls, transL=True, conj=True)
     b = oracle.ctucker(T.conj(), Ls, transL=True, conj=False).conj()
     assert np.allclose(a, b, rtol=0, atol=1e-13)
+
+
+# ------------------------------------------------- Hermite--Laguerre--Fourier
+
+def _golden_hlf():
+    rows = []
+    with open(os.path.join(os.path.dirname(__file__), "golden", "fig_spectral_hlf_accuracy.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                m1, m2, m3, acc = line.split()
+                rows.append(((int(m1), int(m2), int(m3)), float(acc)))
+    return rows
+
+
+@pytest.mark.parametrize("m,beta", [(1, 1.0), (7, 0.7), (45, 1.7), (69, 2.1)])
+def test_hermite_rule_makes_the_functions_orthonormal(m, beta):
+    """Gauss exactness: Psi diag(w) Psi^T = I for the m functions at the m nodes
+    (every product H_i H_j, i, j < m, is integrated exactly)."""
+    x, w = oracle.gauss_hermite(m, beta)
+    Psi = oracle.hermite_functions(m, beta, x).T
+    assert np.allclose(Psi @ np.diag(w) @ Psi.T, np.eye(m), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("m,alpha,beta", [(1, 4.0, 1.0), (6, 0.0, 1.3), (31, 4.0, 12.3), (60, 1.5, 0.8)])
+def test_laguerre_rule_makes_the_functions_orthonormal(m, alpha, beta):
+    x, w = oracle.gauss_laguerre(m, alpha, beta)
+    Psi = oracle.laguerre_functions(m, alpha, beta, x).T
+    assert np.allclose(Psi @ np.diag(w) @ Psi.T, np.eye(m), rtol=0, atol=1e-11)
+
+
+def test_hermite_and_laguerre_functions_match_the_closed_forms():
+    """Against scipy's Hermite and generalized Laguerre polynomials with the
+    normalisations of the paper's definitions (low degrees)."""
+    import math
+    import scipy.special as sp
+    x = np.linspace(-3, 3, 41)
+    beta = 1.3
+    H = oracle.hermite_functions(9, beta, x)
+    for i in range(9):
+        ref = np.sqrt(beta / (np.sqrt(np.pi) * 2.0 ** i * math.factorial(i))) * sp.eval_hermite(i, beta * x) \
+            * np.exp(-(beta * x) ** 2 / 2)
+        assert np.allclose(H[:, i], ref, rtol=1e-12, atol=1e-14)
+    x = np.linspace(0, 9, 37)
+    alpha, beta = 4.0, 0.9
+    Lg = oracle.laguerre_functions(9, alpha, beta, x)
+    for i in range(9):
+        ref = np.sqrt(beta * math.factorial(i) / math.gamma(i + alpha + 1)) * sp.eval_genlaguerre(i, alpha, beta * x) \
+            * (beta * x) ** (alpha / 2) * np.exp(-beta * x / 2)
+        assert np.allclose(Lg[:, i], ref, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("m,n", [(8, 301), (7, 20), (38, 301), (1, 5)])
+def test_fourier_resample_reproduces_trigonometric_polynomials(m, n):
+    """The resampling of the samples of any trigonometric polynomial of degree
+    below m/2 equals its values at the new points; constants stay constant."""
+    F = oracle.fourier_resample(m, n)
+    assert np.allclose(F.sum(axis=1), 1.0, atol=1e-13)
+    t, s = np.arange(m) / m, np.arange(n) / n
+    for k in range(1, (m + 1) // 2):
+        for fn in (np.sin, np.cos):
+            assert np.allclose(F @ fn(2 * np.pi * k * t), fn(2 * np.pi * k * s), atol=1e-12)
+
+
+@pytest.mark.parametrize("m", [1, 2, 7, 8, 64])
+def test_fourier_resample_interpolates_the_samples(m):
+    """At the sample points themselves (n = m) the interpolant reproduces the
+    samples: the matrix is the identity, odd and even m alike."""
+    assert np.allclose(oracle.fourier_resample(m, m), np.eye(m), rtol=0, atol=1e-13)
+
+
+def test_hlf_decomposition_reproduces_the_paper():
+    """The HLF experiment through the oracle's Tucker operator reproduces the
+    accuracies the paper plots for (m1, m2, m3) = (45, 31, 8) ... (69, 105, 38)."""
+    for (m1, m2, m3), acc in _golden_hlf():
+        err = oracle.hlf_error(m1, m2, m3)
+        assert abs(err - acc) <= 2e-3 * acc, ((m1, m2, m3), err, acc)
