@@ -587,6 +587,41 @@ def run_configs(args):
               4 * 4 * 48.0 ** 4, peaks, MULT.get(prec))
     del T, Ls, tgt
 
+    # complex cttucker (conjugate transposes), d = 3, n = m = 128, complex128 / complex64
+    g = np.random.default_rng(2112 + 6)
+    Tc = g.standard_normal((128,) * 3) + 1j * g.standard_normal((128,) * 3)
+    Pc = [g.standard_normal((128, 128)) + 1j * g.standard_normal((128, 128)) for _ in range(3)]
+    # a complex product is 4 real ones: 8 flops per complex multiply-add
+    fl = 4 * W.tucker_flops([128] * 3, [128] * 3)
+    for prec, cdt in (("fp64", torch.complex128), ("3xtf32", torch.complex64), ("bf16x6", torch.complex64)):
+        T = kron.colmajor(torch.from_numpy(np.asfortranarray(Tc)).to(dev, cdt))
+        Ls = [kron.colmajor(torch.from_numpy(np.asfortranarray(P)).to(dev, cdt)) for P in Pc]
+        plan = kron.TuckerPlan([128] * 3, [128] * 3, cdt, prec, trans=True)
+        ws = torch.empty(plan.ctucker_workspace_bytes(), dtype=torch.uint8, device=dev)
+        S = kron.empty_colmajor([128] * 3, cdt, dev)
+        es = 16 if cdt == torch.complex128 else 8
+        ms = _timed(torch, lambda: plan.ctucker_into(T, Ls, S, conj=True, ws=ws), flush=flush)
+        _line("cttucker d=3 n=m=128 " + str(cdt).replace("torch.", ""), prec, ms, fl, 2 * es * 128.0 ** 3, peaks,
+              MULT.get(prec))
+    del T, Ls, S, ws
+
+    # HLF evaluation (Section "Hermite--Laguerre--Fourier function decomposition"):
+    # (69, 105, 38) coefficients -> 301^3 points, Phi_1, Phi_2 from the library, FP64 storage
+    m1, m2, m3, nn = 69, 105, 38, 301
+    Fh = kron.colmajor(torch.randn(m1, m2, m3, dtype=torch.float64, device=dev))
+    b1_, a_, b2_ = 4.0, 4.0, 11.0
+    Phi = [kron.hermite_functions(m1, np.sqrt(2 * m1 + 1) / b1_, -b1_ + 2 * b1_ * np.arange(nn) / nn),
+           kron.laguerre_functions(m2, a_, (4 * m2 + 2 * a_ + 2) / b2_, b2_ * np.arange(nn) / nn),
+           kron.fourier_resample(m3, nn)]
+    for prec in ("fp64", "3xtf32", "bf16x6"):
+        plan = kron.TuckerPlan([m1, m2, m3], [nn] * 3, torch.float64, prec)
+        ws = plan.workspace(dev)
+        S = kron.empty_colmajor([nn] * 3, torch.float64, dev)
+        ms = _timed(torch, lambda: plan.tucker_into(Fh, Phi, S, ws=ws), flush=flush)
+        _line("HLF evaluation (69,105,38) -> 301^3 f64 storage", prec, ms, plan.flops(),
+              8.0 * (m1 * m2 * m3 + nn ** 3), peaks, MULT.get(prec))
+    del Fh, Phi, S, ws
+
     # next rows at the stepper's size: Kronecker-sum action and inverse Tucker, 256^3 FP64
     st = W.stepper(n=N, tau=TAU, nsteps=NSTEPS, with_u0=False)
     V = kron.empty_colmajor([N] * D, torch.float64, dev)
