@@ -209,6 +209,11 @@ kron_status run_chain(const kron_plan_s *pl, const void *T, const void *const *L
             void *img = ws + pl->img_off[mu];
             e = tc_build_bimage(form, c, img, st);
             if (e == cudaSuccess) e = tcp_contract(form, c, img, st);
+        } else if (simt_small_fits(i64, g.m, g.n)) {
+            // small factor: one thread per fibre, op(L) in shared memory
+            Contraction c = tc_mode_contraction(g, src, src64, L[mu], io64, ldL[mu], trans, dst, dst64);
+            c.accumulate = last && acc_last;
+            e = simt_contract_small(i64, c, st);
         } else {
             Contraction c =
                 simt_mode_contraction(g, src, src64, L[mu], io64, ldL[mu], trans, dst, dst64);

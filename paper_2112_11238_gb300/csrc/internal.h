@@ -137,6 +137,11 @@ cudaError_t tcp_jobs_run(const TcpJobs &jobs, const void *table, int *done, cuda
 // ---- CUDA-core path (simt.cu) ----
 // FP64 (f64 = true) or FP32 fused multiply-add.
 cudaError_t simt_contract(bool f64, const Contraction &c, cudaStream_t st);
+// Short contracted index and few outputs per row (K <= 64, N <= 64 in FP32,
+// <= 32 in FP64): one thread per row of C, op(L) in shared memory.  Rows of
+// the contraction must be the tensor's fibres (the tensor-core layout).
+bool simt_small_fits(bool f64, int64_t K, int64_t N);
+cudaError_t simt_contract_small(bool f64, const Contraction &c, cudaStream_t st);
 
 // The real 2n x 2m matrix of a complex mu-mode product with G = op(L)
 // (complex.cu): L complex (interleaved, FP64 or FP32 parts), ldL in complex

@@ -171,7 +171,78 @@ SimtDev make_simt(const Contraction &c) {
     return d;
 }
 
+// Contractions with a short contracted index and few outputs per row (the
+// small modes of a high-order tensor, such as the 20 x 20 factors of a 20^6
+// tensor), where a 64 x 64 output tile would be mostly empty: one thread
+// per row, op(L) (K x N, zero-padded to NM columns) in shared memory, the
+// row's K values read once each and its N outputs accumulated in registers,
+// in ascending k.  Rows of consecutive threads are consecutive fibres, so
+// the loads along k are coalesced whenever the fibres are contiguous.
+constexpr int kSmallK = 64;
+
+template <typename Tc, int NM>
+__global__ void __launch_bounds__(256) simt_small_kernel(const SimtDev p) {
+    __shared__ Tc sB[kSmallK * NM];
+    for (int idx = threadIdx.x; idx < kSmallK * NM; idx += blockDim.x) {
+        const int k = idx / NM, j = idx % NM;
+        sB[idx] = (k < p.K && j < p.N) ? ldv<Tc>(p.B, p.b64, imap(p.colB, j) + imap(p.kB, k)) : Tc(0);
+    }
+    __syncthreads();
+    const int K = (int)p.K, N = (int)p.N;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < p.M; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ra = imap(p.rowA, r), rc = imap(p.rowC, r);
+        Tc acc[NM];
+#pragma unroll
+        for (int j = 0; j < NM; ++j) acc[j] = Tc(0);
+        for (int k = 0; k < K; ++k) {
+            const Tc a = ldv<Tc>(p.A, p.a64, ra + imap(p.kA, k));
+            const Tc *b = sB + k * NM;
+#pragma unroll
+            for (int j = 0; j < NM; ++j) acc[j] = fma(a, b[j], acc[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < NM; ++j) {
+            if (j >= N) break;
+            const int64_t o = rc + imap(p.colC, j);
+            if (p.c64) {
+                double *q = static_cast<double *>(p.C) + o;
+                *q = p.acc ? *q + (double)acc[j] : (double)acc[j];
+            } else {
+                float *q = static_cast<float *>(p.C) + o;
+                *q = p.acc ? (float)(*q + acc[j]) : (float)acc[j];
+            }
+        }
+    }
+}
+
+template <typename Tc, int NM>
+cudaError_t launch_small(const SimtDev &d, cudaStream_t st) {
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((d.M + 255) / 256, 152 * 8));
+    simt_small_kernel<Tc, NM><<<(unsigned)blocks, 256, 0, st>>>(d);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+bool simt_small_fits(bool f64, int64_t K, int64_t N) { return K >= 1 && K <= kSmallK && N >= 1 && N <= (f64 ? 32 : 64); }
+
+cudaError_t simt_contract_small(bool f64, const Contraction &c, cudaStream_t st) {
+    if (c.M == 0 || c.N == 0) return cudaSuccess;
+    if (!simt_small_fits(f64, c.K, c.N)) return cudaErrorInvalidValue;
+    const SimtDev d = make_simt(c);
+    if (f64) {
+        if (c.N <= 8) return launch_small<double, 8>(d, st);
+        if (c.N <= 16) return launch_small<double, 16>(d, st);
+        if (c.N <= 24) return launch_small<double, 24>(d, st);
+        return launch_small<double, 32>(d, st);
+    }
+    if (c.N <= 8) return launch_small<float, 8>(d, st);
+    if (c.N <= 16) return launch_small<float, 16>(d, st);
+    if (c.N <= 24) return launch_small<float, 24>(d, st);
+    if (c.N <= 32) return launch_small<float, 32>(d, st);
+    if (c.N <= 48) return launch_small<float, 48>(d, st);
+    return launch_small<float, 64>(d, st);
+}
 
 size_t simt_splitk_partial_bytes(bool f64, int64_t M, int64_t N, int64_t K) {
     const int64_t chunk = splitk_chunk(M, N, K);
