@@ -39,6 +39,7 @@ struct SimtDev {
     int a64, b64, c64, acc, akc, bkc;
     int64_t kchunk;     // contracted indices per blockIdx.z (split-K), else K
     int64_t czstride;   // element offset of C per blockIdx.z
+    int avec, cvec;     // small kernel: FP32 rows of A / C contiguous and 16-byte aligned
 };
 
 template <typename Tc>
@@ -175,8 +176,8 @@ SimtDev make_simt(const Contraction &c) {
 // small modes of a high-order tensor, such as the 20 x 20 factors of a 20^6
 // tensor), where a 64 x 64 output tile would be mostly empty: one thread
 // per row, op(L) (K x N, zero-padded to NM columns) in shared memory, the
-// row's K values read once each and its N outputs accumulated in registers,
-// in ascending k.  Rows of consecutive threads are consecutive fibres, so
+// row's K values read once each (eight loads in flight) and its N outputs
+// accumulated in registers, in ascending k.  Rows of consecutive threads are consecutive fibres, so
 // the loads along k are coalesced whenever the fibres are contiguous.
 constexpr int kSmallK = 64;
 
@@ -194,11 +195,35 @@ __global__ void __launch_bounds__(256) simt_small_kernel(const SimtDev p) {
         Tc acc[NM];
 #pragma unroll
         for (int j = 0; j < NM; ++j) acc[j] = Tc(0);
-        for (int k = 0; k < K; ++k) {
-            const Tc a = ldv<Tc>(p.A, p.a64, ra + imap(p.kA, k));
-            const Tc *b = sB + k * NM;
+        // eight loads in flight, then their products (rows of sB past K are
+        // zero and the values past K are zero: fma(0, 0, acc) = acc)
+        for (int k0 = 0; k0 < K; k0 += 8) {
+            Tc av[8];
+            if (sizeof(Tc) == 4 && p.avec) {
+                // a contiguous, aligned FP32 row (K a multiple of 4): 16-byte loads
+                const float4 *q = reinterpret_cast<const float4 *>(static_cast<const float *>(p.A) + ra + k0);
+                const float4 v0 = __ldg(q);
+                const float4 v1 = (k0 + 4 < K) ? __ldg(q + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+                av[0] = v0.x; av[1] = v0.y; av[2] = v0.z; av[3] = v0.w;
+                av[4] = v1.x; av[5] = v1.y; av[6] = v1.z; av[7] = v1.w;
+            } else {
 #pragma unroll
-            for (int j = 0; j < NM; ++j) acc[j] = fma(a, b[j], acc[j]);
+                for (int u = 0; u < 8; ++u) av[u] = (k0 + u < K) ? ldv<Tc>(p.A, p.a64, ra + imap(p.kA, k0 + u)) : Tc(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const Tc *b = sB + (k0 + u) * NM;
+#pragma unroll
+                for (int j = 0; j < NM; ++j) acc[j] = fma(av[u], b[j], acc[j]);
+            }
+        }
+        if (sizeof(Tc) == 4 && p.cvec) {
+            // a contiguous, aligned FP32 output row (N a multiple of 4)
+            float4 *q = reinterpret_cast<float4 *>(static_cast<float *>(p.C) + rc);
+#pragma unroll
+            for (int j = 0; j < NM; j += 4)
+                if (j < N) q[j / 4] = make_float4((float)acc[j], (float)acc[j + 1], (float)acc[j + 2], (float)acc[j + 3]);
+            continue;
         }
 #pragma unroll
         for (int j = 0; j < NM; ++j) {
@@ -229,7 +254,12 @@ bool simt_small_fits(bool f64, int64_t K, int64_t N) { return K >= 1 && K <= kSm
 cudaError_t simt_contract_small(bool f64, const Contraction &c, cudaStream_t st) {
     if (c.M == 0 || c.N == 0) return cudaSuccess;
     if (!simt_small_fits(f64, c.K, c.N)) return cudaErrorInvalidValue;
-    const SimtDev d = make_simt(c);
+    SimtDev d = make_simt(c);
+    const bool abase = (reinterpret_cast<uintptr_t>(c.A) & 15) == 0, cbase = (reinterpret_cast<uintptr_t>(c.C) & 15) == 0;
+    d.avec = (!f64 && !c.A_f64 && abase && c.kA.R0 == 0 && c.kA.s0 == 1 && c.rowA.R0 == 0 && c.rowA.s0 % 4 == 0 &&
+              c.K % 4 == 0) ? 1 : 0;
+    d.cvec = (!f64 && !c.C_f64 && cbase && !c.accumulate && c.colC.R0 == 0 && c.colC.s0 == 1 && c.rowC.R0 == 0 &&
+              c.rowC.s0 % 4 == 0 && c.N % 4 == 0) ? 1 : 0;
     if (f64) {
         if (c.N <= 8) return launch_small<double, 8>(d, st);
         if (c.N <= 16) return launch_small<double, 16>(d, st);
