@@ -162,3 +162,54 @@ def test_spectral_argument_validation(lib):
     assert lib.kron_gauss_hermite(4, 0.0, x.ctypes.data, w.ctypes.data) == 1
     assert lib.kron_gauss_laguerre(4, -1.0, 1.0, x.ctypes.data, w.ctypes.data) == 1
     assert lib.kron_gauss_laguerre(4, 1.0, -2.0, x.ctypes.data, w.ctypes.data) == 1
+
+
+def test_ctucker_validation_without_gpu(lib):
+    """kron_ctucker rejects bad calls before any launch: fixed-point precisions,
+    conj outside {0, 1}, null pointers, misalignment to a complex element, a
+    short ld, a small workspace."""
+    h = ctypes.c_void_p()
+    ws = ctypes.c_size_t(0)
+    L = (ctypes.c_void_p * 2)(16, 16)
+    ld = _i64([3, 3])
+    assert lib.kron_plan_create(ctypes.byref(h), 2, _i64([3, 3]), _i64([3, 3]), 0, 5, 0) == 0  # FX32
+    assert lib.kron_ctucker_workspace_size(h, ctypes.byref(ws)) == 2
+    assert lib.kron_ctucker(h, ctypes.c_void_p(16), L, ld, 0, ctypes.c_void_p(16), None, ctypes.c_size_t(0),
+                            None) == 2
+    lib.kron_plan_destroy(h)
+    assert lib.kron_plan_create(ctypes.byref(h), 2, _i64([3, 3]), _i64([3, 3]), 0, 2, 1) == 0  # 3xTF32, trans
+    assert lib.kron_ctucker_workspace_size(h, ctypes.byref(ws)) == 0 and ws.value > 0
+    args = (L, ld)
+    assert lib.kron_ctucker(h, ctypes.c_void_p(16), *args, 2, ctypes.c_void_p(16), None, ctypes.c_size_t(0),
+                            None) == 1
+    assert lib.kron_ctucker(h, None, *args, 1, ctypes.c_void_p(16), None, ctypes.c_size_t(0), None) == 1
+    # complex double: 16-byte elements
+    assert lib.kron_ctucker(h, ctypes.c_void_p(24), *args, 1, ctypes.c_void_p(16), None, ctypes.c_size_t(0),
+                            None) == 3
+    assert lib.kron_ctucker(h, ctypes.c_void_p(16), L, _i64([2, 3]), 1, ctypes.c_void_p(16), None,
+                            ctypes.c_size_t(0), None) == 1
+    assert lib.kron_ctucker(h, ctypes.c_void_p(16), *args, 1, ctypes.c_void_p(16), ctypes.c_void_p(256),
+                            ctypes.c_size_t(0), None) == 4
+    lib.kron_plan_destroy(h)
+
+
+def test_spectral_matrix_validation_without_gpu(lib):
+    lib.kron_hermite_functions.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64,
+                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
+    lib.kron_laguerre_functions.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                            ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                            ctypes.c_void_p]
+    lib.kron_fourier_resample.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.c_void_p]
+    p = ctypes.c_void_p(256)
+    assert lib.kron_hermite_functions(0, 1.0, p, 4, p, 4, 0, None) == 1       # m < 1
+    assert lib.kron_hermite_functions(3, -1.0, p, 4, p, 4, 0, None) == 1      # beta <= 0
+    assert lib.kron_hermite_functions(3, 1.0, p, 4, p, 3, 0, None) == 1       # ldF < n
+    assert lib.kron_hermite_functions(3, 1.0, p, 4, p, 2, 1, None) == 1       # ldF < m (trans)
+    assert lib.kron_hermite_functions(3, 1.0, p, 4, p, 4, 2, None) == 1       # trans not 0 / 1
+    assert lib.kron_hermite_functions(3, 1.0, None, 0, None, 1, 0, None) == 0  # no points: nothing to do
+    assert lib.kron_laguerre_functions(3, -1.0, 1.0, p, 4, p, 4, 0, None) == 1  # alpha <= -1
+    assert lib.kron_laguerre_functions(3, 0.5, 0.0, p, 4, p, 4, 0, None) == 1   # beta <= 0
+    assert lib.kron_fourier_resample(0, 4, p, 4, None) == 1
+    assert lib.kron_fourier_resample(3, 4, p, 3, None) == 1
+    assert lib.kron_fourier_resample(3, 4, None, 4, None) == 1
