@@ -522,9 +522,11 @@ MULT = {"3xtf32": 3, "bf16x3": 3, "bf16x6": 6, "fx32": 10, "fx32h": 6}
 
 
 def run_configs(args):
-    """Times every configuration of the survey's measurement table through
-    the public API (CUDA events, L2 flushed before each run), plus the next
-    rows at the stepper's size.  One JSON line each; not the headline."""
+    """Times the other configurations (Tucker d=3 n=m=100, d=6 n=m=20, 512
+    batched problems, the adjoint d=4 n=m=48, complex cttucker, the HLF
+    evaluation) and the Kronecker-sum action and inverse Tucker operator at
+    the stepper's size, through the public API (CUDA events, L2 flushed
+    before each run).  One JSON line each; not the headline."""
     import torch
     import paper_2112_11238_gb300 as kron
     dev = torch.device("cuda", 0)
