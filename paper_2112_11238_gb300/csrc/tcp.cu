@@ -17,7 +17,10 @@
 //                 in 64-byte-swizzled K-major shared memory
 // Stages are guarded by full/empty mbarriers, accumulators by acc_full /
 // acc_empty mbarriers; with two accumulator buffers the epilogue of tile i
-// overlaps the main loop of tile i+1.  Every wait is bounded.
+// overlaps the main loop of tile i+1.  With one (the fixed-point forms: two
+// regions of 256 columns fill tensor memory) the MMA waits for the epilogue,
+// so the converter warps, idle then, take two thirds of it, staging output
+// boxes in the free A stages for TMA stores.  Every wait is bounded.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
