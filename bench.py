@@ -98,7 +98,9 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled during the timed region:
+    the sampler runs every 25 ms, the timed region starts once it delivers,
+    and only the samples between mark() and stop() are summarised."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -106,28 +108,38 @@ class ClockSampler:
 
     def __init__(self, gpu_index=0):
         self.gpu = gpu_index
-        self.samples = []
+        self.samples = []   # (time, fields)
         self.proc = None
         self.thread = None
+        self.t0 = None
+        self.t1 = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "25"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        deadline = time.monotonic() + 5.0  # the sampler is up once it has delivered
+        while not self.samples and time.monotonic() < deadline and self.proc.poll() is None:
+            time.sleep(0.005)
 
     def _read(self):
         for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) >= 9:
-                self.samples.append(parts)
+                self.samples.append((time.monotonic(), parts))
+
+    def mark(self):
+        """Start of the timed region."""
+        self.t0 = time.monotonic()
 
     def stop(self):
+        self.t1 = time.monotonic()
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -138,18 +150,24 @@ class ClockSampler:
             self.thread.join(timeout=5)
 
     def summary(self):
-        if not self.samples:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
-        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        t0 = self.t0 if self.t0 is not None else float("-inf")
+        t1 = self.t1 if self.t1 is not None else float("inf")
+        inside = [f for t, f in self.samples if t0 <= t <= t1]
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples in the timed region"]}
+        return self._summarise(inside)
+
+    def _summarise(self, samples):
+        sm = [float(s[1]) for s in samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in samples if s[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = set()
-        for s in self.samples:
+        for s in samples:
             for k, name in enumerate(names):
                 if s[5 + k].lower().startswith("active"):
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(self.samples)}
+                "reasons": sorted(reasons), "samples": len(samples)}
 
 
 # ------------------------------------------------------------------ oracle arm
@@ -241,6 +259,7 @@ def run_gpu(args):
     clocks.start()
     barrier(dist)
     torch.cuda.synchronize()
+    clocks.mark()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     for i in range(args.steps):
         l2_flush.zero_()

@@ -57,3 +57,17 @@ def test_launch_count_of_the_fixed_point_stepper():
     # expm (one launch), E images (2 per mode), U -> fixed point (2), 300 mode products
     assert bench.launches_per_step("fx32") == 1 + 6 + 2 + 300
     assert bench.launches_per_step("fx32h") == 1 + 6 + 2 + 300
+
+
+def test_clock_summary_counts_only_the_timed_region():
+    """Samples outside [mark, stop] are left out; throttle reasons are reported."""
+    import bench
+    c = bench.ClockSampler(0)
+    idle = ["0", "1200", "2070", "150", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"]
+    busy = ["0", "2070", "2070", "900", "0x0", "Not Active", "Not Active", "Not Active", "Active"]
+    c.samples = [(1.0, idle), (2.0, busy), (3.0, busy), (9.0, idle)]
+    c.t0, c.t1 = 1.5, 3.5
+    s = c.summary()
+    assert s["samples"] == 2 and s["sm_mhz"] == 2070.0 and s["reasons"] == ["sw_power_cap"]
+    c.t0, c.t1 = 4.0, 5.0
+    assert c.summary()["reasons"] == ["no samples in the timed region"]
