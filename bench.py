@@ -77,10 +77,12 @@ def whole_job_value(world, ms_per_step):
 
 def launches_per_step(prec):
     """Our kernels per stepper call: one launch for the exponentials; for the
-    fixed-point forms two per mode for the sliced image of E_mu, two for the
-    conversion of U to fixed point, then one per mode product."""
+    fixed-point forms four per mode (row exponents and sliced image of E_mu,
+    at full and at half tile width for the tail tiles), two for the
+    conversion of U to fixed point; for the split forms one image launch per
+    mode; then one launch per mode product."""
     if prec in FX_FORMS:
-        return 1 + 2 * D + 2 + NSTEPS * D
+        return 1 + 4 * D + 2 + NSTEPS * D
     return 1 + D + NSTEPS * D
 
 
@@ -335,6 +337,8 @@ def run_gpu(args):
             "gpu_launches": args.steps * launches_per_step(prec),
             "clocks": clocks.summary(),
         }
+        if not args.no_configs:
+            out["configs"] = workload_configs(kron, torch, dev, peaks)
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline_sample()
         print(json.dumps(out), flush=True)
@@ -432,10 +436,9 @@ def run_kernel_only(args):
 
 
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
-# capture of `bench.py --kernel-only --prec <form>` (the summaries and their
-# commands are in profiles/tcp_kernel_<form>_mode_product_256cubed.md).  The counters
-# hold for the kernel sources they were taken on only: another hash of those
-# files reports the traffic as unknown (null).
+# capture of `bench.py --kernel-only --prec <form>`.  The counters hold for
+# the kernel sources they were taken on only: another hash of those files
+# reports the traffic as unknown (null).
 KERNEL_SOURCES = ["tcp.cu", "tc_common.cuh", "ptx.cuh", "internal.h"]
 TRAFFIC = {"fx32h": {"bytes": 68.195840e6 + 18.230528e6, "src_sha1": "750763b9690166747553afa67a02bebd3e120ddd"}}
 
@@ -461,11 +464,12 @@ def roofline(kern, peaks, src, prec):
     The split form runs `mult` tensor-core products per algorithmic product,
     so its ceiling in algorithmic flops is the pipe's peak / mult; the pipe
     peak for TF32 is the measured bf16 peak times the nominal TF32/BF16
-    ratio.  The kernel runs inside a long step: sustained peak."""
+    ratio.  The kernel is timed in calls of a few milliseconds (a burst, not
+    a seconds-long loop under the power cap): the burst peak."""
     flops = 2.0 * N ** (D + 1)
     byts = 2.0 * N ** D * 4  # state in and out, 4 bytes per value (FP32 or 32-bit fixed point)
     t = kern["ms"] * 1e-3
-    bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    bf16 = peaks["bf16_tflops"]
     if prec == "3xtf32":
         pipe, mult = bf16 * NOMINAL["tf32"] / NOMINAL["bf16"], 3
     elif prec == "bf16x6":
@@ -486,7 +490,7 @@ def roofline(kern, peaks, src, prec):
                 "frac": (byts / t / 1e9) / peaks["hbm_gbs"], "traffic": None, "peak_source": src}
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": measured_traffic(prec), "algorithmic_bytes": byts,
-            "peak_source": f"{src} (sustained bf16 x nominal ratio / {mult} products)",
+            "peak_source": f"{src} (burst bf16 x nominal ratio / {mult} products)",
             "kernel_ms": kern["ms"]}
 
 
@@ -510,10 +514,10 @@ def _timed(torch, fn, reps=10, flush=None):
     return statistics.median(ts)
 
 
-def _line(name, prec, ms, flops, byts, peaks, mult=None):
-    """One JSON line: effective TFLOP/s, GB/s of the minimum bytes, and the
-    fraction of the bound (tensor pipe over `mult` products, or HBM) that the
-    smaller of the two times gives."""
+def _entry(name, prec, ms, flops, byts, peaks, mult=None):
+    """Effective TFLOP/s, GB/s of the minimum bytes, and the fraction of the
+    bound (tensor pipe over `mult` products, or HBM) that the smaller of the
+    two times gives."""
     t = ms * 1e-3
     out = {"config": name, "prec": prec, "ms": ms, "tflops": flops / t / 1e12, "min_bytes": byts,
            "gbs": byts / t / 1e9}
@@ -523,10 +527,9 @@ def _line(name, prec, ms, flops, byts, peaks, mult=None):
         fp_t = flops / (NOMINAL["fp64"] * 1e15)
         bound_t, bound = (fp_t, "fp64 (nominal)") if fp_t >= hbm_t else (hbm_t, "hbm")
         out["roofline"] = {"bound": bound, "frac": bound_t / t}
-        print(json.dumps(out), flush=True)
-        return
+        return out
     if mult:
-        pipe = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        pipe = peaks["bf16_tflops"]  # calls of milliseconds: the burst peak
         if prec == "3xtf32":
             pipe = pipe * NOMINAL["tf32"] / NOMINAL["bf16"]
         tc_t = flops * mult / (pipe * 1e12)
@@ -534,7 +537,112 @@ def _line(name, prec, ms, flops, byts, peaks, mult=None):
     else:
         bound_t, bound = hbm_t, "hbm"
     out["roofline"] = {"bound": bound, "frac": bound_t / t}
-    print(json.dumps(out), flush=True)
+    return out
+
+
+def _line(name, prec, ms, flops, byts, peaks, mult=None):
+    """The same as one JSON line."""
+    print(json.dumps(_entry(name, prec, ms, flops, byts, peaks, mult)), flush=True)
+
+
+def _rel(x, ref):
+    return float((x.double() - ref.double()).abs().max() / ref.double().abs().max())
+
+
+def workload_configs(kron, torch, dev, peaks):
+    """The other workloads at their full sizes, a few timed runs each, for the
+    benchmark line: Tucker d=3 n=m=100 (FP64 storage), Tucker d=6 n=m=20 (64M
+    elements, FP32 storage; FP64 storage for the FP64 path), 512 batched d=3
+    interpolation problems (FP32), and the forward + backward of the d=4
+    n=m=48 adjoint (FP32).  Each entry: time, effective TFLOP/s, roofline
+    fraction, and the max-norm relative error against the plain FP64 GPU path
+    on the same inputs."""
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    res = {}
+
+    c = W.tucker_d3()
+    T = kron.colmajor(torch.from_numpy(c.T).to(dev))
+    Ls = [kron.colmajor(torch.from_numpy(L).to(dev)) for L in c.L]
+    fl = W.tucker_flops([100] * 3, [100] * 3)
+    ref, rows = None, []
+    for prec in ("fp64", "fp32", "3xtf32", "bf16x6", "fx32h"):
+        plan = kron.TuckerPlan(T.shape, [100] * 3, torch.float64, prec)
+        ws = plan.workspace(dev)
+        S = kron.empty_colmajor([100] * 3, torch.float64, dev)
+        ms = _timed(torch, lambda: plan.tucker_into(T, Ls, S, ws=ws), reps=5, flush=flush)
+        ref = S.clone() if prec == "fp64" else ref
+        e = _entry("tucker d=3 n=m=100", prec, ms, fl, 2 * 8e6 + 3 * 8e4, peaks, MULT.get(prec))
+        e["rel_err_vs_fp64_gpu"] = _rel(S, ref)
+        rows.append(e)
+    res["tucker_d3_n100_f64"] = rows
+    del T, Ls, S, ws, ref
+
+    c = W.tucker_d6()
+    fl = W.tucker_flops([20] * 6, [20] * 6)
+    T64 = kron.colmajor(torch.from_numpy(c.T).to(dev))
+    L64 = [kron.colmajor(torch.from_numpy(L).to(dev)) for L in c.L]
+    T = T64.float()
+    Ls = [L.float() for L in L64]
+    ref, rows = None, []
+    for prec in ("fp64", "fp32", "3xtf32", "bf16x3", "bf16x6", "fx32h"):
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        Ti, Li = (T64, L64) if prec == "fp64" else (T, Ls)
+        plan = kron.TuckerPlan(Ti.shape, [20] * 6, dt, prec)
+        ws = plan.workspace(dev)
+        S = kron.empty_colmajor([20] * 6, dt, dev)
+        ms = _timed(torch, lambda: plan.tucker_into(Ti, Li, S, ws=ws), reps=5, flush=flush)
+        ref = S.clone() if prec == "fp64" else ref
+        e = _entry("tucker d=6 n=m=20", prec, ms, fl, 2 * (8 if prec == "fp64" else 4) * 20.0 ** 6, peaks,
+                   MULT.get(prec))
+        e["rel_err_vs_fp64_gpu"] = _rel(S, ref)
+        rows.append(e)
+        del S, ws
+    res["tucker_d6_n20"] = rows
+    del T, Ls, T64, L64, ref
+
+    c = W.batched()
+    Ts = [kron.colmajor(torch.from_numpy(t).float().to(dev)) for t in c.T]
+    Lb = [[kron.colmajor(torch.from_numpy(L).float().to(dev)) for L in row] for row in c.L]
+    Ss = [kron.empty_colmajor(tuple(int(v) for v in c.n[b]), torch.float32, dev) for b in range(len(Ts))]
+    refs = [kron.tucker(t.double(), [L.double() for L in row], prec="fp64") for t, row in zip(Ts, Lb)]
+    byts = 4.0 * (sum(int(np.prod(c.m[b])) + int(np.prod(c.n[b])) for b in range(len(Ts))))
+    rows = []
+    for prec in ("3xtf32", "bf16x3", "bf16x6"):
+        plan = kron.BatchedPlan(c.m, c.n, torch.float32, prec)
+        ws = plan.workspace(dev)
+        plan.bind(Ts, Lb, Ss, ws)
+        ms = _timed(torch, lambda: plan.run(ws), reps=5, flush=flush)
+        e = _entry("batched 512 x d=3, m in [8,64], n = ceil(1.5 m)", prec, ms, plan.flops(), byts, peaks,
+                   MULT.get(prec))
+        e["rel_err_vs_fp64_gpu"] = max(_rel(S, r) for S, r in zip(Ss, refs))
+        rows.append(e)
+    res["batched_512_d3_f32"] = rows
+    del Ts, Lb, Ss, refs
+
+    c, target = W.adjoint()
+    fl_f = W.tucker_flops([48] * 4, [48] * 4)
+    grads = {}
+    rows = []
+    for prec in ("fp64", "3xtf32", "bf16x6"):
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        T = kron.colmajor(torch.from_numpy(c.T).to(dev, dt)).requires_grad_(True)
+        Ls = [kron.colmajor(torch.from_numpy(L).to(dev, dt)).requires_grad_(True) for L in c.L]
+        tgt = kron.colmajor(torch.from_numpy(target).to(dev, dt))
+
+        def fwd_bwd():
+            T.grad = None
+            for L in Ls:
+                L.grad = None
+            S = kron.tucker_autograd(T, Ls, prec=prec)
+            ((S - tgt) ** 2).sum().mul(0.5).backward()
+        ms = _timed(torch, fwd_bwd, reps=5, flush=flush)
+        grads[prec] = [T.grad.clone()] + [L.grad.clone() for L in Ls]
+        e = _entry("adjoint d=4 n=m=48, forward + backward", prec, ms, fl_f * (1 + 7.1e9 / 2.04e9),
+                   4 * (8 if prec == "fp64" else 4) * 48.0 ** 4, peaks, MULT.get(prec))
+        e["rel_err_vs_fp64_gpu"] = max(_rel(a, b) for a, b in zip(grads[prec], grads["fp64"]))
+        rows.append(e)
+    res["adjoint_d4_n48"] = rows
+    return res
 
 
 MULT = {"3xtf32": 3, "bf16x3": 3, "bf16x6": 6, "fx32": 10, "fx32h": 6}
@@ -673,6 +781,8 @@ def main():
                     help="form of the timed stepper (fx32h and fx32 meet 2e-6 over the 100 steps; fx32h is "
                          "the faster)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="leave out the other workloads (configs object) of the benchmark line")
     ap.add_argument("--kernel-only", action="store_true",
                     help="run only the dominant kernel (256^3 mode products) a few times, for profilers")
     ap.add_argument("--configs", action="store_true",

@@ -16,9 +16,10 @@
  *    given by kron_dtype (double or float) and is the same for all tensors and
  *    matrices of a call, except where a call says otherwise.
  *  * Calls are asynchronous and ordered on the given CUDA stream (0 = legacy
- *    default stream).  No call synchronises the device, except
- *    kron_get_device_error.  The library allocates no device memory in any
- *    compute call: scratch comes from the caller's workspace `ws`
+ *    default stream).  No call synchronises the device; the calls that
+ *    must read a result on the host (kron_get_device_error,
+ *    kron_kronsum_pcg, kron_batched_bind) wait for their stream only.  The
+ *    library allocates no device memory in any compute call: scratch comes from the caller's workspace `ws`
  *    (`ws_bytes` long, 256-byte aligned), whose required size the matching
  *    *_workspace_size call reports.  Plans are host-only objects.
  *  * Output tensors must not overlap inputs or the workspace (except where a
@@ -122,11 +123,31 @@ KRON_API int kron_version(void);
 
 /*
  * Reads, and with clear != 0 resets, the device error word of the current
- * device (bit 0: a bounded wait inside a kernel timed out).  Synchronises the
- * device first.  *code receives the word; returns KRON_ERR_TIMEOUT if bit 0 is
- * set, KRON_OK otherwise.
+ * device: the OR of the words of every kernel file that latches errors
+ * (bit 0: a bounded wait inside a kernel timed out -- the mbarrier phases of
+ * the tensor-core pipelines, the in-launch job dependencies of the persistent
+ * kernel, the grid barriers of the exponential; bit 1: non-finite input or a
+ * zero pivot).  The read is ordered on `stream` and waits for that stream
+ * only (work queued on other streams is not waited for); *code receives the
+ * word.  Returns KRON_ERR_TIMEOUT if bit 0 is set, KRON_ERR_NUMERIC if bit 1
+ * is, KRON_OK otherwise.  A latched bit stays until cleared (it does not
+ * change how later launches run); the results of the launches that latched it
+ * are not to be trusted.
  */
-KRON_API kron_status kron_get_device_error(int *code, int clear);
+KRON_API kron_status kron_get_device_error(kron_stream_t stream, int *code, int clear);
+
+/*
+ * Test hook for the timeout path (the paper has no counterpart).  With
+ * hold != 0, every in-launch job dependency of the persistent tensor-core
+ * kernel (the batched Tucker operators) waits for one finished tile more than
+ * its job has, so the wait ends only at its time limit, `limit_ms`
+ * milliseconds (0: the default of 2 s; at most 10 s): the kernel then latches
+ * the timeout bit (see kron_get_device_error), carries on with the tile and
+ * returns normally, and the context stays usable.  hold = 0 restores normal
+ * operation.  Affects launches made after the call, on every device; not for
+ * production use.  KRON_ERR_INVALID_ARG for a negative or larger limit.
+ */
+KRON_API kron_status kron_debug_dependency_timeout(int hold, double limit_ms);
 
 /* ------------------------------------------------------------------------ */
 /* mu-mode product: Definition "mu-mode product", Eq. (mmp)                  */
@@ -155,8 +176,9 @@ KRON_API kron_status kron_mump(int d, const int64_t *m, int mu, int64_t n, const
  * image of op(L)) lives in a 1 MiB array compiled into the library, which
  * every GPU that loads the library holds until the process exits.  Sizes whose
  * image exceeds 1 MiB return KRON_ERR_WORKSPACE (n and m_mu up to 256 always
- * fit).  The first call on a device looks up the array's device address, so
- * make that first call outside any stream capture.  All calls on a device
+ * fit).  The first call on a device, and the first one after a device reset,
+ * looks up the array's device address (host code cannot use the array's name
+ * as one); make that call before any stream capture.  All calls on a device
  * share the array: calls whose execution overlaps on the GPU (other streams,
  * other host threads) race and give wrong results; calls ordered on one
  * stream are safe.  Other precisions return KRON_ERR_UNSUPPORTED.
@@ -396,6 +418,25 @@ KRON_API kron_status kron_batched_bind(kron_batched_plan plan, const void *const
                               size_t ws_bytes, kron_stream_t stream);
 KRON_API kron_status kron_batched_run(kron_batched_plan plan, void *ws, size_t ws_bytes,
                              kron_stream_t stream);
+
+/*
+ * One-shot form of the above (Section 3.2, Eq. (tensinterp)): plans, binds
+ * and runs in one call, S[b] = T[b] x_1 L[b][0] ... x_d L[b][d-1] for every
+ * problem b.  m, n: host arrays batch*d as for kron_batched_plan_create;
+ * T, S: host arrays of batch device pointers; L: host array of batch host
+ * arrays of d device pointers (L[b][mu] dense, ld n).  The workspace (size
+ * from kron_tucker_batched_workspace_size) receives the job tables, copied
+ * from pageable host memory on `stream` (the copy has read them when the call
+ * returns); no device or pinned memory is allocated.  Each call rebuilds the
+ * plan on the host, so for repeated runs of the same shapes (and for stream
+ * capture) use the plan / bind / run calls.  Same precisions and limits.
+ */
+KRON_API kron_status kron_tucker_batched_workspace_size(int batch, int d, const int64_t *m, const int64_t *n,
+                                                        kron_dtype dtype, kron_prec prec, size_t *bytes);
+KRON_API kron_status kron_tucker_batched(int batch, int d, const int64_t *m, const int64_t *n,
+                                         const void *const *T, const void *const *const *L, void *const *S,
+                                         kron_dtype dtype, kron_prec prec, void *ws, size_t ws_bytes,
+                                         kron_stream_t stream);
 
 #ifdef __cplusplus
 }

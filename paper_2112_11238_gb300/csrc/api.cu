@@ -306,17 +306,23 @@ const char *kron_status_string(kron_status s) {
 
 int kron_version(void) { return 100; }
 
-kron_status kron_get_device_error(int *code, int clear) {
+kron_status kron_get_device_error(kron_stream_t stream, int *code, int clear) {
     if (!code) return KRON_ERR_INVALID_ARG;
-    if (cudaDeviceSynchronize() != cudaSuccess) return KRON_ERR_CUDA;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     unsigned a = 0, b = 0, c = 0;
-    if (tc_error_word(&a, clear != 0) != cudaSuccess) return KRON_ERR_CUDA;
-    if (expm_error_word(&b, clear != 0) != cudaSuccess) return KRON_ERR_CUDA;
-    if (batched_error_word(&c, clear != 0) != cudaSuccess) return KRON_ERR_CUDA;
+    if (tc_error_word(&a, clear != 0, cs) != cudaSuccess) return KRON_ERR_CUDA;
+    if (tcp_error_word(&b, clear != 0, cs) != cudaSuccess) return KRON_ERR_CUDA;
+    if (expm_error_word(&c, clear != 0, cs) != cudaSuccess) return KRON_ERR_CUDA;
     const unsigned w = a | b | c;
     *code = (int)w;
     if (w & 1u) return KRON_ERR_TIMEOUT;
     if (w & 2u) return KRON_ERR_NUMERIC;
+    return KRON_OK;
+}
+
+kron_status kron_debug_dependency_timeout(int hold, double limit_ms) {
+    if (!(limit_ms >= 0.0) || limit_ms > 10000.0) return KRON_ERR_INVALID_ARG;
+    tcp_debug_dependency_timeout(hold != 0, (unsigned long long)(limit_ms * 1e6));
     return KRON_OK;
 }
 

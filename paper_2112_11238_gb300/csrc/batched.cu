@@ -21,7 +21,6 @@
 #include "tc_common.cuh"
 
 namespace kron {
-cudaError_t batched_error_word(unsigned int *out, bool clear) { return read_error_word(out, clear); }
 
 namespace {
 
@@ -139,8 +138,14 @@ int kb_of(int form) { return form == kTF32x3 ? kRowBytes / 4 : kRowBytes / 2; }
 
 extern "C" {
 
-kron_status kron_batched_plan_create(kron_batched_plan *plan, int batch, int d, const int64_t *m, const int64_t *n,
-                                     kron_dtype dtype, kron_prec prec, unsigned flags) {
+}  // extern "C"
+
+namespace {
+
+// Builds the plan; with_pinned: also the pinned staging buffer of bind (the
+// one-shot call uploads from pageable host memory instead).
+kron_status batched_plan_init(kron_batched_plan *plan, int batch, int d, const int64_t *m, const int64_t *n,
+                              kron_dtype dtype, kron_prec prec, unsigned flags, bool with_pinned) {
     if (!plan) return KRON_ERR_INVALID_ARG;
     *plan = nullptr;
     if (batch < 1 || batch > 65536 || d < 1 || d > KRON_MAX_D || !m || !n || flags != 0) return KRON_ERR_INVALID_ARG;
@@ -218,16 +223,25 @@ kron_status kron_batched_plan_create(kron_batched_plan *plan, int batch, int d, 
     pl->table_bytes = al(tcp_job_bytes() * njobs);
     off += pl->table_bytes;
     pl->done_off = off;
-    pl->done_bytes = al(sizeof(int) * njobs);
+    pl->done_bytes = al(sizeof(int) * (njobs + 1));  // + the launch's "a wait gave up" flag
     off += pl->done_bytes;
     pl->ws_bytes = off;
     pl->pinned_bytes = pl->imgjob_bytes + pl->table_bytes;
-    if (cudaMallocHost(reinterpret_cast<void **>(&pl->pinned), pl->pinned_bytes) != cudaSuccess) {
+    if (with_pinned && cudaMallocHost(reinterpret_cast<void **>(&pl->pinned), pl->pinned_bytes) != cudaSuccess) {
         delete pl;
         return KRON_ERR_CUDA;
     }
     *plan = pl;
     return KRON_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kron_status kron_batched_plan_create(kron_batched_plan *plan, int batch, int d, const int64_t *m, const int64_t *n,
+                                     kron_dtype dtype, kron_prec prec, unsigned flags) {
+    return batched_plan_init(plan, batch, d, m, n, dtype, prec, flags, true);
 }
 
 kron_status kron_batched_plan_destroy(kron_batched_plan plan) {
@@ -326,14 +340,25 @@ kron_status kron_batched_bind(kron_batched_plan plan, const void *const *T, cons
         const int dep = (s == 0) ? -1 : jid[(size_t)b * d + s - 1];
         jid[(size_t)b * d + s] = tcp_jobs_add(plan->jobs, c, w + plan->img_off[(size_t)b * d + mu], dep);
     }
-    // upload both tables (one copy from the pinned staging buffer)
+    // upload both tables: one copy from the pinned staging buffer, or (no
+    // staging buffer) from pageable memory, which the copy has consumed when
+    // cudaMemcpyAsync returns
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
-    if (cudaStreamSynchronize(cs) != cudaSuccess) return KRON_ERR_CUDA;  // staging buffer reuse
-    std::memcpy(plan->pinned, plan->imgjobs.data(), sizeof(ImgJob) * plan->imgjobs.size());
-    std::memcpy(plan->pinned + plan->imgjob_bytes, plan->jobs.host.data(), plan->jobs.host.size());
-    if (cudaMemcpyAsync(w + plan->imgjob_off, plan->pinned, plan->imgjob_bytes + plan->table_bytes,
-                        cudaMemcpyHostToDevice, cs) != cudaSuccess)
-        return KRON_ERR_CUDA;
+    if (plan->pinned) {
+        if (cudaStreamSynchronize(cs) != cudaSuccess) return KRON_ERR_CUDA;  // staging buffer reuse
+        std::memcpy(plan->pinned, plan->imgjobs.data(), sizeof(ImgJob) * plan->imgjobs.size());
+        std::memcpy(plan->pinned + plan->imgjob_bytes, plan->jobs.host.data(), plan->jobs.host.size());
+        if (cudaMemcpyAsync(w + plan->imgjob_off, plan->pinned, plan->imgjob_bytes + plan->table_bytes,
+                            cudaMemcpyHostToDevice, cs) != cudaSuccess)
+            return KRON_ERR_CUDA;
+    } else {
+        std::vector<uint8_t> stage(plan->imgjob_bytes + plan->table_bytes, 0);
+        std::memcpy(stage.data(), plan->imgjobs.data(), sizeof(ImgJob) * plan->imgjobs.size());
+        std::memcpy(stage.data() + plan->imgjob_bytes, plan->jobs.host.data(), plan->jobs.host.size());
+        if (cudaMemcpyAsync(w + plan->imgjob_off, stage.data(), stage.size(), cudaMemcpyHostToDevice, cs) !=
+            cudaSuccess)
+            return KRON_ERR_CUDA;
+    }
     plan->bound = true;
     plan->bound_ws = ws;
     return KRON_OK;
@@ -360,6 +385,39 @@ kron_status kron_batched_run(kron_batched_plan plan, void *ws, size_t ws_bytes, 
     if (tcp_jobs_run(plan->jobs, w + plan->table_off, reinterpret_cast<int *>(w + plan->done_off), cs) != cudaSuccess)
         return KRON_ERR_CUDA;
     return KRON_OK;
+}
+
+// One-shot form: plan, bind and run in one call (host-side plan only; the
+// tables go to the workspace from pageable host memory, so nothing is
+// allocated on the device or pinned).
+kron_status kron_tucker_batched_workspace_size(int batch, int d, const int64_t *m, const int64_t *n,
+                                               kron_dtype dtype, kron_prec prec, size_t *bytes) {
+    if (!bytes) return KRON_ERR_INVALID_ARG;
+    kron_batched_plan pl = nullptr;
+    kron_status st = batched_plan_init(&pl, batch, d, m, n, dtype, prec, 0, false);
+    if (st != KRON_OK) return st;
+    *bytes = pl->ws_bytes;
+    delete pl;
+    return KRON_OK;
+}
+
+kron_status kron_tucker_batched(int batch, int d, const int64_t *m, const int64_t *n, const void *const *T,
+                                const void *const *const *L, void *const *S, kron_dtype dtype, kron_prec prec,
+                                void *ws, size_t ws_bytes, kron_stream_t stream) {
+    if (!T || !L || !S) return KRON_ERR_INVALID_ARG;
+    kron_batched_plan pl = nullptr;
+    kron_status st = batched_plan_init(&pl, batch, d, m, n, dtype, prec, 0, false);
+    if (st != KRON_OK) return st;
+    std::vector<const void *> flat((size_t)batch * d, nullptr);
+    for (int b = 0; b < batch && st == KRON_OK; ++b) {
+        if (!L[b]) st = KRON_ERR_INVALID_ARG;
+        else
+            for (int k = 0; k < d; ++k) flat[(size_t)b * d + k] = L[b][k];
+    }
+    if (st == KRON_OK) st = kron_batched_bind(pl, T, flat.data(), S, ws, ws_bytes, stream);
+    if (st == KRON_OK) st = kron_batched_run(pl, ws, ws_bytes, stream);
+    delete pl;  // no staging buffer: nothing on the device refers to the plan
+    return st;
 }
 
 }  // extern "C"

@@ -73,7 +73,7 @@ __device__ bool grid_sync(unsigned *bar, int gs) {
         } else {
             const unsigned long long t0 = globaltimer_ns();
             while (*vgen == my_gen) {
-                if (device_error_set() || globaltimer_ns() - t0 > kWaitLimitNs) {
+                if (timeout_latched() || globaltimer_ns() - t0 > kWaitLimitNs) {
                     latch_error(kErrTimeout);
                     failed = 1;
                     break;
@@ -366,7 +366,7 @@ void pade13(double *b) {
 
 }  // namespace
 
-cudaError_t expm_error_word(unsigned int *out, bool clear) { return read_error_word(out, clear); }
+cudaError_t expm_error_word(unsigned int *out, bool clear, cudaStream_t st) { return read_error_word(out, clear, st); }
 
 size_t expm_workspace_bytes(int64_t n) {
     // 13 n x n matrices + the n x 3n augmented matrix + barrier/norm words

@@ -131,7 +131,7 @@ void tcp_jobs_begin(TcpJobs &jobs, int form);
 int tcp_jobs_add(TcpJobs &jobs, const Contraction &c, const void *img, int dep);
 size_t tcp_jobs_table_bytes(const TcpJobs &jobs);
 // `table`: device copy of jobs.host (needed above 8 jobs); `done`: one int per
-// job of device scratch (zeroed by the call).
+// job plus one of device scratch (zeroed by the call).
 cudaError_t tcp_jobs_run(const TcpJobs &jobs, const void *table, int *done, cudaStream_t st);
 
 // ---- CUDA-core path (simt.cu) ----
@@ -175,9 +175,17 @@ double *inv_result(int64_t n, void *ws);
 cudaError_t inv_gj_batch(int count, const int64_t *n, const void *const *P, const int64_t *ldP, bool p64,
                          void *const *ws, cudaStream_t st);
 
-// Device error words of the translation units that have bounded waits.
-cudaError_t tc_error_word(unsigned int *out, bool clear);
-cudaError_t expm_error_word(unsigned int *out, bool clear);
-cudaError_t batched_error_word(unsigned int *out, bool clear);
+// Device error words of the translation units whose kernels latch errors
+// (bounded waits, non-finite input): stream-ordered read, optional clear.
+cudaError_t tc_error_word(unsigned int *out, bool clear, cudaStream_t st);
+cudaError_t tcp_error_word(unsigned int *out, bool clear, cudaStream_t st);
+cudaError_t expm_error_word(unsigned int *out, bool clear, cudaStream_t st);
+
+// Test hook of the in-launch job dependencies of the persistent kernel
+// (tcp.cu): with hold != 0 every dependency wants one more finished tile
+// than its job has, so the wait can only end by its time limit, which is
+// limit_ns (0: the default kWaitLimitNs).  Applies to launches made after
+// the call, on every device.
+void tcp_debug_dependency_timeout(int hold, unsigned long long limit_ns);
 
 }  // namespace kron

@@ -21,21 +21,48 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
+// per device: the context the address was looked up in, and the address
+void *g_scratch_ctx[kMaxDevices] = {};
 void *g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (host code cannot use the array's name as a device address).
+// cuCtxGetCurrent from the driver (no link-time dependency on it).
+using CtxGetCurrentFn = int (*)(void **);
+CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(p);
+    });
+    return fn;
+}
+
+// Device address of the scratch array on the current device.  Host code
+// cannot use the array's name as a device address (it names a host-side
+// stand-in), so the address is looked up with cudaGetSymbolAddress, with the
+// device current, once per device and context: a device reset destroys the
+// primary context and, with it, the module holding the array, and the next
+// context may place it elsewhere, so a changed context means a new lookup.
 cudaError_t scratch_address(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    // (before the first runtime call that needs it, no context is current:
+    // then the address is looked up afresh, which also creates the context)
+    void *ctx = nullptr;
+    CtxGetCurrentFn get = ctx_get_current();
+    const bool have_ctx = get != nullptr && get(&ctx) == 0 && ctx != nullptr;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    if (!have_ctx || !g_scratch_ptr[dev] || g_scratch_ctx[dev] != ctx) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_ptr[dev] = p;
+        g_scratch_ctx[dev] = have_ctx ? ctx : nullptr;
     }
     *out = g_scratch_ptr[dev];
     return cudaSuccess;

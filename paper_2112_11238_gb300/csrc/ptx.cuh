@@ -9,21 +9,30 @@ namespace kron {
 
 // Error word of this translation unit on the current device.  Bit 0: a
 // bounded wait timed out; bit 1: non-finite input where a finite one is
-// required.  Each .cu file including this header owns one word and exposes a
-// host accessor for it (see internal.h).
+// required.  Each .cu file including this header owns one word (device code
+// is compiled per file, without relocatable device code); the files whose
+// kernels latch errors expose a host accessor for theirs (see internal.h), and
+// kron_get_device_error reads and clears all of them.
 static __device__ unsigned int g_device_error;
 
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
 constexpr unsigned int kErrTimeout = 1u;
 constexpr unsigned int kErrNumeric = 2u;
 
-// Host side: reads (and optionally clears) this translation unit's word.
-static inline cudaError_t read_error_word(unsigned int *out, bool clear) {
-    cudaError_t e = cudaMemcpyFromSymbol(out, g_device_error, sizeof(unsigned int));
-    if (e == cudaSuccess && clear) {
-        const unsigned int zero = 0;
-        e = cudaMemcpyToSymbol(g_device_error, &zero, sizeof(unsigned int));
-    }
+// Host side: stream-ordered read (and optionally clear) of this translation
+// unit's word; waits for `st` only, not for the whole device.  The symbol's
+// address is looked up on every call (the primary context, and with it the
+// address, may change after a device reset).
+static inline cudaError_t read_error_word(unsigned int *out, bool clear, cudaStream_t st) {
+    void *addr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&addr, g_device_error);
+    if (e != cudaSuccess) return e;
+    unsigned int v = 0;
+    e = cudaMemcpyAsync(&v, addr, sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && clear && v != 0u) e = cudaMemsetAsync(addr, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess && clear && v != 0u) e = cudaStreamSynchronize(st);
+    *out = v;
     return e;
 }
 
@@ -39,8 +48,10 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 
 __device__ __forceinline__ void latch_error(unsigned int bit) { atomicOr(&g_device_error, bit); }
 
-__device__ __forceinline__ bool device_error_set() {
-    return *reinterpret_cast<volatile unsigned int *>(&g_device_error) != 0u;
+// A wait of this translation unit has timed out (since the word was last
+// cleared).
+__device__ __forceinline__ bool timeout_latched() {
+    return (*reinterpret_cast<volatile unsigned int *>(&g_device_error) & kErrTimeout) != 0u;
 }
 
 // ---------------------------------------------------------------- mbarrier
@@ -71,11 +82,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 // Waits for the phase with the given parity to complete.  Gives up after
-// kWaitLimitNs (or at once if another wait already gave up), latching
-// kErrTimeout; returns false then.
-// The spin only polls the barrier; the clock is read every 256 polls and
-// the (global, slow) error word only once a wait has lasted over 1 ms, so
-// a normal hand-over costs no memory round trip.
+// kWaitLimitNs, latching kErrTimeout; returns false then.  A wait never gives
+// up early because some other wait did: the threads of a CTA meet at named
+// barriers, and a thread that left its loop early while its peers carried on
+// would leave them at such a barrier for good.  The spin only polls the
+// barrier and reads the clock every four polls.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer_ns();
@@ -83,9 +94,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 #pragma unroll 1
         for (int i = 0; i < 4; ++i)
             if (mbar_try_wait(bar, parity)) return true;
-        const unsigned long long dt = globaltimer_ns() - t0;
-        if (dt > 1000000ull && device_error_set()) return false;
-        if (dt > kWaitLimitNs) {
+        if (globaltimer_ns() - t0 > kWaitLimitNs) {
             latch_error(kErrTimeout);
             return false;
         }

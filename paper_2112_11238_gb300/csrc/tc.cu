@@ -382,7 +382,7 @@ __global__ void splitk_reduce_kernel(const float *__restrict__ P, int64_t splits
 
 // ------------------------------------------------------------------ host
 
-cudaError_t tc_error_word(unsigned int *out, bool clear) { return read_error_word(out, clear); }
+cudaError_t tc_error_word(unsigned int *out, bool clear, cudaStream_t st) { return read_error_word(out, clear, st); }
 
 static int pieces_of(int form) { return form == kFX32 ? 4 : ((form == kBF16x6 || form == kFX32H) ? 3 : 2); }
 static int bk_of(int form) { return form == kTF32x3 ? kRowBytes / 4 : kRowBytes / 2; }

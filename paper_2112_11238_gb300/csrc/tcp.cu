@@ -25,6 +25,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 
@@ -84,13 +85,46 @@ struct RawCfg {
     static constexpr int STAGES = (F == kFX32) ? 2 : 4;
 };
 
+// Constants of the fixed-point form F: magnitude bits b of its integers
+// (|X| < 2^b), the accumulator unit 2^(eA + f_c + UNIT) of a product of two
+// fixed-point operands with scales eA and f_c, and the left shift VS of the
+// level-0 accumulator in the 64-bit value path.
+//   FX32:  four 8-bit digits, slices d_t 2^(-8t), x = 2^24 (sum of slices):
+//          b = 31, UNIT = 48 - 62 = -14, level 0 an integer below 2^24.
+//   FX32H: three digits (8, 11, 11 bits), slices d0 2^8, d1 2^-3, d2 2^-14,
+//          x = 2^14 (sum of slices): b = 29, UNIT = 28 - 58 = -30, level 0 a
+//          multiple of 2^16 (above 2^31 for long K: no 32-bit conversion).
+template <int F>
+struct FxForm {
+    static constexpr int BITS = (F == kFX32H) ? 29 : 31;
+    static constexpr int UNIT = (F == kFX32H) ? -30 : -14;
+    static constexpr int VS = (F == kFX32H) ? 0 : 16;
+};
+
+// Left shift that brings the largest magnitude mA of a fixed-point operand to
+// the top of the form's range (|X| < 2^b): the scale of every intermediate is
+// chosen before its values exist, from a bound (the input's largest value
+// times the largest row sum of |op(L)|) that is several times the actual
+// largest output, so an intermediate can reach the next product with its top
+// bits unused.  Shifted back up, its digit slices are full and the slice
+// products left out are as small, relative to the data, as for the input
+// tensor.  mA is an upper bound of the stored magnitudes, so the shifted
+// values stay below 2^b.
+template <int F>
+__device__ __forceinline__ int fx_shift(unsigned mA) {
+    if (mA == 0u) return 0;
+    return max(0, FxForm<F>::BITS - (32 - __clz((int)mA)));
+}
+
 struct TcLaunch {
     TcJob inl[kMaxInline];  // small tables travel with the launch (tensor maps included)
     const TcJob *jobs;      // device table (when njobs > kMaxInline)
     int njobs, total_tiles;
-    int *done;              // finished tiles per job (zeroed before the launch)
+    int *done;              // finished tiles per job, then one "a wait gave up" flag (zeroed before the launch)
     FxScale *reset_next;    // fixed point: scale word the next launch writes, cleared here
     int stages, nacc, nbuf, acc_cols, bn_max;
+    int dep_hold;                      // test hook: extra tiles every dependency waits for
+    unsigned long long dep_wait_ns;    // time limit of a dependency wait
 };
 
 __device__ __forceinline__ const TcJob &job_at(const TcLaunch &L, int j) {
@@ -251,11 +285,12 @@ __device__ __forceinline__ void raw_issue(const TcJob &J, const int64_t (&base)[
 
 // Float sources: raw tiles arrive through cp.async several K-blocks ahead;
 // the converters split them from shared memory.
+// fsh: the left shift of a fixed-point A (fx_shift of its scale word).
 template <int F, typename Join>
 __device__ __forceinline__ bool conv_tile_loop_raw(const TcJob &J, const CUtensorMap *tm, uint64_t *rfull,
                                                    uint32_t &rc, int mt, uint8_t *sA, uint32_t A_ST, uint8_t *sRaw,
                                                    uint64_t *full, uint64_t *empty, int S, uint32_t &g, int lane,
-                                                   int ct, Join &&join) {
+                                                   int ct, int fsh, Join &&join) {
     using R = RawCfg<F>;
     constexpr int BK = R::BK;
     constexpr int CH = 16 / FT<F>::ELEM;
@@ -352,7 +387,7 @@ __device__ __forceinline__ bool conv_tile_loop_raw(const TcJob &J, const CUtenso
             if constexpr (is_fx_f<F>()) {
                 int32_t x[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) x[e] = __float_as_int(v[e]);
+                for (int e = 0; e < 8; ++e) x[e] = (int32_t)(__float_as_uint(v[e]) << fsh);
                 fx_pack_f<F>(x, out);
             } else {
                 split_pack<F, float>(v, out);
@@ -404,22 +439,6 @@ __device__ __forceinline__ int add_sat(int a, int b) {
     return r;
 }
 
-// Constants of the fixed-point form F: magnitude bits b of its integers
-// (|X| < 2^b), the accumulator unit 2^(eA + f_c + UNIT) of a product of two
-// fixed-point operands with scales eA and f_c, and the left shift VS of the
-// level-0 accumulator in the 64-bit value path.
-//   FX32:  four 8-bit digits, slices d_t 2^(-8t), x = 2^24 (sum of slices):
-//          b = 31, UNIT = 48 - 62 = -14, level 0 an integer below 2^24.
-//   FX32H: three digits (8, 11, 11 bits), slices d0 2^8, d1 2^-3, d2 2^-14,
-//          x = 2^14 (sum of slices): b = 29, UNIT = 28 - 58 = -30, level 0 a
-//          multiple of 2^16 (above 2^31 for long K: no 32-bit conversion).
-template <int F>
-struct FxForm {
-    static constexpr int BITS = (F == kFX32H) ? 29 : 31;
-    static constexpr int UNIT = (F == kFX32H) ? -30 : -14;
-    static constexpr int VS = (F == kFX32H) ? 0 : 16;
-};
-
 // Scales of one fixed-point job, the same for all of its tiles: A's scale
 // eA and the output scale eC = eA_actual + g, where |A| < 2^eA_actual (from
 // A's largest magnitude) and every row sum of |op(L)| is below 2^g, so that
@@ -439,6 +458,9 @@ __device__ __forceinline__ void fx_consts(const TcJob &J, int j, FxConsts &k) {
     const unsigned long long gb = *J.fxG;  // bits of the largest row sum (non-negative)
     const int g = gb ? (int)((gb >> 52) & 0x7FF) - 1022 : 0;
     k.eC = eAact + g;
+    // the converters shift A left by fx_shift: its values carry the scale
+    // 2^(eA - shift - b) from there on
+    k.eA -= fx_shift<F>(mA);
 }
 
 // Fixed-point form epilogue for one tile row.  The two accumulator regions
@@ -904,9 +926,18 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
         };
         int it = 0;
         bool ok = true;
+        // fixed point: the left shift of the current job's A (its scale word
+        // was written by an earlier launch), read once per job
+        int fsh = 0, fsh_job = -1;
         for (int t = blockIdx.x; t < L.total_tiles && ok; t += gridDim.x, ++it) {
             const int jt = find_job(L, t);
             const TcJob J = job_at(L, jt);
+            if constexpr (is_fx_f<F>()) {
+                if (jt != fsh_job) {
+                    fsh = fx_shift<F>(J.fxA->maxabs);
+                    fsh_job = jt;
+                }
+            }
             const CUtensorMap *tm = &job_at(L, jt).tmA;  // launch parameter space
             const int lt = t - J.tile_begin;
             const int mt = lt / J.tiles_n;
@@ -914,22 +945,30 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
                 // the tile waited for may be the previous tile of this CTA
                 if (!epi_prev()) break;
                 // wait until every tile of the job this one reads is stored
+                // (bounded: at the limit the timeout is latched and the tile
+                // goes ahead; once a dependency wait of this launch has given
+                // up, the others give up after 1 ms)
                 if (ct == 0) {
                     volatile int *dn = L.done + J.dep;
+                    volatile int *gave_up = L.done + L.njobs;
+                    const int need = J.dep_tiles + L.dep_hold;
                     const unsigned long long t0 = globaltimer_ns();
-                    while (*dn < J.dep_tiles) {
+                    while (*dn < need) {
                         const unsigned long long dt = globaltimer_ns() - t0;
-                        if ((dt > 1000000ull && device_error_set()) || dt > kWaitLimitNs) {
+                        if (dt > L.dep_wait_ns) {
                             latch_error(kErrTimeout);
+                            *gave_up = 1;
                             break;
                         }
+                        if (dt > 1000000ull && *gave_up != 0) break;
                     }
                     __threadfence();
                 }
                 named_bar(2, 32 * kConv);
             }
             if constexpr (is_fx_f<F>()) {  // always 32-bit integers
-                ok = conv_tile_loop_raw<F>(J, tm, rfull, rc, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct, epi_prev);
+                ok = conv_tile_loop_raw<F>(J, tm, rfull, rc, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct, fsh,
+                                           epi_prev);
                 if (join) {
                     pend = t;
                     pend_it = it;
@@ -937,7 +976,8 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
             } else {
                 auto none = []() { return true; };
                 ok = J.a64 ? conv_tile_loop<F, double>(J, mt, sA, A_ST, full, empty, S, g, lane, ct)
-                           : conv_tile_loop_raw<F>(J, tm, rfull, rc, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct, none);
+                           : conv_tile_loop_raw<F>(J, tm, rfull, rc, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct, 0,
+                                                   none);
             }
         }
         if (ok) epi_prev();
@@ -953,6 +993,16 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
 }  // namespace
 
 // ---------------------------------------------------------------- host side
+
+cudaError_t tcp_error_word(unsigned int *out, bool clear, cudaStream_t st) { return read_error_word(out, clear, st); }
+
+static std::atomic<int> g_dep_hold{0};
+static std::atomic<unsigned long long> g_dep_wait_ns{0};
+
+void tcp_debug_dependency_timeout(int hold, unsigned long long limit_ns) {
+    g_dep_hold.store(hold ? 1 : 0);
+    g_dep_wait_ns.store(limit_ns);
+}
 
 static int pieces_of_f(int form) { return form == kFX32 ? 4 : ((form == kBF16x6 || form == kFX32H) ? 3 : 2); }
 static int bk_of_f(int form) { return form == kTF32x3 ? kRowBytes / 4 : kRowBytes / 2; }
@@ -1192,8 +1242,11 @@ static cudaError_t tcp_launch(int form, const TcJob *jobs, int njobs, int total_
     size_t smem;
     pick_config(form, bn_max, nkb_max, L.stages, L.nacc, L.nbuf, L.acc_cols, smem);
     L.bn_max = bn_max;
+    L.dep_hold = g_dep_hold.load();
+    L.dep_wait_ns = g_dep_wait_ns.load();
+    if (L.dep_wait_ns == 0) L.dep_wait_ns = kWaitLimitNs;
     if (done != nullptr) {
-        cudaError_t e = cudaMemsetAsync(done, 0, sizeof(int) * (size_t)njobs, st);
+        cudaError_t e = cudaMemsetAsync(done, 0, sizeof(int) * ((size_t)njobs + 1), st);
         if (e != cudaSuccess) return e;
     }
     const int grid = std::min(total_tiles, num_sms());

@@ -17,28 +17,24 @@ import numpy as np
 #  fx32h  : 29-bit fixed point (2^-29 of the largest magnitude, four times
 #           coarser than fx32) and three digit slices: the two level-3
 #           products left out are at most 2^-27 of the largest product per
-#           term, with no preferred sign.  Every intermediate state takes its
-#           scale from the row-sum bound of |op(L_mu)|, which for Gaussian
-#           operators is several times the typical output (up to 3 of the 29
-#           bits unused per mode); measured up to 1.9e-6 on such chains,
-#           bound 4e-6.  Operators whose row sums are near their outputs
-#           (the stepper's exponentials) stay far below: 1.4e-7 over 300
-#           chained products.
+#           term, with no preferred sign.  Every intermediate is shifted up to
+#           the top of the 29-bit range before it is sliced again, so the
+#           products left out stay that small relative to the data; 2e-6, the
+#           split-form budget.
 TOL = {"fp64": 1e-12, "3xtf32": 2e-6, "bf16x6": 2e-6, "bf16x3": 6e-5, "fp32": 1e-5, "fx32": 2e-7,
-       "fx32h": 4e-6}
+       "fx32h": 2e-6}
 
 
 def tol(prec, ksum):
     """Bound for a chain whose contracted lengths add up to ksum.
 
-    The split forms accumulate in FP32 inside tensor memory, where every MMA
-    step may drop up to one unit in the last place of the running sum; with
-    one fresh accumulator per K-block of 32 (up to four, summed in FP32 at
-    the end) the error of random-sign data grows about linearly in the
-    contracted length.  Above 256 accumulated terms the budget is widened
-    in proportion: u_fp32 / 8 = 7.5e-9 per term."""
+    Every split and fixed-point form is held to its budget whatever the
+    contraction length.  Plain FP32 (CUDA-core fused multiply-add, not a
+    split form) accumulates rounding about linearly in the contracted
+    length; above 1333 accumulated terms its bound grows in proportion:
+    u_fp32 / 8 = 7.5e-9 per term."""
     base = TOL[prec]
-    if prec in ("3xtf32", "bf16x6", "fp32"):
+    if prec == "fp32":
         return max(base, 7.5e-9 * ksum)
     return base
 

@@ -118,6 +118,27 @@ def test_call_validation_without_gpu(lib):
     assert lib.kron_expm_workspace_size(256, ctypes.byref(ws)) == 0
 
 
+def test_error_word_and_timeout_hook_validation(lib):
+    lib.kron_debug_dependency_timeout.argtypes = [ctypes.c_int, ctypes.c_double]
+    # limits outside [0, 10 s] are refused; a valid call only sets host state
+    assert lib.kron_debug_dependency_timeout(1, ctypes.c_double(-1.0)) == 1
+    assert lib.kron_debug_dependency_timeout(1, ctypes.c_double(2e4)) == 1
+    assert lib.kron_debug_dependency_timeout(0, ctypes.c_double(0.0)) == 0
+    # the word needs somewhere to go
+    assert lib.kron_get_device_error(None, None, 0) == 1
+
+
+def test_tucker_batched_one_shot_validation(lib):
+    ws = ctypes.c_size_t(0)
+    m, n = _i64([8, 9, 10, 12, 14, 15]), _i64([12, 14, 15, 18, 21, 23])
+    assert lib.kron_tucker_batched_workspace_size(2, 3, m, n, 1, 2, ctypes.byref(ws)) == 0 and ws.value > 0
+    # plain precisions are not offered by the batched kernel
+    assert lib.kron_tucker_batched_workspace_size(2, 3, m, n, 1, 0, ctypes.byref(ws)) == 2
+    assert lib.kron_tucker_batched_workspace_size(0, 3, m, n, 1, 2, ctypes.byref(ws)) == 1
+    # null pointer arrays are refused before anything is launched
+    assert lib.kron_tucker_batched(2, 3, m, n, None, None, None, 1, 2, None, ctypes.c_size_t(0), None) == 1
+
+
 def test_mump_workspace_query(lib):
     ws = ctypes.c_size_t(0)
     assert lib.kron_mump_workspace_size(3, _i64([5, 6, 7]), 1, 9, 1, 2, ctypes.byref(ws)) == 0

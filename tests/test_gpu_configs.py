@@ -1,14 +1,14 @@
 """Parity at the full workload sizes, against the FP64 oracle.
 
 * Tucker d=3, n=m=100 (random normal): every output against the oracle.
-* Tucker d=6, n=m=20 (Chebyshev-Vandermonde L): a sampled sub-grid of outputs,
-  S[I_1, ..., I_6] = T x_1 L_1[I_1, :] ... x_6 L_6[I_6, :], computed by the
-  oracle with row-subsampled matrices.
+* Tucker d=6, n=m=20 (Chebyshev-Vandermonde L): all 64M outputs against the
+  oracle's (computed once per module).
 * Stepper, 256^3, tau = 1e-4, 100 steps: the rank-4 initial field makes the
   exact U_100 = sum_r (E^100 f_r1) o (E^100 f_r2) o (E^100 f_r3) with the
   closed-form E^100 = exp(100 tau A) (oracle, long double).
 * Adjoint d=4, n=m=48: gradients against the oracle gradient and against
-  central differences of the FP64 loss.
+  central differences of the FP64 loss along 16 random directions per
+  argument.
 """
 import numpy as np
 import pytest
@@ -41,35 +41,27 @@ def test_tucker_d3_n100(kron, cfg_d3, prec):
     S = kron.tucker(to_dev(c.T), [to_dev(L) for L in c.L], prec=prec)
     err = rel_err(to_host(S), ref)
     print(f"tucker d=3 n=100 {prec}: max-norm rel err {err:.3e}")
-    # the workload budget for every split form, fx32 included.  fx32h: every
-    # intermediate state takes its scale from the row-sum bound of |L_mu|,
-    # which on these Gaussian operators is about 9 times the typical output
-    # (about 3 of its 29 bits unused per mode); measured 1.9e-6, bound 4e-6
-    bound = 2e-6 if prec == "fx32" else TOL[prec]
+    # the workload budget for every split form, both fixed-point forms included
+    bound = 2e-6 if prec in ("fx32", "fx32h") else TOL[prec]
     assert err <= bound, err
 
 
 @pytest.fixture(scope="module")
 def cfg_d6():
     c = W.tucker_d6()
-    g = np.random.default_rng(99)
-    idx = [np.sort(g.choice(20, 3, replace=False)) for _ in range(6)]
-    ref = oracle.tucker(c.T, [L[i, :] for L, i in zip(c.L, idx)])
-    return c, idx, ref
+    return c, oracle.tucker(c.T, c.L)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "3xtf32", "bf16x3", "bf16x6", "fp32", "fx32", "fx32h"])
-def test_tucker_d6_n20_sampled(kron, cfg_d6, prec):
+def test_tucker_d6_n20_full(kron, cfg_d6, prec):
+    """All 64M outputs of the d=6 n=m=20 chain against the FP64 oracle."""
     import torch
-    c, idx, ref = cfg_d6
+    c, ref = cfg_d6
     dtype = torch.float64 if prec in ("fp64", "fx32", "fx32h") else torch.float32
     S = kron.tucker(to_dev(c.T, dtype), [to_dev(L, dtype) for L in c.L], prec=prec)
-    ix = [torch.as_tensor(i, device=S.device) for i in idx]
-    sub = S
-    for mu, i in enumerate(ix):
-        sub = sub.index_select(mu, i)
-    err = rel_err(to_host(sub), ref)
-    print(f"tucker d=6 n=20 {prec}: sampled max-norm rel err {err:.3e}")
+    err = rel_err(to_host(S), ref)
+    del S
+    print(f"tucker d=6 n=20 {prec}: max-norm rel err over all 64M outputs {err:.3e}")
     assert err <= max(TOL[prec], 1e-7 if dtype == torch.float32 else 0), err
 
 
@@ -145,22 +137,44 @@ def test_adjoint_d4_n48_against_oracle_gradient(kron, cfg_adjoint, prec):
     print()
 
 
-def _loss64(T, Ls, target):
-    r = oracle.tucker(T, Ls) - target
-    return 0.5 * float(np.sum(r * r))
+def _tucker64(T, Ls):
+    """The Tucker operator by numpy.tensordot, one mode at a time (FP64)."""
+    X = T
+    for mu, L in enumerate(Ls):
+        X = np.moveaxis(np.tensordot(L, X, axes=([1], [mu])), 0, mu)
+    return X
 
 
-# BF16x6 meets the 1e-6 budget; 3xTF32 accumulates its 8 chained products
-# (4 forward, 4 backward) into FP32 tensor memory with K-step truncation, and
-# its directional derivatives come out about 2e-6 off, so it is held to 3e-6.
+def _loss_diff(Sp, Sm, target):
+    """l(x + h v) - l(x - h v) for l = 0.5 ||S - target||^2, from the two
+    outputs: 0.5 sum (r+ - r-)(r+ + r-), free of the cancellation of
+    subtracting the two (large) losses."""
+    rp, rm = Sp - target, Sm - target
+    return 0.5 * float(np.sum((rp - rm) * (rp + rm)))
+
+
+# Directional derivatives are compared on their natural scale: for a random
+# direction v the derivative <g, v> is a normal variable of standard deviation
+# ||g|| ||v|| / sqrt(N), so a direction nearly orthogonal to g has a derivative
+# near zero, whose relative error grows without bound for any gradient with
+# rounding in it (the per-direction relative error is Cauchy-distributed).  The
+# error of every direction is therefore taken relative to the root mean square
+# of the FD derivatives of its argument over the 16 directions, an estimate of
+# that standard deviation computed from the FP64 loss alone.
+# BF16x6 meets the 1e-6 budget.  3xTF32 does not: it accumulates its 8
+# chained products (4 forward, 4 backward) into FP32 tensor memory with K-step
+# truncation; it is held to a larger bound, a documented shortfall (the
+# autograd default is BF16x6).
 FD_BOUND = {"bf16x6": 1e-6, "3xtf32": 3e-6}
+FD_DIRECTIONS = 16
 
 
 @pytest.mark.parametrize("prec", ["3xtf32", "bf16x6"])
 def test_adjoint_d4_n48_central_differences(kron, cfg_adjoint, prec):
     """<grad, v> of the split-precision adjoint against central differences of
-    the FP64 loss (h = 1e-6 relative); the loss is quadratic along v, so the
-    difference quotient is exact up to rounding."""
+    the FP64 loss (h = 1e-6 relative), for 16 random directions v per argument
+    (T and each L_mu); the loss is quadratic along v, so the difference
+    quotient is exact up to rounding."""
     import torch
     c, target, _, _ = cfg_adjoint
     T = to_dev(c.T, torch.float32).requires_grad_(True)
@@ -168,29 +182,40 @@ def test_adjoint_d4_n48_central_differences(kron, cfg_adjoint, prec):
     S = kron.tucker_autograd(T, Ls, prec=prec)
     loss = 0.5 * ((S - to_dev(target, torch.float32)) ** 2).sum()
     loss.backward()
+    gT = to_host(T.grad)
+    gL = [to_host(L.grad) for L in Ls]
     # the FD reference is evaluated on the same (FP32-rounded) inputs
     T32 = c.T.astype(np.float32).astype(np.float64)
     L32 = [L.astype(np.float32).astype(np.float64) for L in c.L]
     tg = target.astype(np.float32).astype(np.float64)
     g = np.random.default_rng(3)
-    V = np.asfortranarray(g.standard_normal(T32.shape))
-    h = 1e-6 * np.linalg.norm(T32) / np.linalg.norm(V)
-    fd = (_loss64(T32 + h * V, L32, tg) - _loss64(T32 - h * V, L32, tg)) / (2 * h)
-    an = float(np.sum(to_host(T.grad) * V))
     bound = FD_BOUND[prec]
-    print(f"adjoint FD {prec}: dT {abs(an - fd) / abs(fd):.2e}", end="")
-    assert abs(an - fd) <= bound * abs(fd), (an, fd)
-    for k in range(4):
-        V = np.asfortranarray(g.standard_normal(L32[k].shape))
-        h = 1e-6 * np.linalg.norm(L32[k]) / np.linalg.norm(V)
-        Lp = list(L32); Lm = list(L32)
-        Lp[k] = L32[k] + h * V
-        Lm[k] = L32[k] - h * V
-        fd = (_loss64(T32, Lp, tg) - _loss64(T32, Lm, tg)) / (2 * h)
-        an = float(np.sum(to_host(Ls[k].grad) * V))
-        print(f" dL{k} {abs(an - fd) / abs(fd):.2e}", end="")
-        assert abs(an - fd) <= bound * abs(fd), (k, an, fd)
-    print()
+    names = ["dT"] + [f"dL{k}" for k in range(4)]
+    report, failures = [], []
+    for arg in range(5):
+        base = T32 if arg == 0 else L32[arg - 1]
+        grad = gT if arg == 0 else gL[arg - 1]
+        fds, ans = [], []
+        for _ in range(FD_DIRECTIONS):
+            V = np.asfortranarray(g.standard_normal(base.shape))
+            h = 1e-6 * np.linalg.norm(base) / np.linalg.norm(V)
+            if arg == 0:
+                Sp, Sm = _tucker64(base + h * V, L32), _tucker64(base - h * V, L32)
+            else:
+                Lp, Lm = list(L32), list(L32)
+                Lp[arg - 1], Lm[arg - 1] = base + h * V, base - h * V
+                Sp, Sm = _tucker64(T32, Lp), _tucker64(T32, Lm)
+            fds.append(_loss_diff(Sp, Sm, tg) / (2 * h))
+            ans.append(float(np.sum(grad * V)))
+        fds, ans = np.array(fds), np.array(ans)
+        scale = float(np.sqrt(np.mean(fds ** 2)))
+        err = np.abs(ans - fds) / scale
+        report.append(f"{names[arg]} {err.max():.2e} (per direction {np.max(np.abs(ans - fds) / np.abs(fds)):.1e})")
+        if err.max() > bound:
+            failures.append((names[arg], float(err.max())))
+    print(f"adjoint FD {prec}, {FD_DIRECTIONS} directions per argument, worst error on the rms scale: " +
+          ", ".join(report))
+    assert not failures, failures
 
 
 @pytest.fixture(scope="module")
@@ -227,3 +252,59 @@ def test_batched_512_interpolation(kron, cfg_batched, prec):
     torch.cuda.synchronize()
     for a, b in zip(first, Ss[:8]):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("prec", ["3xtf32", "bf16x6"])
+def test_batched_512_cuda_graph_replay(kron, cfg_batched, prec):
+    """The bound batched run (counter reset, L splitting, one persistent
+    launch) captured in a CUDA graph: a replay gives the eager run's bits."""
+    import torch
+    c = cfg_batched
+    dev = torch.device("cuda")
+    Ts = [to_dev(t, torch.float32) for t in c.T]
+    Ls = [[to_dev(L, torch.float32) for L in row] for row in c.L]
+    Ss = [kron.empty_colmajor(tuple(int(v) for v in c.n[b]), torch.float32, dev) for b in range(len(Ts))]
+    plan = kron.BatchedPlan(c.m, c.n, torch.float32, prec)
+    ws = plan.workspace(dev)
+    plan.bind(Ts, Ls, Ss, ws)
+    plan.run(ws)
+    torch.cuda.synchronize()
+    eager = [s.clone() for s in Ss]
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(graph, stream=side):
+        plan.run(ws)
+    for s in Ss:
+        s.fill_(float("nan"))
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert kron.device_error() == 0
+    for a, b in zip(eager, Ss):
+        assert torch.equal(a, b)
+
+
+def test_tucker_batched_one_shot_matches_plan(kron, cfg_batched):
+    """kron_tucker_batched (plan, bind and run in one C call) against the
+    plan / bind / run route: the same job table, so the same bits; and
+    against the oracle."""
+    import torch
+    c = cfg_batched
+    sub = range(0, len(c.T), 8)  # 64 of the 512 problems
+    Ts = [to_dev(c.T[b], torch.float32) for b in sub]
+    Ls = [[to_dev(L, torch.float32) for L in c.L[b]] for b in sub]
+    Ss = kron.tucker_batched(Ts, Ls, prec="3xtf32")
+    m = np.asarray([c.m[b] for b in sub])
+    n = np.asarray([c.n[b] for b in sub])
+    dev = torch.device("cuda")
+    Sp = [kron.empty_colmajor(tuple(int(v) for v in n[i]), torch.float32, dev) for i in range(len(Ts))]
+    plan = kron.BatchedPlan(m, n, torch.float32, "3xtf32")
+    ws = plan.workspace(dev)
+    plan.bind(Ts, Ls, Sp, ws)
+    plan.run(ws)
+    torch.cuda.synchronize()
+    assert kron.device_error() == 0
+    for i, b in enumerate(sub):
+        assert torch.equal(Ss[i], Sp[i])
+        assert rel_err(to_host(Ss[i]), oracle.tucker(c.T[b], c.L[b])) <= TOL["3xtf32"]
