@@ -113,6 +113,7 @@ typedef enum kron_prec {
 /* Plan flags. */
 #define KRON_PLAN_TRANS_L 0x1u     /* use L_mu^T for every mode (cf. the paper's cttucker) */
 #define KRON_PLAN_NATURAL_ORDER 0x2u /* apply modes in order 1..d instead of the cost-minimising order */
+#define KRON_PLAN_UNFUSED 0x4u     /* split forms: every mode product its own launch (no fused groups) */
 
 typedef struct kron_plan_s *kron_plan;
 
@@ -195,6 +196,10 @@ KRON_API kron_status kron_mump_noalloc(int d, const int64_t *m, int mu, int64_t 
  * precision and the flags; it chooses the order in which the d mu-mode
  * products run (the result is independent of the order, Section 2) so as to
  * minimise the flop count, unless KRON_PLAN_NATURAL_ORDER is given.
+ * With the split forms, up to three small modes (m_mu, n_mu <= 32) applied one
+ * after the other on neighbouring indices mu, mu + 1, .. run as one fused
+ * launch that keeps the intermediates on chip (the first group's input must
+ * then be FP32); KRON_PLAN_UNFUSED runs every product as its own launch.
  */
 KRON_API kron_status kron_plan_create(kron_plan *plan, int d, const int64_t *m, const int64_t *n,
                              kron_dtype dtype, kron_prec prec, unsigned flags);

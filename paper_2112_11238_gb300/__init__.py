@@ -41,6 +41,7 @@ PREC = {"fp64": 0, "fp32": 1, "3xtf32": 2, "bf16x3": 3, "bf16x6": 4, "fx32": 5, 
 SPLIT_PRECS = ("3xtf32", "bf16x3", "bf16x6")
 PLAN_TRANS_L = 0x1
 PLAN_NATURAL_ORDER = 0x2
+PLAN_UNFUSED = 0x4
 MAX_D = 6
 
 _i64p = ctypes.POINTER(ctypes.c_int64)
@@ -268,14 +269,15 @@ class TuckerPlan:
     """A libkron plan: fixed d, sizes, dtype, precision and mode order."""
 
     def __init__(self, m, n, dtype=torch.float64, prec="fp64", trans: bool = False,
-                 natural_order: bool = False):
+                 natural_order: bool = False, fused: bool = True):
         self.m = [int(v) for v in m]
         self.n = [int(v) for v in n]
         self.d = len(self.m)
         self.dtype = dtype
         self.prec = prec
         self.trans = trans
-        flags = (PLAN_TRANS_L if trans else 0) | (PLAN_NATURAL_ORDER if natural_order else 0)
+        flags = ((PLAN_TRANS_L if trans else 0) | (PLAN_NATURAL_ORDER if natural_order else 0) |
+                 (0 if fused else PLAN_UNFUSED))
         h = ctypes.c_void_p()
         # complex plans take the dtype of the real and imaginary parts
         dt = F64 if dtype in (torch.float64, torch.complex128) else F32
@@ -418,12 +420,13 @@ class TuckerPlan:
 
 
 def tucker(T: torch.Tensor, Ls, prec="fp64", trans: bool = False, natural_order: bool = False,
-           stream=None) -> torch.Tensor:
-    """Tucker operator T x_1 op(L_1) x_2 ... x_d op(L_d) (Eq. (tuckerop))."""
+           fused: bool = True, stream=None) -> torch.Tensor:
+    """Tucker operator T x_1 op(L_1) x_2 ... x_d op(L_d) (Eq. (tuckerop)); fused=False
+    runs every mode product of the split forms as its own launch."""
     T = colmajor(T)
     Ls = [L.to(T.dtype) for L in Ls]
     n = [(L.shape[1] if trans else L.shape[0]) for L in Ls]
-    plan = TuckerPlan(T.shape, n, T.dtype, prec, trans, natural_order)
+    plan = TuckerPlan(T.shape, n, T.dtype, prec, trans, natural_order, fused)
     S = empty_colmajor(n, T.dtype, T.device)
     return plan.tucker_into(T, Ls, S, stream=stream)
 

@@ -196,11 +196,57 @@ kron_status run_chain(const kron_plan_s *pl, const void *T, const void *const *L
     for (int k = 0; k < d; ++k) cur[k] = pl->m[k];
     const void *src = T;
     bool src64 = io64;
+    int writes = 0;  // intermediates written so far (ping-pong buffers)
     for (int s = 0; s < d; ++s) {
         const int mu = pl->order[s];
         const ModeGeom g = mode_geom(d, cur, mu, pl->n[mu]);
+        // split forms: consecutive small modes mu, mu + 1, .. applied in a row
+        // run as one fused group with the intermediates on chip
+        int gsz = 0;
+        GroupSpec gs;
+        if (split && !src64 && !(pl->flags & KRON_PLAN_UNFUSED)) {
+            for (int gg = std::min(3, d - s); gg >= 1 && gsz == 0; --gg) {
+                bool ok = !(acc_last && s + gg == d);
+                for (int t = 0; t < gg && ok; ++t) ok = pl->order[s + t] == mu + t;
+                if (!ok) continue;
+                GroupSpec c;
+                c.g = gg;
+                c.P = prod(cur, 0, mu);
+                c.Q = prod(cur, mu + gg, d);
+                for (int t = 0; t < gg; ++t) {
+                    c.m[t] = cur[mu + t];
+                    c.n[t] = pl->n[mu + t];
+                    c.img[t] = ws + pl->img_off[mu + t];
+                }
+                if (tcg_fits(form, c)) {
+                    gsz = gg;
+                    gs = c;
+                }
+            }
+        }
+        if (gsz > 0) {
+            const bool last = (s + gsz == d);
+            void *dst = last ? S : (void *)(ws + pl->buf_off[writes & 1]);
+            const bool dst64 = last ? io64 : false;
+            for (int t = 0; t < gsz; ++t) {
+                const int nu = mu + t;
+                int64_t gc[KRON_MAX_D];
+                for (int k = 0; k < d; ++k) gc[k] = cur[k];
+                for (int k = 0; k < t; ++k) gc[mu + k] = pl->n[mu + k];
+                const ModeGeom gt = mode_geom(d, gc, nu, pl->n[nu]);
+                Contraction c = tc_mode_contraction(gt, nullptr, false, L[nu], io64, ldL[nu], trans, nullptr, false);
+                if (tc_build_bimage(form, c, ws + pl->img_off[nu], st) != cudaSuccess) return KRON_ERR_CUDA;
+            }
+            if (tcg_run(form, gs, static_cast<const float *>(src), dst, dst64, st) != cudaSuccess) return KRON_ERR_CUDA;
+            for (int t = 0; t < gsz; ++t) cur[mu + t] = pl->n[mu + t];
+            src = dst;
+            src64 = dst64;
+            ++writes;
+            s += gsz - 1;
+            continue;
+        }
         const bool last = (s == d - 1);
-        void *dst = last ? S : (void *)(ws + pl->buf_off[s & 1]);
+        void *dst = last ? S : (void *)(ws + pl->buf_off[writes & 1]);
         const bool dst64 = last ? io64 : (split ? false : i64);
         cudaError_t e;
         if (split) {
@@ -224,6 +270,7 @@ kron_status run_chain(const kron_plan_s *pl, const void *T, const void *const *L
         cur[mu] = pl->n[mu];
         src = dst;
         src64 = dst64;
+        ++writes;
     }
     return KRON_OK;
 }
@@ -396,7 +443,7 @@ kron_status kron_plan_create(kron_plan *plan, int d, const int64_t *m, const int
     if (!plan) return KRON_ERR_INVALID_ARG;
     *plan = nullptr;
     if (!valid_dtype(dtype) || !valid_prec(prec)) return KRON_ERR_INVALID_ARG;
-    if (flags & ~(KRON_PLAN_TRANS_L | KRON_PLAN_NATURAL_ORDER)) return KRON_ERR_INVALID_ARG;
+    if (flags & ~(KRON_PLAN_TRANS_L | KRON_PLAN_NATURAL_ORDER | KRON_PLAN_UNFUSED)) return KRON_ERR_INVALID_ARG;
     kron_status st = check_shape(d, m, n);
     if (st != KRON_OK) return st;
     auto *pl = new (std::nothrow) kron_plan_s();

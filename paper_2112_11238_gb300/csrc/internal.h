@@ -134,6 +134,19 @@ size_t tcp_jobs_table_bytes(const TcpJobs &jobs);
 // job plus one of device scratch (zeroed by the call).
 cudaError_t tcp_jobs_run(const TcpJobs &jobs, const void *table, int *done, cudaStream_t st);
 
+// ---- fused groups of small modes (tcg.cu) ----
+// Modes a .. a+g-1 (g <= 3) of a column-major tensor X[P, m_0, .., m_{g-1}, Q]
+// mapped to n_0 .. n_{g-1} in one launch, applied in that order; img[t]: the
+// image of op(L_t) made by tc_build_bimage.  Every m, n <= 32; the split forms.
+struct GroupSpec {
+    int g = 0;
+    int64_t P = 1, Q = 1;
+    int64_t m[3] = {1, 1, 1}, n[3] = {1, 1, 1};
+    const void *img[3] = {nullptr, nullptr, nullptr};
+};
+bool tcg_fits(int form, const GroupSpec &gs);
+cudaError_t tcg_run(int form, const GroupSpec &gs, const float *src, void *dst, bool dst64, cudaStream_t st);
+
 // ---- CUDA-core path (simt.cu) ----
 // FP64 (f64 = true) or FP32 fused multiply-add.
 cudaError_t simt_contract(bool f64, const Contraction &c, cudaStream_t st);

@@ -184,14 +184,16 @@ __device__ __forceinline__ void split_pack(const Tin (&v)[16 / FT<F>::ELEM], uin
 // d1 + 128, d2 + 128, d3 + 128 and y >> 24 = d0.  Each digit becomes a float
 // exactly through the 2^23 exponent trick (one OR, one FMA), and the high
 // halves of two floats are packed into one bf16x2 word with a byte permute.
-__device__ __forceinline__ void fx_pack(const int32_t (&v)[8], uint4 (&out)[4]) {
+// mul: a power of two the values are scaled by first (their left shift),
+// folded into the digit offset's addition as one multiply-add.
+__device__ __forceinline__ void fx_pack(const int32_t (&v)[8], uint4 (&out)[4], int mul = 1) {
     uint32_t w[4][4];
 #pragma unroll
     for (int e = 0; e < 8; e += 2) {
         float f[4][2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const long long y64 = (long long)v[e + h] + 0x808080ll;
+            const long long y64 = (long long)v[e + h] * mul + 0x808080ll;
             const uint32_t y = (uint32_t)y64;
             const int d0 = (int)(y64 >> 24);
             f[0][h] = __int_as_float(0x4B400000 + d0) - 12582912.0f;
@@ -215,14 +217,14 @@ __device__ __forceinline__ void fx_pack(const int32_t (&v)[8], uint4 (&out)[4]) 
 // d2 + 1024 in its 11-bit fields and y >> 22 = d0 (no overflow below 2^29);
 // each digit becomes a float exactly through the 2^23 exponent trick, and
 // pairs are rounded to f16x2, exact for these values.
-__device__ __forceinline__ void fx_pack3(const int32_t (&v)[8], uint4 (&out)[3]) {
+__device__ __forceinline__ void fx_pack3(const int32_t (&v)[8], uint4 (&out)[3], int mul = 1) {
     uint32_t w[3][4];
 #pragma unroll
     for (int e = 0; e < 8; e += 2) {
         float f[3][2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int y = v[e + h] + 0x200400;
+            const int y = v[e + h] * mul + 0x200400;
             f[0][h] = fmaf(__int_as_float(0x4B400000 + (y >> 22)), 256.0f, -3221225472.0f);
             f[1][h] = fmaf(__uint_as_float(0x4B000000u | (((uint32_t)y >> 11) & 0x7FFu)), 0.125f, -1048704.0f);
             f[2][h] = fmaf(__uint_as_float(0x4B000000u | ((uint32_t)y & 0x7FFu)), 6.103515625e-05f,
@@ -240,9 +242,9 @@ __device__ __forceinline__ void fx_pack3(const int32_t (&v)[8], uint4 (&out)[3])
 
 // Digits of the fixed-point form F.
 template <int F>
-__device__ __forceinline__ void fx_pack_f(const int32_t (&v)[8], uint4 (&out)[FT<F>::PIECES]) {
-    if constexpr (F == kFX32H) fx_pack3(v, out);
-    else fx_pack(v, out);
+__device__ __forceinline__ void fx_pack_f(const int32_t (&v)[8], uint4 (&out)[FT<F>::PIECES], int mul = 1) {
+    if constexpr (F == kFX32H) fx_pack3(v, out, mul);
+    else fx_pack(v, out, mul);
 }
 
 template <int F, typename Tin>

@@ -1,0 +1,477 @@
+// tcg.cu -- a group of up to three consecutive small mu-mode products fused
+// in one launch, the intermediates kept on chip (Definition "Tucker
+// operator", Eq. (tuckerop): the d products in sequence; the remark in
+// Section 2 that consecutive products need not go through memory in
+// between, there merging the permutations).
+//
+// The group applies modes a, a+1, ..., a+g-1 (g <= 3, every m, n <= 32) of a
+// column-major tensor whose modes before a have already been applied.  With
+// P = prod of the sizes before a and Q = prod of the sizes after the group,
+// the tensor is X[p, j_0, .., j_{g-1}, q]; a work unit is PB consecutive p
+// (PB a power of two; 1 when P = 1, so that a unit is one contiguous slab)
+// and one q.  Per unit, one CTA:
+//   1. loads X[p0 .. p0+PB-1, :, :, :, q] into an FP32 staging array in
+//      shared memory, one row per fibre of the first mode and the contracted
+//      index k along the row (odd pitch: conflict-free for any lane order);
+//   2. for each mode t of the group: splits the staged values into the
+//      form's pieces (3xTF32 / BF16x3 / BF16x6) in the K-major 64-byte-
+//      swizzled layout of the tcgen05 descriptors (up to four 128-row tiles);
+//      tile by tile, one thread issues the MMAs of the tile against the
+//      mode's op(L) image (kept in shared memory for the whole launch) into
+//      tensor memory (hi * hi apart from the cross products, as in the other
+//      kernels) while the next tile is converted; four groups of four warps,
+//      one tile each, read the accumulators back and write the outputs into
+//      the staging array as the rows of the next mode, or, after the last
+//      mode, to global memory;
+// so the group reads X and writes its output once.  Rows are ordered p
+// fastest, then the other local indices in increasing order, so the global
+// loads and stores run along p (or along the slab when P = 1).
+// Every wait is bounded; a CTA's decision to stop is taken by one thread and
+// shared through shared memory, so no thread is left at a barrier.
+#include <algorithm>
+#include <mutex>
+
+#include "tc_common.cuh"
+
+namespace kron {
+
+namespace {
+
+constexpr int kGThreads = 512;   // sixteen warps: four groups of one warp per tensor-memory lane quarter
+constexpr int kPitch = 33;       // staging row pitch in floats (odd)
+constexpr int kGMaxTiles = 4;    // rows per mode <= 512
+constexpr uint32_t kTile = kBM * kRowBytes;  // one piece of one K-block of a 128-row tile
+constexpr int kLoadDepth = 4;    // 16-byte input loads in flight per thread
+
+struct GLaunch {
+    const float *src;
+    void *dst;
+    int dst64;
+    int g;
+    int cur[3][3];      // cur[t][dim]: sizes of the local dims when mode t is applied
+    int K[3], N[3], BN[3], KB[3], rows[3], tiles[3];
+    const uint8_t *img[3];   // images of op(L_t) in global memory
+    uint32_t simg[3];        // their offsets in shared memory
+    uint32_t img_bytes[3];
+    int64_t P, Q;
+    int PB, lpb;
+    int64_t pblocks, units;
+    int64_t Gin, Gout;       // elements of one (p, q) slab before / after the group
+    uint32_t magic0;         // ceil(2^32 / cur[0][0])
+    uint32_t op_off, stage_off, bar_off;
+    int kbmax;
+    int vec4;                // groups of four input elements are 16-byte aligned
+};
+
+__device__ __forceinline__ void named_bar(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// The dims other than t, in increasing order (g <= 3): their indices.
+__device__ __forceinline__ void others(int g, int t, int &da, int &db) {
+    da = db = -1;
+    int c = 0;
+    for (int d = 0; d < g; ++d) {
+        if (d == t) continue;
+        if (c == 0) da = d;
+        else db = d;
+        ++c;
+    }
+}
+
+template <int F>
+__global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant__ GLaunch L) {
+    using T = FT<F>;
+    constexpr int CH = 16 / T::ELEM;     // values per 16-byte chunk
+    constexpr int BK = kRowBytes / T::ELEM;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *op = smem + L.op_off;
+    float *stage = reinterpret_cast<float *>(smem + L.stage_off);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar_off);  // one per tile
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + kGMaxTiles);
+    int *flag = reinterpret_cast<int *>(tslot + 1);
+    int *gflag = flag + 1;  // per tile: its MMAs completed
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        for (int i = 0; i < kGMaxTiles; ++i) {
+            mbar_init(smem_u32(&bar[i]), 1);
+            gflag[i] = 1;
+        }
+        fence_mbar_init();
+        *flag = 1;
+    }
+    if (warp == 0) {
+        tmem_alloc(smem_u32(tslot), 256);
+        tmem_relinquish();
+    }
+    // the images of op(L_t): small, loaded once (16-byte words)
+    for (int t = 0; t < L.g; ++t) {
+        const uint4 *s = reinterpret_cast<const uint4 *>(L.img[t]);
+        uint4 *d = reinterpret_cast<uint4 *>(smem + L.simg[t]);
+        for (uint32_t i = tid; i < L.img_bytes[t] / 16; i += kGThreads) d[i] = __ldg(s + i);
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    uint32_t phases = 0;  // bit i: parity of tile i's barrier
+
+    for (int64_t u = blockIdx.x; u < L.units; u += gridDim.x) {
+        const int64_t pblk = u % L.pblocks, q = u / L.pblocks;
+        const int64_t p0 = pblk * L.PB;
+        const int PB = L.PB;
+        const int64_t pvalid = min((int64_t)PB, L.P - p0);
+        // ---- 1. load the unit: element e = pb + PB * (j_0 + cur0 (j_1 + cur1 j_2)),
+        // in groups of four consecutive elements (four p of one fibre, or,
+        // for P = 1, four neighbours in the slab), 16-byte loads where the
+        // group is contiguous and aligned, kLoadDepth groups in flight per thread
+        {
+            const uint32_t E4 = (uint32_t)(((int64_t)PB * L.Gin + 3) / 4);
+            const float *src = L.src + p0 + L.P * L.Gin * q;
+            const uint32_t c0 = (uint32_t)L.cur[0][0];
+            const bool vec = L.vec4 != 0 && (PB == 1 || pvalid == PB);
+            for (uint32_t g0 = tid; g0 < E4; g0 += kLoadDepth * kGThreads) {
+                float v[kLoadDepth][4];
+#pragma unroll
+                for (int u = 0; u < kLoadDepth; ++u) {
+                    const uint32_t e = (g0 + u * kGThreads) * 4;
+                    if (g0 + u * kGThreads < E4) {
+                        if (PB == 1) {
+                            if (vec) {
+                                const float4 x = __ldg(reinterpret_cast<const float4 *>(src + e));
+                                v[u][0] = x.x; v[u][1] = x.y; v[u][2] = x.z; v[u][3] = x.w;
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < 4; ++i) v[u][i] = e + i < (uint32_t)L.Gin ? __ldg(src + e + i) : 0.f;
+                            }
+                        } else {
+                            const uint32_t rest = e >> L.lpb;
+                            const int pb = (int)(e & (uint32_t)(PB - 1));
+                            const float *a = src + pb + L.P * (int64_t)rest;
+                            if (vec) {
+                                const float4 x = __ldg(reinterpret_cast<const float4 *>(a));
+                                v[u][0] = x.x; v[u][1] = x.y; v[u][2] = x.z; v[u][3] = x.w;
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < 4; ++i) v[u][i] = pb + i < pvalid ? __ldg(a + i) : 0.f;
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kLoadDepth; ++u) {
+                    const uint32_t e = (g0 + u * kGThreads) * 4;
+                    if (g0 + u * kGThreads >= E4) continue;
+                    if (PB == 1) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const uint32_t rest = e + i;
+                            if (rest >= (uint32_t)L.Gin) continue;
+                            const uint32_t o = __umulhi(rest, L.magic0);  // rest / cur0
+                            stage[o * kPitch + (rest - o * c0)] = v[u][i];
+                        }
+                    } else {
+                        const uint32_t rest = e >> L.lpb;
+                        const int pb = (int)(e & (uint32_t)(PB - 1));
+                        const uint32_t o = __umulhi(rest, L.magic0);
+                        float *d = stage + (pb + PB * (int)o) * kPitch + (rest - o * c0);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) d[i * kPitch] = v[u][i];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        for (int t = 0; t < L.g; ++t) {
+            const int K = L.K[t], N = L.N[t], rows = L.rows[t], tiles = L.tiles[t];
+            const int kb_n = L.KB[t];
+            const uint32_t idesc = make_idesc(T::FMT, kBM, (uint32_t)L.BN[t]);
+            const uint32_t img = smem_u32(smem + L.simg[t]);
+            const uint32_t PIECE_B = (uint32_t)L.BN[t] * kRowBytes;
+            // ---- 2a/2b. tile by tile: staged rows -> pieces (K-major swizzled),
+            // then one thread issues that tile's MMAs (they run while the next
+            // tile is converted) and commits them to the tile's barrier
+            for (int tile = 0; tile < tiles; ++tile) {
+                const int items = kBM * 4 * kb_n;  // (row, 16-byte chunk) items of the tile
+                for (int it = tid; it < items; it += kGThreads) {
+                    const int r = it % kBM, ch = it / kBM;  // ch: chunk over kb_n K-blocks
+                    const int row = tile * kBM + r;
+                    const int k0 = ch * CH;
+                    float v[CH];
+#pragma unroll
+                    for (int e = 0; e < CH; ++e)
+                        v[e] = (row < rows && k0 + e < K) ? stage[row * kPitch + k0 + e] : 0.f;
+                    uint4 out[T::PIECES];
+                    split_pack<F, float>(v, out);
+                    uint8_t *base = op + ((size_t)(tile * L.kbmax + (ch >> 2)) * T::PIECES) * kTile;
+                    const uint32_t off = swz(r, ch & 3);
+#pragma unroll
+                    for (int p = 0; p < T::PIECES; ++p) *reinterpret_cast<uint4 *>(base + p * kTile + off) = out[p];
+                }
+                fence_proxy_async_smem();
+                __syncthreads();
+                if (tid == 0) {
+                    tc_fence_after();
+                    const uint32_t d = tmem + (uint32_t)(tile * 64);  // two regions of 32 columns
+                    for (int kb = 0; kb < kb_n; ++kb) {
+                        const int kval = min(BK, K - kb * BK);
+                        const int ksteps = (kval + T::MMA_K - 1) / T::MMA_K;
+                        const uint32_t a_base = smem_u32(op + ((size_t)(tile * L.kbmax + kb) * T::PIECES) * kTile);
+                        const uint32_t b_base = img + (uint32_t)(kb * T::PIECES) * PIECE_B;
+                        for (int ks = 0; ks < ksteps; ++ks) {
+#pragma unroll
+                            for (int pr = 0; pr < T::NPROD; ++pr) {
+                                int pa, pb;
+                                prod_pieces<F>(pr, pa, pb);
+                                const uint64_t ad = smem_desc_kmajor(a_base + pa * kTile + ks * 32, kRowBytes);
+                                const uint64_t bd = smem_desc_kmajor(b_base + pb * PIECE_B + ks * 32, kRowBytes);
+                                const bool first = kb == 0 && ks == 0 && first_in_region<F>(pr);
+                                tc_mma<T::KIND>(d + (uint32_t)region_of<F>(pr) * 32u, ad, bd, idesc, first ? 0u : 1u);
+                            }
+                        }
+                    }
+                    tc_commit(smem_u32(&bar[tile]));
+                }
+            }
+            // each group of four warps (one per lane quarter) takes one tile:
+            // its first thread waits for the tile's MMAs, the group follows
+            const int wg = warp >> 2;
+            if (wg < tiles) {
+                if ((tid & 127) == 0) gflag[wg] = mbar_wait(smem_u32(&bar[wg]), (phases >> wg) & 1u) ? 1 : 0;
+                named_bar(1 + wg, 128);
+            }
+            phases ^= (1u << tiles) - 1u;
+            const bool good = wg < tiles && gflag[wg] != 0;
+            // ---- 2c. epilogue: tensor memory -> next mode's staged rows or C
+            const bool last = (t == L.g - 1);
+            int da, db;
+            others(L.g, t, da, db);
+            const int qd = warp & 3;
+            if (good) {
+                const int tile = wg;
+                tc_fence_after();
+                uint32_t r0[32], r1[32];
+                const uint32_t ta = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(tile * 64);
+                tmem_ld32(ta, r0);
+                tmem_ld32(ta + 32u, r1);
+                tmem_ld_wait();
+                const int row = tile * kBM + qd * 32 + lane;
+                // decode the row: pb, then the dims other than t
+                const int pb = row & (PB - 1);
+                int o = row >> L.lpb;
+                int j[3] = {0, 0, 0};
+                if (da >= 0) {
+                    const int sa = L.cur[t][da];
+                    j[da] = o % sa;
+                    o /= sa;
+                }
+                if (db >= 0) j[db] = o;
+                if (row >= rows || pb >= pvalid) {
+                } else if (!last) {
+                    // next mode t + 1: rows over the dims other than t + 1
+                    // (sizes cur[t + 1]), k = j[t + 1]; linear in j[t] = c
+                    int na, nb;
+                    others(L.g, t + 1, na, nb);
+                    const int sa = L.cur[t + 1][na >= 0 ? na : 0];
+                    int r0i = pb, rc = 0;
+                    // flatten: j[na] + sa * j[nb]
+                    const int ja = (na == t) ? 0 : (na >= 0 ? j[na] : 0);
+                    const int jb = (nb == t) ? 0 : (nb >= 0 ? j[nb] : 0);
+                    r0i += PB * (ja + sa * jb);
+                    rc = PB * ((na == t) ? 1 : ((nb == t) ? sa : 0));
+                    float *dst = stage + r0i * kPitch + j[t + 1];
+                    const int step = rc * kPitch;
+#pragma unroll
+                    for (int c = 0; c < 32; ++c)
+                        if (c < N) dst[c * step] = __uint_as_float(r1[c]) + __uint_as_float(r0[c]);
+                } else {
+                    // C: p + P (j_0 + n_0 (j_1 + n_1 j_2) + Gout q), j[t] = c
+                    int64_t idx = 0, mult = 1, cs = 0;
+                    for (int d = 0; d < L.g; ++d) {
+                        if (d == t) cs = mult;
+                        else idx += mult * j[d];
+                        mult *= (d == t) ? N : L.cur[t][d];
+                    }
+                    const int64_t base = p0 + pb + L.P * (idx + L.Gout * q);
+                    const int64_t step = L.P * cs;
+                    if (L.dst64) {
+                        double *dst = static_cast<double *>(L.dst) + base;
+#pragma unroll
+                        for (int c = 0; c < 32; ++c)
+                            if (c < N) dst[c * step] = (double)(__uint_as_float(r1[c]) + __uint_as_float(r0[c]));
+                    } else {
+                        float *dst = static_cast<float *>(L.dst) + base;
+#pragma unroll
+                        for (int c = 0; c < 32; ++c)
+                            if (c < N) dst[c * step] = __uint_as_float(r1[c]) + __uint_as_float(r0[c]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+            // a tile whose wait ran out stops the CTA (decided the same way by
+            // every thread: the flags were written before the barrier)
+            for (int i = 0; i < tiles; ++i)
+                if (gflag[i] == 0) *flag = 0;
+            __syncthreads();
+            if (*flag == 0) break;
+        }
+        if (*flag == 0) break;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 256);
+    }
+}
+
+constexpr size_t kGSmemMax = 227 * 1024;
+
+}  // namespace
+
+static int g_pieces(int form) { return form == kBF16x6 ? 3 : 2; }
+static int g_bk(int form) { return form == kTF32x3 ? kRowBytes / 4 : kRowBytes / 2; }
+
+// Fills the launch for a group with p-blocks of at most pb_cap; false if it
+// does not fit (sizes, shared memory).
+static bool tcg_plan_pb(int form, const GroupSpec &gs, int pb_cap, GLaunch &L, size_t &smem) {
+    if (form != kTF32x3 && form != kBF16x3 && form != kBF16x6) return false;
+    if (gs.g < 1 || gs.g > 3 || gs.P < 1 || gs.Q < 1) return false;
+    L = GLaunch{};
+    L.g = gs.g;
+    int sz[3] = {1, 1, 1};
+    for (int t = 0; t < gs.g; ++t) {
+        if (gs.m[t] < 1 || gs.m[t] > 32 || gs.n[t] < 1 || gs.n[t] > 32) return false;
+        sz[t] = (int)gs.m[t];
+    }
+    const int bk = g_bk(form);
+    int64_t rows_max = 1;
+    for (int t = 0; t < gs.g; ++t) {
+        for (int d = 0; d < 3; ++d) L.cur[t][d] = d < gs.g ? sz[d] : 1;
+        int64_t r = 1;
+        for (int d = 0; d < gs.g; ++d)
+            if (d != t) r *= sz[d];
+        L.rows[t] = (int)r;  // times PB below
+        rows_max = std::max(rows_max, r);
+        L.K[t] = (int)gs.m[t];
+        L.N[t] = (int)gs.n[t];
+        L.BN[t] = tc_tile_n(form, gs.n[t]);
+        if (L.BN[t] > 32) return false;
+        L.KB[t] = (int)((gs.m[t] + bk - 1) / bk);
+        sz[t] = (int)gs.n[t];
+    }
+    // p-block: one slab when P = 1; else the largest power of two with at
+    // most 512 rows per mode (four tiles), at least 8 (32-byte runs) when P
+    // allows
+    // (at least 4 when P > 1: the loads take four consecutive p at a time)
+    int PB = 1;
+    if (gs.P > 1) {
+        PB = 4;
+        while (PB < pb_cap && (int64_t)PB * 2 * rows_max <= kGMaxTiles * kBM && PB * 2 <= gs.P) PB *= 2;
+        if (PB < 8 && gs.P >= 8) return false;
+    }
+    if ((int64_t)PB * rows_max > kGMaxTiles * kBM) return false;
+    L.PB = PB;
+    L.lpb = 0;
+    while ((1 << L.lpb) < PB) ++L.lpb;
+    int kbmax = 1, tiles_max = 1;
+    for (int t = 0; t < gs.g; ++t) {
+        L.rows[t] *= PB;
+        L.tiles[t] = (L.rows[t] + kBM - 1) / kBM;
+        tiles_max = std::max(tiles_max, L.tiles[t]);
+        kbmax = std::max(kbmax, L.KB[t]);
+    }
+    L.kbmax = kbmax;
+    L.P = gs.P;
+    L.Q = gs.Q;
+    L.pblocks = (gs.P + PB - 1) / PB;
+    L.units = L.pblocks * gs.Q;
+    L.Gin = 1;
+    L.Gout = 1;
+    for (int t = 0; t < gs.g; ++t) {
+        L.Gin *= gs.m[t];
+        L.Gout *= gs.n[t];
+    }
+    L.magic0 = (uint32_t)(((1ull << 32) + (uint64_t)gs.m[0] - 1) / (uint64_t)gs.m[0]);
+    // shared memory: operand tiles, staging, images, barrier + slots
+    size_t off = 0;
+    L.op_off = 0;
+    off += (size_t)tiles_max * kbmax * g_pieces(form) * kTile;
+    int64_t stage_rows = 0;
+    for (int t = 0; t < gs.g; ++t) stage_rows = std::max<int64_t>(stage_rows, L.rows[t]);
+    L.stage_off = (uint32_t)off;
+    off += ((size_t)stage_rows * kPitch * 4 + 1023) / 1024 * 1024;
+    for (int t = 0; t < gs.g; ++t) {
+        L.img[t] = static_cast<const uint8_t *>(gs.img[t]);
+        L.simg[t] = (uint32_t)off;
+        L.img_bytes[t] = (uint32_t)(L.KB[t] * g_pieces(form) * L.BN[t] * kRowBytes);
+        off += (L.img_bytes[t] + 1023) / 1024 * 1024;
+    }
+    L.bar_off = (uint32_t)off;
+    off += 64;
+    smem = off + 1024;  // alignment slack
+    return smem <= kGSmemMax;
+}
+
+// One CTA per SM (sixteen warps): the largest p-block that fits, so that a
+// unit has as many tiles (work between two waits) as possible.
+static bool tcg_plan(int form, const GroupSpec &gs, GLaunch &L, size_t &smem) {
+    for (int cap = 512; cap >= 8; cap /= 2) {
+        if (tcg_plan_pb(form, gs, cap, L, smem)) return true;
+        if (gs.P == 1) break;  // one slab per unit: nothing to shrink
+    }
+    return false;
+}
+
+bool tcg_fits(int form, const GroupSpec &gs) {
+    GLaunch L;
+    size_t smem = 0;
+    return tcg_plan(form, gs, L, smem);
+}
+
+template <int F>
+static cudaError_t tcg_launch_f(const GLaunch &L, size_t smem, cudaStream_t st) {
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [&] {
+        attr = cudaFuncSetAttribute(tcg_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGSmemMax);
+    });
+    if (attr != cudaSuccess) return attr;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // resident CTAs per SM (registers: one of sixteen warps; tensor memory:
+    // 256 columns each, so at most two)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tcg_kernel<F>, kGThreads, smem) != cudaSuccess)
+        per_sm = 1;
+    per_sm = std::max(1, std::min(per_sm, 2));
+    const int64_t grid = std::min<int64_t>(L.units, (int64_t)std::max(1, sms) * per_sm);
+    tcg_kernel<F><<<(unsigned)grid, kGThreads, smem, st>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t tcg_run(int form, const GroupSpec &gs, const float *src, void *dst, bool dst64, cudaStream_t st) {
+    GLaunch L;
+    size_t smem = 0;
+    if (!tcg_plan(form, gs, L, smem)) return cudaErrorInvalidValue;
+    if (L.units == 0) return cudaSuccess;
+    L.src = src;
+    L.dst = dst;
+    L.dst64 = dst64 ? 1 : 0;
+    // four consecutive elements of a group start 16-byte aligned: P = 1 with
+    // slabs of a multiple of four, or p-blocks (PB >= 4) with P a multiple of four
+    const bool base16 = (reinterpret_cast<uintptr_t>(src) & 15) == 0;
+    L.vec4 = base16 && ((L.P == 1 && L.Gin % 4 == 0) || (L.P > 1 && L.PB >= 4 && L.P % 4 == 0)) ? 1 : 0;
+    switch (form) {
+        case kTF32x3: return tcg_launch_f<kTF32x3>(L, smem, st);
+        case kBF16x3: return tcg_launch_f<kBF16x3>(L, smem, st);
+        case kBF16x6: return tcg_launch_f<kBF16x6>(L, smem, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace kron

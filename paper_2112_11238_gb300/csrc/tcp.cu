@@ -285,12 +285,12 @@ __device__ __forceinline__ void raw_issue(const TcJob &J, const int64_t (&base)[
 
 // Float sources: raw tiles arrive through cp.async several K-blocks ahead;
 // the converters split them from shared memory.
-// fsh: the left shift of a fixed-point A (fx_shift of its scale word).
+// fmul: 2^(left shift) of a fixed-point A (fx_shift of its scale word).
 template <int F, typename Join>
 __device__ __forceinline__ bool conv_tile_loop_raw(const TcJob &J, const CUtensorMap *tm, uint64_t *rfull,
                                                    uint32_t &rc, int mt, uint8_t *sA, uint32_t A_ST, uint8_t *sRaw,
                                                    uint64_t *full, uint64_t *empty, int S, uint32_t &g, int lane,
-                                                   int ct, int fsh, Join &&join) {
+                                                   int ct, int fmul, Join &&join) {
     using R = RawCfg<F>;
     constexpr int BK = R::BK;
     constexpr int CH = 16 / FT<F>::ELEM;
@@ -387,8 +387,8 @@ __device__ __forceinline__ bool conv_tile_loop_raw(const TcJob &J, const CUtenso
             if constexpr (is_fx_f<F>()) {
                 int32_t x[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) x[e] = (int32_t)(__float_as_uint(v[e]) << fsh);
-                fx_pack_f<F>(x, out);
+                for (int e = 0; e < 8; ++e) x[e] = __float_as_int(v[e]);
+                fx_pack_f<F>(x, out, fmul);
             } else {
                 split_pack<F, float>(v, out);
             }
@@ -928,13 +928,13 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
         bool ok = true;
         // fixed point: the left shift of the current job's A (its scale word
         // was written by an earlier launch), read once per job
-        int fsh = 0, fsh_job = -1;
+        int fmul = 1, fsh_job = -1;
         for (int t = blockIdx.x; t < L.total_tiles && ok; t += gridDim.x, ++it) {
             const int jt = find_job(L, t);
             const TcJob J = job_at(L, jt);
             if constexpr (is_fx_f<F>()) {
                 if (jt != fsh_job) {
-                    fsh = fx_shift<F>(J.fxA->maxabs);
+                    fmul = 1 << fx_shift<F>(J.fxA->maxabs);
                     fsh_job = jt;
                 }
             }
@@ -967,7 +967,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
                 named_bar(2, 32 * kConv);
             }
             if constexpr (is_fx_f<F>()) {  // always 32-bit integers
-                ok = conv_tile_loop_raw<F>(J, tm, rfull, rc, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct, fsh,
+                ok = conv_tile_loop_raw<F>(J, tm, rfull, rc, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct, fmul,
                                            epi_prev);
                 if (join) {
                     pend = t;
@@ -976,7 +976,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
             } else {
                 auto none = []() { return true; };
                 ok = J.a64 ? conv_tile_loop<F, double>(J, mt, sA, A_ST, full, empty, S, g, lane, ct)
-                           : conv_tile_loop_raw<F>(J, tm, rfull, rc, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct, 0,
+                           : conv_tile_loop_raw<F>(J, tm, rfull, rc, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct, 1,
                                                    none);
             }
         }

@@ -87,6 +87,35 @@ def test_tucker_matches_oracle(kron, m, n, prec):
     assert err <= tol(prec, sum(m)), (prec, m, n, err)
 
 
+# chains whose small modes run as fused groups (up to three neighbouring
+# modes with m, n <= 32 per launch, intermediates on chip): groups at the
+# start (contiguous slabs) and after larger modes (p-blocks with a ragged
+# tail), single small modes, n != m, sizes of 1
+FUSED_CASES = [
+    ((20, 20, 20), (20, 20, 20)), ((7, 9, 5, 11), (13, 4, 8, 3)), ((32, 1, 17), (5, 32, 2)),
+    ((40, 12, 13, 14), (40, 9, 30, 7)), ((3, 50, 6, 7, 8), (4, 50, 9, 2, 31)), ((5,) * 6, (6, 4, 7, 3, 5, 2)),
+    ((33, 31, 3), (29, 30, 31)), ((1, 1, 1), (32, 1, 16)), ((16, 16, 16, 16, 16), (16,) * 5),
+]
+
+
+@pytest.mark.parametrize("prec", ["3xtf32", "bf16x3", "bf16x6"])
+@pytest.mark.parametrize("m,n", FUSED_CASES)
+def test_fused_groups_match_oracle_and_unfused(kron, m, n, prec):
+    import torch
+    T = rnd(*m)
+    Ls = [rnd(n[k], m[k]) for k in range(len(m))]
+    ref = oracle.tucker(T, Ls)
+    Tf = to_dev(T, torch.float32)
+    Lf = [to_dev(L, torch.float32) for L in Ls]
+    S = kron.tucker(Tf, Lf, prec=prec, natural_order=True)
+    U = kron.tucker(Tf, Lf, prec=prec, natural_order=True, fused=False)
+    ref32 = oracle.tucker(to_host(Tf), [to_host(L) for L in Lf])
+    assert rel_err(to_host(S), ref32) <= TOL[prec], (prec, m, n, rel_err(to_host(S), ref32))
+    assert rel_err(to_host(U), ref32) <= TOL[prec]
+    assert rel_err(to_host(S), ref) <= max(TOL[prec], 1e-6)
+    assert kron.device_error() == 0
+
+
 KSV_SHAPES = [(7,), (37, 19), (9, 33, 17), (130, 5, 3), (20, 20, 20, 3), (3, 4, 5, 6, 7)]
 
 
