@@ -54,9 +54,11 @@ def test_single_rank_needs_no_process_group():
 
 
 def test_launch_count_of_the_fixed_point_stepper():
-    # expm (one launch), E images (2 per mode), U -> fixed point (2), 300 mode products
-    assert bench.launches_per_step("fx32") == 1 + 6 + 2 + 300
-    assert bench.launches_per_step("fx32h") == 1 + 6 + 2 + 300
+    # expm (one launch), E images at full and half tile width (rows + image
+    # each: 4 per mode), U -> fixed point (2), 300 mode products: the 315
+    # launches of the stepper's ncu launch list
+    assert bench.launches_per_step("fx32") == 1 + 12 + 2 + 300
+    assert bench.launches_per_step("fx32h") == 1 + 12 + 2 + 300
 
 
 def test_clock_summary_counts_only_the_timed_region():
