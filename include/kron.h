@@ -425,6 +425,27 @@ KRON_API kron_status kron_batched_run(kron_batched_plan plan, void *ws, size_t w
                              kron_stream_t stream);
 
 /*
+ * Autotuning of a bound plan (the paper has no counterpart; Section 3.2 and
+ * Section 4.3 give the workload).  Times candidate launch configurations of
+ * the persistent kernel on the bound operands -- N-tile width cap 32, 64 or
+ * 128 (64 at most for BF16X6), 2 pipeline stages or as many as fit, 1, 2 or
+ * as many accumulator sets per tile as tensor memory allows -- each on three
+ * runs after a warm-up, keeps the fastest for later kron_batched_run calls
+ * and re-binds the tables into the workspace.  The runs overwrite the bound
+ * outputs S.  If the environment variable KRON_AUTOTUNE_CACHE names a file,
+ * the choice is looked up there first, keyed by the GPU's name, d, batch, a
+ * hash of the shapes, dtype and precision (*from_cache = 1 and nothing is
+ * timed), and otherwise appended to it as one JSON object per line.  The
+ * tile width and the stage count do not change the arithmetic; the number of
+ * accumulator sets changes the order of the FP32 sums, so results may differ
+ * in the last bits.  Synchronises `stream` (it reads the timings).
+ * kron_batched_tuning reports the configuration in use (0: built-in rule).
+ */
+KRON_API kron_status kron_batched_autotune(kron_batched_plan plan, void *ws, size_t ws_bytes, kron_stream_t stream,
+                                           int *from_cache);
+KRON_API kron_status kron_batched_tuning(kron_batched_plan plan, int *bn_cap, int *stages, int *nacc);
+
+/*
  * One-shot form of the above (Section 3.2, Eq. (tensinterp)): plans, binds
  * and runs in one call, S[b] = T[b] x_1 L[b][0] ... x_d L[b][d-1] for every
  * problem b.  m, n: host arrays batch*d as for kron_batched_plan_create;

@@ -98,6 +98,8 @@ _sig("kron_batched_workspace_size", [_vp, ctypes.POINTER(_sz)])
 _sig("kron_batched_flops", [_vp], ctypes.c_double)
 _sig("kron_batched_bind", [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, _sz, _vp])
 _sig("kron_batched_run", [_vp, _vp, _sz, _vp])
+_sig("kron_batched_autotune", [_vp, _vp, _sz, _vp, ctypes.POINTER(_ci)])
+_sig("kron_batched_tuning", [_vp, ctypes.POINTER(_ci), ctypes.POINTER(_ci), ctypes.POINTER(_ci)])
 _sig("kron_tucker_batched_workspace_size", [_ci, _ci, _i64p, _i64p, _ci, _ci, ctypes.POINTER(_sz)])
 _sig("kron_tucker_batched", [_ci, _ci, _i64p, _i64p, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.POINTER(_vp)),
                              ctypes.POINTER(_vp), _ci, _ci, _vp, _sz, _vp])
@@ -113,7 +115,7 @@ EXPORTS = [
     "kron_expkronsum_workspace_size", "kron_expkronsum_step", "kron_expkronsum_apply",
     "kron_batched_plan_create", "kron_batched_plan_destroy", "kron_batched_workspace_size",
     "kron_batched_flops", "kron_batched_bind", "kron_batched_run",
-    "kron_tucker_batched_workspace_size", "kron_tucker_batched",
+    "kron_tucker_batched_workspace_size", "kron_tucker_batched", "kron_batched_autotune", "kron_batched_tuning",
 ]
 
 
@@ -685,6 +687,23 @@ class BatchedPlan:
 
     def run(self, ws, stream=None):
         _check(_lib.kron_batched_run(self._h, ws.data_ptr(), ws.numel(), _stream(stream)), "kron_batched_run")
+
+    def autotune(self, ws, stream=None) -> bool:
+        """Times candidate launch configurations on the bound operands (their
+        outputs are overwritten) and keeps the fastest; with
+        KRON_AUTOTUNE_CACHE set, reuses / records the choice there.  Returns
+        True when the choice came from the cache."""
+        hit = ctypes.c_int(0)
+        _check(_lib.kron_batched_autotune(self._h, ws.data_ptr(), ws.numel(), _stream(stream), ctypes.byref(hit)),
+               "kron_batched_autotune")
+        return bool(hit.value)
+
+    def tuning(self):
+        """(N-tile width cap, stages, accumulator sets); 0 = built-in rule."""
+        a, b, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(_lib.kron_batched_tuning(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "kron_batched_tuning")
+        return a.value, b.value, c.value
 
 
 def tucker_batched(Ts, Ls, prec="3xtf32", stream=None):

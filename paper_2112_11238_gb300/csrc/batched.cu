@@ -13,9 +13,13 @@
 // into its image, and the persistent kernel -- plus a memset of the job
 // counters, so a bound run can be captured in a CUDA graph.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include "tc_common.cuh"
@@ -103,6 +107,12 @@ struct kron_batched_plan_s {
     size_t pinned_bytes = 0;
     bool bound = false;
     void *bound_ws = nullptr;
+    // the bound operands (kept for re-binding under another configuration)
+    std::vector<const void *> bT, bL;
+    std::vector<void *> bS;
+    // launch configuration (0: the built-in rule): N-tile width cap,
+    // pipeline stages, accumulator sets per tile
+    int tune_bn = 0, tune_stages = 0, tune_nacc = 0;
 };
 
 namespace {
@@ -133,6 +143,9 @@ void problem_order(int d, const int64_t *m, const int64_t *n, int *order) {
 }
 
 int kb_of(int form) { return form == kTF32x3 ? kRowBytes / 4 : kRowBytes / 2; }
+
+// N-tile width caps the tuner tries (the built-in rule is the largest).
+constexpr int kTileCaps[] = {32, 64, 128};
 
 }  // namespace
 
@@ -187,12 +200,12 @@ kron_status batched_plan_init(kron_batched_plan *plan, int batch, int d, const i
             }
         }
         for (int k = 0; k < d; ++k) {
+            // room for the image at every N-tile width the tuner may pick
             pl->img_off[(size_t)b * d + k] = off;
-            off += al(tc_bimage_bytes(pl->form, nb[k], mb[k]));
-            const int bn = tc_tile_n(pl->form, nb[k]);
-            const int64_t nt = (nb[k] + bn - 1) / bn;
-            const int64_t kb = (mb[k] + kb_of(pl->form) - 1) / kb_of(pl->form);
-            pl->img_items += nt * kb * bn * kChunks;
+            size_t ib = 0;
+            for (int cap : kTileCaps)
+                ib = std::max(ib, tc_bimage_bytes_bn(pl->form, nb[k], mb[k], tc_tile_n_cap(pl->form, nb[k], cap)));
+            off += al(ib);
         }
     }
     // waves: groups of problems whose intermediates take about 32 MB
@@ -234,6 +247,8 @@ kron_status batched_plan_init(kron_batched_plan *plan, int batch, int d, const i
     *plan = pl;
     return KRON_OK;
 }
+
+kron_status batched_build(kron_batched_plan plan, void *ws, kron_stream_t stream);
 
 }  // namespace
 
@@ -279,6 +294,24 @@ kron_status kron_batched_bind(kron_batched_plan plan, const void *const *T, cons
             if (reinterpret_cast<uintptr_t>(l) % es) return KRON_ERR_ALIGNMENT;
         }
     }
+    plan->bT.assign(T, T + batch);
+    plan->bL.assign(L, L + (size_t)batch * d);
+    plan->bS.assign(S, S + batch);
+    return batched_build(plan, ws, stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Job tables of the bound operands under the plan's launch configuration,
+// uploaded into the workspace on `stream`.
+kron_status batched_build(kron_batched_plan plan, void *ws, kron_stream_t stream) {
+    const int d = plan->d, batch = plan->batch;
+    const void *const *L = plan->bL.data();
+    const void *const *T = plan->bT.data();
+    void *const *S = plan->bS.data();
+    const int cap = plan->tune_bn > 0 ? plan->tune_bn : (1 << 20);
     auto *w = static_cast<uint8_t *>(ws);
     const bool io64 = plan->dtype == KRON_F64;
     // image jobs
@@ -292,7 +325,7 @@ kron_status kron_batched_bind(kron_batched_plan plan, const void *const *T, cons
             J.K = plan->m[(size_t)b * d + k];
             J.ld = J.N;
             J.img = w + plan->img_off[(size_t)b * d + k];
-            J.BN = tc_tile_n(plan->form, J.N);
+            J.BN = tc_tile_n_cap(plan->form, J.N, cap);
             J.l64 = io64;
             const int64_t nt = (J.N + J.BN - 1) / J.BN;
             const int64_t kb = (J.K + kb_of(plan->form) - 1) / kb_of(plan->form);
@@ -300,8 +333,11 @@ kron_status kron_batched_bind(kron_batched_plan plan, const void *const *T, cons
             J.begin = begin;
             begin += J.items;
         }
+    plan->img_items = begin;
     // tensor-core jobs in launch order; job index of (b, s) for dependencies
     tcp_jobs_begin(plan->jobs, plan->form);
+    plan->jobs.stages = plan->tune_stages;
+    plan->jobs.nacc = plan->tune_nacc;
     std::vector<int> jid((size_t)batch * d, -1);
     for (const auto &bs : plan->seq) {
         const int b = bs.first, s = bs.second;
@@ -338,7 +374,8 @@ kron_status kron_batched_bind(kron_batched_plan plan, const void *const *T, cons
         c.C_f64 = dst64;
         c.colC = IdxMap{0, P, 0};
         const int dep = (s == 0) ? -1 : jid[(size_t)b * d + s - 1];
-        jid[(size_t)b * d + s] = tcp_jobs_add(plan->jobs, c, w + plan->img_off[(size_t)b * d + mu], dep);
+        jid[(size_t)b * d + s] = tcp_jobs_add(plan->jobs, c, w + plan->img_off[(size_t)b * d + mu], dep,
+                                              tc_tile_n_cap(plan->form, nn, cap));
     }
     // upload both tables: one copy from the pinned staging buffer, or (no
     // staging buffer) from pageable memory, which the copy has consumed when
@@ -363,6 +400,10 @@ kron_status kron_batched_bind(kron_batched_plan plan, const void *const *T, cons
     plan->bound_ws = ws;
     return KRON_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 kron_status kron_batched_run(kron_batched_plan plan, void *ws, size_t ws_bytes, kron_stream_t stream) {
     if (!plan || !ws) return KRON_ERR_INVALID_ARG;
@@ -418,6 +459,157 @@ kron_status kron_tucker_batched(int batch, int d, const int64_t *m, const int64_
     if (st == KRON_OK) st = kron_batched_run(pl, ws, ws_bytes, stream);
     delete pl;  // no staging buffer: nothing on the device refers to the plan
     return st;
+}
+
+// ------------------------------------------------------------- autotuning
+//
+// kron_batched_autotune times candidate launch configurations of a bound
+// plan -- the N-tile width cap (image layout and MMA width), the pipeline
+// stages and the accumulator sets per tile of the persistent kernel -- on
+// the bound operands, keeps the fastest, and records it in the file named by
+// KRON_AUTOTUNE_CACHE (one JSON object per line), keyed by the GPU's name and
+// the plan's shapes, dtype and precision; a later plan with the same key
+// takes the recorded choice without timing.
+
+}  // extern "C"
+
+namespace {
+
+uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull) {
+    const auto *b = static_cast<const uint8_t *>(p);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+std::string tune_key(const kron_batched_plan_s *pl) {
+    int dev = 0;
+    cudaDeviceProp prop{};
+    cudaGetDevice(&dev);
+    cudaGetDeviceProperties(&prop, dev);
+    std::string gpu(prop.name);
+    for (char &c : gpu)
+        if (c == '"' || c == '\\' || c == '|') c = '_';
+    uint64_t h = fnv1a(pl->m.data(), pl->m.size() * sizeof(int64_t));
+    h = fnv1a(pl->n.data(), pl->n.size() * sizeof(int64_t), h);
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "%s|d=%d|batch=%d|shapes=%016llx|dtype=%d|prec=%d", gpu.c_str(), pl->d, pl->batch,
+                  (unsigned long long)h, (int)pl->dtype, (int)pl->prec);
+    return std::string(buf);
+}
+
+std::mutex g_cache_mu;
+
+// The last record of `key` in the cache file.
+bool cache_lookup(const char *path, const std::string &key, int &bn, int &stages, int &nacc) {
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    const std::string tag = "\"key\": \"" + key + "\"";
+    char line[1024];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {
+        if (!std::strstr(line, tag.c_str())) continue;
+        int a = 0, b = 0, c = 0;
+        const char *p = std::strstr(line, "\"bn\":");
+        const char *q = std::strstr(line, "\"stages\":");
+        const char *r = std::strstr(line, "\"nacc\":");
+        if (p && q && r && std::sscanf(p, "\"bn\": %d", &a) == 1 && std::sscanf(q, "\"stages\": %d", &b) == 1 &&
+            std::sscanf(r, "\"nacc\": %d", &c) == 1) {
+            bn = a;
+            stages = b;
+            nacc = c;
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void cache_store(const char *path, const std::string &key, int bn, int stages, int nacc, float ms) {
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "{\"key\": \"%s\", \"bn\": %d, \"stages\": %d, \"nacc\": %d, \"ms\": %.6f}\n", key.c_str(), bn,
+                 stages, nacc, (double)ms);
+    std::fclose(f);
+}
+
+}  // namespace
+
+extern "C" {
+
+kron_status kron_batched_autotune(kron_batched_plan plan, void *ws, size_t ws_bytes, kron_stream_t stream,
+                                  int *from_cache) {
+    if (!plan || !ws) return KRON_ERR_INVALID_ARG;
+    if (!plan->bound || ws != plan->bound_ws) return KRON_ERR_INVALID_ARG;
+    if (ws_bytes < plan->ws_bytes) return KRON_ERR_WORKSPACE;
+    if (from_cache) *from_cache = 0;
+    const char *path = std::getenv("KRON_AUTOTUNE_CACHE");
+    const std::string key = tune_key(plan);
+    int bn = 0, stages = 0, nacc = 0;
+    if (path && *path && cache_lookup(path, key, bn, stages, nacc)) {
+        plan->tune_bn = bn;
+        plan->tune_stages = stages;
+        plan->tune_nacc = nacc;
+        if (from_cache) *from_cache = 1;
+        return batched_build(plan, ws, stream);
+    }
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess) return KRON_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return KRON_ERR_CUDA;
+    }
+    // candidates: every tile-width cap the form allows, stages 2 or as many
+    // as fit, one accumulator set, two, or as many as fit
+    const int caps_max = plan->form == kBF16x6 ? 64 : 128;
+    float best = -1.f;
+    int bb = 0, bs = 0, ba = 0;
+    kron_status st = KRON_OK;
+    for (int cap : kTileCaps) {
+        if (cap > caps_max || st != KRON_OK) continue;
+        for (int sg : {2, 0})
+            for (int na : {1, 2, 0}) {
+                if (st != KRON_OK) break;
+                plan->tune_bn = cap;
+                plan->tune_stages = sg;
+                plan->tune_nacc = na;
+                st = batched_build(plan, ws, stream);
+                if (st == KRON_OK) st = kron_batched_run(plan, ws, ws_bytes, stream);  // warm-up
+                if (st == KRON_OK && cudaEventRecord(e0, cs) != cudaSuccess) st = KRON_ERR_CUDA;
+                for (int r = 0; r < 3 && st == KRON_OK; ++r) st = kron_batched_run(plan, ws, ws_bytes, stream);
+                if (st == KRON_OK && cudaEventRecord(e1, cs) != cudaSuccess) st = KRON_ERR_CUDA;
+                float ms = 0.f;
+                if (st == KRON_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                    st = KRON_ERR_CUDA;
+                if (st == KRON_OK && (best < 0.f || ms < best)) {
+                    best = ms;
+                    bb = cap;
+                    bs = sg;
+                    ba = na;
+                }
+            }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != KRON_OK) return st;
+    plan->tune_bn = bb;
+    plan->tune_stages = bs;
+    plan->tune_nacc = ba;
+    if (path && *path) cache_store(path, key, bb, bs, ba, best / 3.f);
+    return batched_build(plan, ws, stream);
+}
+
+kron_status kron_batched_tuning(kron_batched_plan plan, int *bn_cap, int *stages, int *nacc) {
+    if (!plan || !bn_cap || !stages || !nacc) return KRON_ERR_INVALID_ARG;
+    *bn_cap = plan->tune_bn;
+    *stages = plan->tune_stages;
+    *nacc = plan->tune_nacc;
+    return KRON_OK;
 }
 
 }  // extern "C"

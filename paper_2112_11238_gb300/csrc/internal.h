@@ -71,8 +71,9 @@ struct FxScale {
 size_t tc_bimage_bytes(int form, int64_t N, int64_t K);
 // the same for an explicit N-tile width bn
 size_t tc_bimage_bytes_bn(int form, int64_t N, int64_t K, int bn);
-// N-tile width the tensor-core kernels use for a given N.
+// N-tile width the tensor-core kernels use for a given N (at most cap).
 int tc_tile_n(int form, int64_t N);
+int tc_tile_n_cap(int form, int64_t N, int cap);
 // Writes the image of B (given as a Contraction's B side: colB/kB maps over
 // N x K) into `img` (device, tc_bimage_bytes long).
 cudaError_t tc_build_bimage(int form, const Contraction &c, void *img, cudaStream_t st);
@@ -125,10 +126,14 @@ struct TcpJobs {
     int total_tiles = 0;
     int bn_max = 16;
     int nkb_max = 1;
+    // launch configuration chosen by a caller (0: the built-in rule):
+    // pipeline stages and accumulator sets per tile
+    int stages = 0, nacc = 0;
 };
 size_t tcp_job_bytes();
 void tcp_jobs_begin(TcpJobs &jobs, int form);
-int tcp_jobs_add(TcpJobs &jobs, const Contraction &c, const void *img, int dep);
+// bn: N-tile width of the job (that of its image; 0: tc_tile_n).
+int tcp_jobs_add(TcpJobs &jobs, const Contraction &c, const void *img, int dep, int bn = 0);
 size_t tcp_jobs_table_bytes(const TcpJobs &jobs);
 // `table`: device copy of jobs.host (needed above 8 jobs); `done`: one int per
 // job plus one of device scratch (zeroed by the call).

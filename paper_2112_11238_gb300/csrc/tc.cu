@@ -388,8 +388,10 @@ static int pieces_of(int form) { return form == kFX32 ? 4 : ((form == kBF16x6 ||
 static int bk_of(int form) { return form == kTF32x3 ? kRowBytes / 4 : kRowBytes / 2; }
 static int max_bn(int form) { return form == kBF16x6 ? 64 : (is_fx_form(form) ? 256 : 128); }
 
-int tc_tile_n(int form, int64_t N) {
-    const int64_t mx = max_bn(form);
+int tc_tile_n(int form, int64_t N) { return tc_tile_n_cap(form, N, 1 << 20); }
+
+int tc_tile_n_cap(int form, int64_t N, int cap) {
+    const int64_t mx = std::max<int64_t>(16, std::min<int64_t>(max_bn(form), cap));
     const int64_t nt = (N + mx - 1) / mx;
     int64_t bn = (N + nt - 1) / nt;
     bn = (bn + 15) / 16 * 16;

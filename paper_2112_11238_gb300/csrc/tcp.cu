@@ -1162,8 +1162,9 @@ static void setup_tmc(TcJob &J, const Contraction &c) {
 
 static constexpr size_t kSmemMax = 227 * 1024;
 
+// want_stages / want_nacc > 0: the caller's choice, clamped to what fits.
 static void pick_config(int form, int bn_max, int nkb_max, int &stages, int &nacc, int &nbuf, int &acc_cols,
-                        size_t &smem) {
+                        size_t &smem, int want_stages = 0, int want_nacc = 0) {
     acc_cols = bn_max <= 32 ? 32 : (bn_max <= 64 ? 64 : (bn_max <= 128 ? 128 : 256));
     // two accumulator buffers (epilogue overlapped) when tensor memory
     // allows, then more accumulator sets per tile (accuracy)
@@ -1171,6 +1172,7 @@ static void pick_config(int form, int bn_max, int nkb_max, int &stages, int &nac
     const int budget = std::max(1, 512 / (rg * acc_cols));  // NACC * NBUF
     nbuf = std::min(2, budget);
     nacc = std::max(1, std::min(4, budget / nbuf));
+    if (want_nacc > 0) nacc = std::min(nacc, want_nacc);
     // the fixed-point form keeps one exact accumulator set per tile
     if (nkb_max < 2 || is_fx_form(form)) nacc = 1;
     const size_t a_st = (size_t)pieces_of_f(form) * kBM * kRowBytes;
@@ -1188,6 +1190,7 @@ static void pick_config(int form, int bn_max, int nkb_max, int &stages, int &nac
     }
     stages = 1;
     while (stages < 8 && (size_t)(stages + 1) * (a_st + b_st) + raw + extra <= kSmemMax) ++stages;
+    if (want_stages > 0) stages = std::min(stages, want_stages);
     smem = (size_t)stages * (a_st + b_st) + raw + extra;
 }
 
@@ -1227,7 +1230,8 @@ static int num_sms() {
 // device copy of the jobs when there are more than kMaxInline of them;
 // `done` holds one int per job, zeroed here.
 static cudaError_t tcp_launch(int form, const TcJob *jobs, int njobs, int total_tiles, int bn_max, int nkb_max,
-                              const void *table, int *done, cudaStream_t st, FxScale *reset_next = nullptr) {
+                              const void *table, int *done, cudaStream_t st, FxScale *reset_next = nullptr,
+                              int want_stages = 0, int want_nacc = 0) {
     if (total_tiles <= 0) return cudaSuccess;
     TcLaunch L;
     std::memset(&L, 0, sizeof(L));
@@ -1240,7 +1244,7 @@ static cudaError_t tcp_launch(int form, const TcJob *jobs, int njobs, int total_
     else
         L.jobs = static_cast<const TcJob *>(table);
     size_t smem;
-    pick_config(form, bn_max, nkb_max, L.stages, L.nacc, L.nbuf, L.acc_cols, smem);
+    pick_config(form, bn_max, nkb_max, L.stages, L.nacc, L.nbuf, L.acc_cols, smem, want_stages, want_nacc);
     L.bn_max = bn_max;
     L.dep_hold = g_dep_hold.load();
     L.dep_wait_ns = g_dep_wait_ns.load();
@@ -1349,8 +1353,8 @@ void tcp_jobs_begin(TcpJobs &jobs, int form) {
     jobs.nkb_max = 1;
 }
 
-int tcp_jobs_add(TcpJobs &jobs, const Contraction &c, const void *img, int dep) {
-    TcJob J = make_job(jobs.form, c, img);
+int tcp_jobs_add(TcpJobs &jobs, const Contraction &c, const void *img, int dep, int bn) {
+    TcJob J = make_job(jobs.form, c, img, bn);
     J.tile_begin = jobs.total_tiles;
     J.dep = dep;
     if (dep >= 0) {
@@ -1372,7 +1376,7 @@ size_t tcp_jobs_table_bytes(const TcpJobs &jobs) { return jobs.host.size(); }
 cudaError_t tcp_jobs_run(const TcpJobs &jobs, const void *table, int *done, cudaStream_t st) {
     const int njobs = (int)(jobs.host.size() / sizeof(TcJob));
     return tcp_launch(jobs.form, reinterpret_cast<const TcJob *>(jobs.host.data()), njobs, jobs.total_tiles,
-                      jobs.bn_max, jobs.nkb_max, table, done, st);
+                      jobs.bn_max, jobs.nkb_max, table, done, st, nullptr, jobs.stages, jobs.nacc);
 }
 
 }  // namespace kron

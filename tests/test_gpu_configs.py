@@ -308,3 +308,62 @@ def test_tucker_batched_one_shot_matches_plan(kron, cfg_batched):
     for i, b in enumerate(sub):
         assert torch.equal(Ss[i], Sp[i])
         assert rel_err(to_host(Ss[i]), oracle.tucker(c.T[b], c.L[b])) <= TOL["3xtf32"]
+
+
+def test_batched_autotune_cache_and_bits(kron, cfg_batched, tmp_path, monkeypatch):
+    """The autotuner times its candidates on the 512 problems, records the
+    winner in KRON_AUTOTUNE_CACHE, and a second plan of the same shapes takes
+    it from there without timing.  Tile width and stage count leave the
+    arithmetic unchanged: every configuration with the same number of
+    accumulator sets gives the same bits."""
+    import torch
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("KRON_AUTOTUNE_CACHE", str(cache))
+    c = cfg_batched
+    dev = torch.device("cuda")
+    Ts = [to_dev(t, torch.float32) for t in c.T]
+    Ls = [[to_dev(L, torch.float32) for L in row] for row in c.L]
+    Ss = [kron.empty_colmajor(tuple(int(v) for v in c.n[b]), torch.float32, dev) for b in range(len(Ts))]
+    plan = kron.BatchedPlan(c.m, c.n, torch.float32, "3xtf32")
+    ws = plan.workspace(dev)
+    plan.bind(Ts, Ls, Ss, ws)
+    assert plan.autotune(ws) is False
+    chosen = plan.tuning()
+    assert chosen[0] in (32, 64, 128)
+    lines = cache.read_text().strip().splitlines()
+    assert len(lines) == 1 and '"bn": %d' % chosen[0] in lines[0]
+    plan.run(ws)
+    torch.cuda.synchronize()
+    assert kron.device_error() == 0
+    tuned = [s.clone() for s in Ss]
+    for b in range(0, len(Ts), 16):
+        assert rel_err(to_host(tuned[b]), oracle.tucker(c.T[b], c.L[b])) <= TOL["3xtf32"]
+    # the cache is hit by a new plan of the same shapes
+    plan2 = kron.BatchedPlan(c.m, c.n, torch.float32, "3xtf32")
+    ws2 = plan2.workspace(dev)
+    plan2.bind(Ts, Ls, Ss, ws2)
+    assert plan2.autotune(ws2) is True
+    assert plan2.tuning() == chosen
+    plan2.run(ws2)
+    torch.cuda.synchronize()
+    for a, b in zip(tuned, Ss):
+        assert torch.equal(a, b)
+    # one accumulator set, other tile widths and stage counts: same bits
+    # (configurations given to new plans through the cache file)
+    key = lines[0].split('"key": "')[1].split('"')[0]
+    ref_bits = None
+    for cap, stages in ((64, 2), (32, 0), (128, 0), (128, 2)):
+        cache.write_text('{"key": "%s", "bn": %d, "stages": %d, "nacc": 1, "ms": 0}\n' % (key, cap, stages))
+        plan3 = kron.BatchedPlan(c.m, c.n, torch.float32, "3xtf32")
+        ws3 = plan3.workspace(dev)
+        plan3.bind(Ts, Ls, Ss, ws3)
+        assert plan3.autotune(ws3) is True
+        assert plan3.tuning() == (cap, stages, 1)
+        plan3.run(ws3)
+        torch.cuda.synchronize()
+        if ref_bits is None:
+            ref_bits = [x.clone() for x in Ss]
+        else:
+            for a, b in zip(ref_bits, Ss):
+                assert torch.equal(a, b), (cap, stages)
+    assert kron.device_error() == 0
