@@ -79,24 +79,53 @@ __device__ __forceinline__ void others(int g, int t, int &da, int &db) {
     }
 }
 
+// Copies unit u of the group's input into the staging array with 4-byte
+// asynchronous copies (element e = pb + PB (j_0 + cur0 (j_1 + cur1 j_2))
+// goes to row pb + PB (j_1 + cur1 j_2), column j_0); threads t0, t0 + nt, ..
+// take part.  Padding p (past P) is not copied: its rows only feed outputs
+// that are never stored.
+__device__ __forceinline__ void load_unit(const GLaunch &L, int64_t u, float *stage, int t0, int nt) {
+    const int64_t pblk = u % L.pblocks, q = u / L.pblocks;
+    const int64_t p0 = pblk * L.PB;
+    const int PB = L.PB;
+    const int64_t pvalid = min((int64_t)PB, L.P - p0);
+    const uint32_t E = (uint32_t)((int64_t)PB * L.Gin);
+    const float *src = L.src + p0 + L.P * L.Gin * q;
+    const uint32_t c0 = (uint32_t)L.cur[0][0];
+    const uint32_t s0 = smem_u32(stage);
+    for (uint32_t e = t0; e < E; e += nt) {
+        const int pb = (int)(e & (uint32_t)(PB - 1));
+        const uint32_t rest = e >> L.lpb;
+        if (pb >= pvalid) continue;
+        const uint32_t o = __umulhi(rest, L.magic0);  // rest / cur0
+        const uint32_t srow = (uint32_t)pb + (uint32_t)PB * o;
+        cp_async4(s0 + (srow * kPitch + (rest - o * c0)) * 4u, src + pb + L.P * (int64_t)rest, 4u);
+    }
+    cp_async_commit();
+}
+
 template <int F>
 __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant__ GLaunch L) {
     using T = FT<F>;
     constexpr int CH = 16 / T::ELEM;     // values per 16-byte chunk
     constexpr int BK = kRowBytes / T::ELEM;
+    constexpr int kConvT = kGThreads - 32;  // converter threads (all warps but the last)
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *op = smem + L.op_off;
     float *stage = reinterpret_cast<float *>(smem + L.stage_off);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar_off);  // one per tile
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + kGMaxTiles);
+    uint64_t *bar_mma = reinterpret_cast<uint64_t *>(smem + L.bar_off);  // per tile: its MMAs completed
+    uint64_t *bar_conv = bar_mma + kGMaxTiles;                            // per tile: its operand is written
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_conv + kGMaxTiles);
     int *flag = reinterpret_cast<int *>(tslot + 1);
-    int *gflag = flag + 1;  // per tile: its MMAs completed
+    int *gflag = flag + 1;  // per tile: its waits ended in time
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool mma_warp = warp == kGThreads / 32 - 1;
 
     if (tid == 0) {
         for (int i = 0; i < kGMaxTiles; ++i) {
-            mbar_init(smem_u32(&bar[i]), 1);
+            mbar_init(smem_u32(&bar_mma[i]), 1);
+            mbar_init(smem_u32(&bar_conv[i]), kConvT / 32);
             gflag[i] = 1;
         }
         fence_mbar_init();
@@ -117,136 +146,100 @@ __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    uint32_t phases = 0;  // bit i: parity of tile i's barrier
+    uint32_t phases = 0;  // bit i: parity of tile i's two barriers
+    if (blockIdx.x < L.units) load_unit(L, blockIdx.x, stage, tid, kGThreads);
 
     for (int64_t u = blockIdx.x; u < L.units; u += gridDim.x) {
         const int64_t pblk = u % L.pblocks, q = u / L.pblocks;
         const int64_t p0 = pblk * L.PB;
         const int PB = L.PB;
         const int64_t pvalid = min((int64_t)PB, L.P - p0);
-        // ---- 1. load the unit: element e = pb + PB * (j_0 + cur0 (j_1 + cur1 j_2)),
-        // in groups of four consecutive elements (four p of one fibre, or,
-        // for P = 1, four neighbours in the slab), 16-byte loads where the
-        // group is contiguous and aligned, kLoadDepth groups in flight per thread
-        {
-            const uint32_t E4 = (uint32_t)(((int64_t)PB * L.Gin + 3) / 4);
-            const float *src = L.src + p0 + L.P * L.Gin * q;
-            const uint32_t c0 = (uint32_t)L.cur[0][0];
-            const bool vec = L.vec4 != 0 && (PB == 1 || pvalid == PB);
-            for (uint32_t g0 = tid; g0 < E4; g0 += kLoadDepth * kGThreads) {
-                float v[kLoadDepth][4];
-#pragma unroll
-                for (int u = 0; u < kLoadDepth; ++u) {
-                    const uint32_t e = (g0 + u * kGThreads) * 4;
-                    if (g0 + u * kGThreads < E4) {
-                        if (PB == 1) {
-                            if (vec) {
-                                const float4 x = __ldg(reinterpret_cast<const float4 *>(src + e));
-                                v[u][0] = x.x; v[u][1] = x.y; v[u][2] = x.z; v[u][3] = x.w;
-                            } else {
-#pragma unroll
-                                for (int i = 0; i < 4; ++i) v[u][i] = e + i < (uint32_t)L.Gin ? __ldg(src + e + i) : 0.f;
-                            }
-                        } else {
-                            const uint32_t rest = e >> L.lpb;
-                            const int pb = (int)(e & (uint32_t)(PB - 1));
-                            const float *a = src + pb + L.P * (int64_t)rest;
-                            if (vec) {
-                                const float4 x = __ldg(reinterpret_cast<const float4 *>(a));
-                                v[u][0] = x.x; v[u][1] = x.y; v[u][2] = x.z; v[u][3] = x.w;
-                            } else {
-#pragma unroll
-                                for (int i = 0; i < 4; ++i) v[u][i] = pb + i < pvalid ? __ldg(a + i) : 0.f;
-                            }
-                        }
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < kLoadDepth; ++u) {
-                    const uint32_t e = (g0 + u * kGThreads) * 4;
-                    if (g0 + u * kGThreads >= E4) continue;
-                    if (PB == 1) {
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const uint32_t rest = e + i;
-                            if (rest >= (uint32_t)L.Gin) continue;
-                            const uint32_t o = __umulhi(rest, L.magic0);  // rest / cur0
-                            stage[o * kPitch + (rest - o * c0)] = v[u][i];
-                        }
-                    } else {
-                        const uint32_t rest = e >> L.lpb;
-                        const int pb = (int)(e & (uint32_t)(PB - 1));
-                        const uint32_t o = __umulhi(rest, L.magic0);
-                        float *d = stage + (pb + PB * (int)o) * kPitch + (rest - o * c0);
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) d[i * kPitch] = v[u][i];
-                    }
-                }
-            }
-        }
+        // ---- 1. the unit's input (copies issued during the previous unit)
+        cp_async_wait<0>();
         __syncthreads();
         for (int t = 0; t < L.g; ++t) {
             const int K = L.K[t], N = L.N[t], rows = L.rows[t], tiles = L.tiles[t];
             const int kb_n = L.KB[t];
-            const uint32_t idesc = make_idesc(T::FMT, kBM, (uint32_t)L.BN[t]);
-            const uint32_t img = smem_u32(smem + L.simg[t]);
-            const uint32_t PIECE_B = (uint32_t)L.BN[t] * kRowBytes;
-            // ---- 2a/2b. tile by tile: staged rows -> pieces (K-major swizzled),
-            // then one thread issues that tile's MMAs (they run while the next
-            // tile is converted) and commits them to the tile's barrier
-            for (int tile = 0; tile < tiles; ++tile) {
-                const int items = kBM * 4 * kb_n;  // (row, 16-byte chunk) items of the tile
-                for (int it = tid; it < items; it += kGThreads) {
-                    const int r = it % kBM, ch = it / kBM;  // ch: chunk over kb_n K-blocks
-                    const int row = tile * kBM + r;
-                    const int k0 = ch * CH;
-                    float v[CH];
+            const bool last = (t == L.g - 1);
+            // ---- 2a. converters, tile by tile: staged rows -> pieces in the
+            // K-major swizzled layout; each warp signals the tile's barrier.
+            // Chunks past the last K-step of the MMAs are never read.
+            if (!mma_warp) {
+                const int kread = (K + T::MMA_K - 1) / T::MMA_K * T::MMA_K;
+                const int nch = (kread + CH - 1) / CH;  // chunks read by the MMAs
+                for (int tile = 0; tile < tiles; ++tile) {
+                    const int items = kBM * nch;
+                    for (int it = tid; it < items; it += kConvT) {
+                        const int r = it % kBM, ch = it / kBM;
+                        const int row = tile * kBM + r;
+                        const int k0 = ch * CH;
+                        float v[CH];
 #pragma unroll
-                    for (int e = 0; e < CH; ++e)
-                        v[e] = (row < rows && k0 + e < K) ? stage[row * kPitch + k0 + e] : 0.f;
-                    uint4 out[T::PIECES];
-                    split_pack<F, float>(v, out);
-                    uint8_t *base = op + ((size_t)(tile * L.kbmax + (ch >> 2)) * T::PIECES) * kTile;
-                    const uint32_t off = swz(r, ch & 3);
+                        for (int e = 0; e < CH; ++e)
+                            v[e] = (row < rows && k0 + e < K) ? stage[row * kPitch + k0 + e] : 0.f;
+                        uint4 out[T::PIECES];
+                        split_pack<F, float>(v, out);
+                        uint8_t *base = op + ((size_t)(tile * L.kbmax + (ch >> 2)) * T::PIECES) * kTile;
+                        const uint32_t off = swz(r, ch & 3);
 #pragma unroll
-                    for (int p = 0; p < T::PIECES; ++p) *reinterpret_cast<uint4 *>(base + p * kTile + off) = out[p];
+                        for (int p = 0; p < T::PIECES; ++p) *reinterpret_cast<uint4 *>(base + p * kTile + off) = out[p];
+                    }
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&bar_conv[tile]));
                 }
-                fence_proxy_async_smem();
-                __syncthreads();
-                if (tid == 0) {
+                // every converter has read the stage: the epilogue may write
+                // the next mode's rows there, or, after the last mode, the
+                // next unit's input may go there while this unit finishes
+                named_bar(5, kConvT);
+                if (last && u + gridDim.x < L.units) load_unit(L, u + gridDim.x, stage, tid, kConvT);
+            } else if (lane == 0) {
+                // ---- 2b. the MMAs of each tile as soon as it is converted
+                const uint32_t idesc = make_idesc(T::FMT, kBM, (uint32_t)L.BN[t]);
+                const uint32_t img = smem_u32(smem + L.simg[t]);
+                const uint32_t PIECE_B = (uint32_t)L.BN[t] * kRowBytes;
+                const uint64_t adesc0 = smem_desc_kmajor(smem_u32(op), kRowBytes);
+                const uint64_t bdesc0 = smem_desc_kmajor(img, kRowBytes);
+                for (int tile = 0; tile < tiles; ++tile) {
+                    if (!mbar_wait(smem_u32(&bar_conv[tile]), (phases >> tile) & 1u)) {
+                        gflag[tile] = 0;
+                        continue;  // its MMA barrier never completes: the tile's group times out too
+                    }
                     tc_fence_after();
                     const uint32_t d = tmem + (uint32_t)(tile * 64);  // two regions of 32 columns
                     for (int kb = 0; kb < kb_n; ++kb) {
                         const int kval = min(BK, K - kb * BK);
                         const int ksteps = (kval + T::MMA_K - 1) / T::MMA_K;
-                        const uint32_t a_base = smem_u32(op + ((size_t)(tile * L.kbmax + kb) * T::PIECES) * kTile);
-                        const uint32_t b_base = img + (uint32_t)(kb * T::PIECES) * PIECE_B;
+                        // descriptor address fields advance by bytes / 16
+                        const uint32_t a_off = (uint32_t)((tile * L.kbmax + kb) * T::PIECES) * kTile;
+                        const uint32_t b_off = (uint32_t)(kb * T::PIECES) * PIECE_B;
                         for (int ks = 0; ks < ksteps; ++ks) {
 #pragma unroll
                             for (int pr = 0; pr < T::NPROD; ++pr) {
                                 int pa, pb;
                                 prod_pieces<F>(pr, pa, pb);
-                                const uint64_t ad = smem_desc_kmajor(a_base + pa * kTile + ks * 32, kRowBytes);
-                                const uint64_t bd = smem_desc_kmajor(b_base + pb * PIECE_B + ks * 32, kRowBytes);
+                                const uint64_t ad = adesc0 + ((a_off + pa * kTile + ks * 32) >> 4);
+                                const uint64_t bd = bdesc0 + ((b_off + pb * PIECE_B + ks * 32) >> 4);
                                 const bool first = kb == 0 && ks == 0 && first_in_region<F>(pr);
                                 tc_mma<T::KIND>(d + (uint32_t)region_of<F>(pr) * 32u, ad, bd, idesc, first ? 0u : 1u);
                             }
                         }
                     }
-                    tc_commit(smem_u32(&bar[tile]));
+                    tc_commit(smem_u32(&bar_mma[tile]));
                 }
             }
-            // each group of four warps (one per lane quarter) takes one tile:
-            // its first thread waits for the tile's MMAs, the group follows
+            __syncwarp();  // the issuing lane rejoins its warp
+            // ---- 2c. epilogue: each group of four warps (one per lane
+            // quarter) takes one tile; its first thread waits for the tile's
+            // MMAs, the group follows
             const int wg = warp >> 2;
             if (wg < tiles) {
-                if ((tid & 127) == 0) gflag[wg] = mbar_wait(smem_u32(&bar[wg]), (phases >> wg) & 1u) ? 1 : 0;
+                if ((tid & 127) == 0 && !mbar_wait(smem_u32(&bar_mma[wg]), (phases >> wg) & 1u)) gflag[wg] = 0;
+                __syncwarp();
                 named_bar(1 + wg, 128);
             }
             phases ^= (1u << tiles) - 1u;
             const bool good = wg < tiles && gflag[wg] != 0;
-            // ---- 2c. epilogue: tensor memory -> next mode's staged rows or C
-            const bool last = (t == L.g - 1);
             int da, db;
             others(L.g, t, da, db);
             const int qd = warp & 3;
@@ -276,12 +269,11 @@ __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant
                     int na, nb;
                     others(L.g, t + 1, na, nb);
                     const int sa = L.cur[t + 1][na >= 0 ? na : 0];
-                    int r0i = pb, rc = 0;
                     // flatten: j[na] + sa * j[nb]
                     const int ja = (na == t) ? 0 : (na >= 0 ? j[na] : 0);
                     const int jb = (nb == t) ? 0 : (nb >= 0 ? j[nb] : 0);
-                    r0i += PB * (ja + sa * jb);
-                    rc = PB * ((na == t) ? 1 : ((nb == t) ? sa : 0));
+                    const int r0i = pb + PB * (ja + sa * jb);
+                    const int rc = PB * ((na == t) ? 1 : ((nb == t) ? sa : 0));
                     float *dst = stage + r0i * kPitch + j[t + 1];
                     const int step = rc * kPitch;
 #pragma unroll
@@ -321,6 +313,7 @@ __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant
         }
         if (*flag == 0) break;
     }
+    cp_async_wait<0>();
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -412,7 +405,7 @@ static bool tcg_plan_pb(int form, const GroupSpec &gs, int pb_cap, GLaunch &L, s
         off += (L.img_bytes[t] + 1023) / 1024 * 1024;
     }
     L.bar_off = (uint32_t)off;
-    off += 64;
+    off += 128;  // two barriers per tile, tensor-memory slot, flags
     smem = off + 1024;  // alignment slack
     return smem <= kGSmemMax;
 }
