@@ -96,6 +96,8 @@ struct kron_batched_plan_s {
     std::vector<size_t> buf_off;        // batch * (d - 1) intermediates
     size_t imgjob_off = 0, imgjob_bytes = 0;
     size_t table_off = 0, table_bytes = 0;
+    size_t tilejob_off = 0, tilejob_bytes = 0;
+    int64_t tiles_max = 0;
     size_t done_off = 0, done_bytes = 0;
     size_t ws_bytes = 0;
     double flops = 0;
@@ -190,6 +192,8 @@ kron_status batched_plan_init(kron_batched_plan *plan, int batch, int d, const i
         for (int k = 0; k < d; ++k) cur[k] = mb[k];
         for (int s = 0; s < d; ++s) {
             const int mu = pl->order[(size_t)b * d + s];
+            // tiles of this mode at the narrowest tile width (16)
+            pl->tiles_max += ((prodv(cur, d) / cur[mu] + 127) / 128) * ((nb[mu] + 15) / 16);
             pl->flops += 2.0 * (double)nb[mu] * (double)prodv(cur, d);
             cur[mu] = nb[mu];
             if (s < d - 1) {
@@ -235,11 +239,15 @@ kron_status batched_plan_init(kron_batched_plan *plan, int batch, int d, const i
     pl->table_off = off;
     pl->table_bytes = al(tcp_job_bytes() * njobs);
     off += pl->table_bytes;
+    // the job of every tile, right after the job table (one upload for both)
+    pl->tilejob_off = off;
+    pl->tilejob_bytes = al(sizeof(int) * (size_t)pl->tiles_max);
+    off += pl->tilejob_bytes;
     pl->done_off = off;
     pl->done_bytes = al(sizeof(int) * (njobs + 1));  // + the launch's "a wait gave up" flag
     off += pl->done_bytes;
     pl->ws_bytes = off;
-    pl->pinned_bytes = pl->imgjob_bytes + pl->table_bytes;
+    pl->pinned_bytes = pl->imgjob_bytes + pl->table_bytes + pl->tilejob_bytes;
     if (with_pinned && cudaMallocHost(reinterpret_cast<void **>(&pl->pinned), pl->pinned_bytes) != cudaSuccess) {
         delete pl;
         return KRON_ERR_CUDA;
@@ -377,6 +385,7 @@ kron_status batched_build(kron_batched_plan plan, void *ws, kron_stream_t stream
         jid[(size_t)b * d + s] = tcp_jobs_add(plan->jobs, c, w + plan->img_off[(size_t)b * d + mu], dep,
                                               tc_tile_n_cap(plan->form, nn, cap));
     }
+    if ((int64_t)plan->jobs.tile_job.size() > plan->tiles_max) return KRON_ERR_INVALID_ARG;  // not reached
     // upload both tables: one copy from the pinned staging buffer, or (no
     // staging buffer) from pageable memory, which the copy has consumed when
     // cudaMemcpyAsync returns
@@ -385,13 +394,17 @@ kron_status batched_build(kron_batched_plan plan, void *ws, kron_stream_t stream
         if (cudaStreamSynchronize(cs) != cudaSuccess) return KRON_ERR_CUDA;  // staging buffer reuse
         std::memcpy(plan->pinned, plan->imgjobs.data(), sizeof(ImgJob) * plan->imgjobs.size());
         std::memcpy(plan->pinned + plan->imgjob_bytes, plan->jobs.host.data(), plan->jobs.host.size());
-        if (cudaMemcpyAsync(w + plan->imgjob_off, plan->pinned, plan->imgjob_bytes + plan->table_bytes,
-                            cudaMemcpyHostToDevice, cs) != cudaSuccess)
+        std::memcpy(plan->pinned + plan->imgjob_bytes + plan->table_bytes, plan->jobs.tile_job.data(),
+                    sizeof(int) * plan->jobs.tile_job.size());
+        if (cudaMemcpyAsync(w + plan->imgjob_off, plan->pinned, plan->pinned_bytes, cudaMemcpyHostToDevice, cs) !=
+            cudaSuccess)
             return KRON_ERR_CUDA;
     } else {
-        std::vector<uint8_t> stage(plan->imgjob_bytes + plan->table_bytes, 0);
+        std::vector<uint8_t> stage(plan->imgjob_bytes + plan->table_bytes + plan->tilejob_bytes, 0);
         std::memcpy(stage.data(), plan->imgjobs.data(), sizeof(ImgJob) * plan->imgjobs.size());
         std::memcpy(stage.data() + plan->imgjob_bytes, plan->jobs.host.data(), plan->jobs.host.size());
+        std::memcpy(stage.data() + plan->imgjob_bytes + plan->table_bytes, plan->jobs.tile_job.data(),
+                    sizeof(int) * plan->jobs.tile_job.size());
         if (cudaMemcpyAsync(w + plan->imgjob_off, stage.data(), stage.size(), cudaMemcpyHostToDevice, cs) !=
             cudaSuccess)
             return KRON_ERR_CUDA;
@@ -423,7 +436,8 @@ kron_status kron_batched_run(kron_batched_plan plan, void *ws, size_t ws_bytes, 
         default: return KRON_ERR_UNSUPPORTED;
     }
     if (cudaGetLastError() != cudaSuccess) return KRON_ERR_CUDA;
-    if (tcp_jobs_run(plan->jobs, w + plan->table_off, reinterpret_cast<int *>(w + plan->done_off), cs) != cudaSuccess)
+    if (tcp_jobs_run(plan->jobs, w + plan->table_off, reinterpret_cast<int *>(w + plan->done_off), cs,
+                     reinterpret_cast<const int *>(w + plan->tilejob_off)) != cudaSuccess)
         return KRON_ERR_CUDA;
     return KRON_OK;
 }

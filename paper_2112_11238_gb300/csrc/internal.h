@@ -129,15 +129,18 @@ struct TcpJobs {
     // launch configuration chosen by a caller (0: the built-in rule):
     // pipeline stages and accumulator sets per tile
     int stages = 0, nacc = 0;
+    std::vector<int> tile_job;  // job of every tile (uploaded for tables above 8 jobs)
 };
 size_t tcp_job_bytes();
 void tcp_jobs_begin(TcpJobs &jobs, int form);
 // bn: N-tile width of the job (that of its image; 0: tc_tile_n).
 int tcp_jobs_add(TcpJobs &jobs, const Contraction &c, const void *img, int dep, int bn = 0);
 size_t tcp_jobs_table_bytes(const TcpJobs &jobs);
-// `table`: device copy of jobs.host (needed above 8 jobs); `done`: one int per
-// job plus one of device scratch (zeroed by the call).
-cudaError_t tcp_jobs_run(const TcpJobs &jobs, const void *table, int *done, cudaStream_t st);
+// `table`: device copy of jobs.host and `tile_job` of jobs.tile_job (both
+// needed above 8 jobs); `done`: one int per job plus one of device scratch
+// (zeroed by the call).
+cudaError_t tcp_jobs_run(const TcpJobs &jobs, const void *table, int *done, cudaStream_t st,
+                         const int *tile_job = nullptr);
 
 // ---- fused groups of small modes (tcg.cu) ----
 // Modes a .. a+g-1 (g <= 3) of a column-major tensor X[P, m_0, .., m_{g-1}, Q]

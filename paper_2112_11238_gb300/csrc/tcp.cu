@@ -125,6 +125,7 @@ struct TcLaunch {
     int stages, nacc, nbuf, acc_cols, bn_max;
     int dep_hold;                      // test hook: extra tiles every dependency waits for
     unsigned long long dep_wait_ns;    // time limit of a dependency wait
+    const int *tile_job;               // device table tile -> job (large job tables), or null
 };
 
 __device__ __forceinline__ const TcJob &job_at(const TcLaunch &L, int j) {
@@ -132,6 +133,9 @@ __device__ __forceinline__ const TcJob &job_at(const TcLaunch &L, int j) {
 }
 
 __device__ __forceinline__ int find_job(const TcLaunch &L, int t) {
+    // large tables (the batched operators: thousands of jobs of a few tiles)
+    // come with a tile -> job table: one load instead of a search
+    if (L.tile_job != nullptr) return __ldg(L.tile_job + t);
     int lo = 0, hi = L.njobs - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -1231,7 +1235,7 @@ static int num_sms() {
 // `done` holds one int per job, zeroed here.
 static cudaError_t tcp_launch(int form, const TcJob *jobs, int njobs, int total_tiles, int bn_max, int nkb_max,
                               const void *table, int *done, cudaStream_t st, FxScale *reset_next = nullptr,
-                              int want_stages = 0, int want_nacc = 0) {
+                              int want_stages = 0, int want_nacc = 0, const int *tile_job = nullptr) {
     if (total_tiles <= 0) return cudaSuccess;
     TcLaunch L;
     std::memset(&L, 0, sizeof(L));
@@ -1239,6 +1243,7 @@ static cudaError_t tcp_launch(int form, const TcJob *jobs, int njobs, int total_
     L.total_tiles = total_tiles;
     L.done = done;
     L.reset_next = reset_next;
+    L.tile_job = njobs > kMaxInline ? tile_job : nullptr;
     if (njobs <= kMaxInline)
         for (int j = 0; j < njobs; ++j) L.inl[j] = jobs[j];
     else
@@ -1348,6 +1353,7 @@ cudaError_t tcp_contract(int form, const Contraction &c, const void *img, cudaSt
 void tcp_jobs_begin(TcpJobs &jobs, int form) {
     jobs.form = form;
     jobs.host.clear();
+    jobs.tile_job.clear();
     jobs.total_tiles = 0;
     jobs.bn_max = 16;
     jobs.nkb_max = 1;
@@ -1363,6 +1369,7 @@ int tcp_jobs_add(TcpJobs &jobs, const Contraction &c, const void *img, int dep, 
         D->publish = 1;
     }
     jobs.total_tiles += J.tiles_m * J.tiles_n;
+    jobs.tile_job.insert(jobs.tile_job.end(), (size_t)J.tiles_m * J.tiles_n, (int)(jobs.host.size() / sizeof(TcJob)));
     jobs.bn_max = std::max(jobs.bn_max, (int)J.BN);
     jobs.nkb_max = std::max(jobs.nkb_max, (int)J.nkb);
     const size_t off = jobs.host.size();
@@ -1373,10 +1380,10 @@ int tcp_jobs_add(TcpJobs &jobs, const Contraction &c, const void *img, int dep, 
 
 size_t tcp_jobs_table_bytes(const TcpJobs &jobs) { return jobs.host.size(); }
 
-cudaError_t tcp_jobs_run(const TcpJobs &jobs, const void *table, int *done, cudaStream_t st) {
+cudaError_t tcp_jobs_run(const TcpJobs &jobs, const void *table, int *done, cudaStream_t st, const int *tile_job) {
     const int njobs = (int)(jobs.host.size() / sizeof(TcJob));
     return tcp_launch(jobs.form, reinterpret_cast<const TcJob *>(jobs.host.data()), njobs, jobs.total_tiles,
-                      jobs.bn_max, jobs.nkb_max, table, done, st, nullptr, jobs.stages, jobs.nacc);
+                      jobs.bn_max, jobs.nkb_max, table, done, st, nullptr, jobs.stages, jobs.nacc, tile_job);
 }
 
 }  // namespace kron
