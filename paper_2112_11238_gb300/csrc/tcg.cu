@@ -59,6 +59,8 @@ struct GLaunch {
     int64_t Gin, Gout;       // elements of one (p, q) slab before / after the group
     uint32_t magic0;         // ceil(2^32 / cur[0][0])
     uint32_t op_off, stage_off, bar_off;
+    uint32_t etab_off[3];    // per mode: table of the epilogue's per-row offsets (shared memory)
+    int64_t estep[3];        // per mode: the offset's step per output column
     int kbmax;
     int vec4;                // groups of four input elements are 16-byte aligned
 };
@@ -104,6 +106,64 @@ __device__ __forceinline__ void load_unit(const GLaunch &L, int64_t u, float *st
     cp_async_commit();
 }
 
+// Where the epilogue of mode t puts the outputs of row `row`: for a mode
+// before the last, the word offset in the staging array of the next mode's
+// row for output column 0 (the column adds estep[t] per step); for the last
+// mode, the element offset in C apart from p0 and q (p0 + off + P Gout q).
+// Rows are decoded as pb (fastest), then the dims other than t in increasing
+// order.  The same for every unit: built once per CTA.
+__device__ __forceinline__ int64_t epi_offset(const GLaunch &L, int t, int row) {
+    const int PB = L.PB;
+    const int pb = row & (PB - 1);
+    int o = row >> L.lpb;
+    int da, db;
+    others(L.g, t, da, db);
+    int j[3] = {0, 0, 0};
+    if (da >= 0) {
+        const int sa = L.cur[t][da];
+        j[da] = o % sa;
+        o /= sa;
+    }
+    if (db >= 0) j[db] = o;
+    if (t < L.g - 1) {
+        // next mode t + 1: rows over the dims other than t + 1 (sizes
+        // cur[t + 1]), k = j[t + 1]; linear in j[t]
+        int na, nb;
+        others(L.g, t + 1, na, nb);
+        const int sa = L.cur[t + 1][na >= 0 ? na : 0];
+        const int ja = (na == t) ? 0 : (na >= 0 ? j[na] : 0);
+        const int jb = (nb == t) ? 0 : (nb >= 0 ? j[nb] : 0);
+        return (int64_t)(pb + PB * (ja + sa * jb)) * kPitch + j[t + 1];
+    }
+    // C: p + P (j_0 + n_0 (j_1 + n_1 j_2) + Gout q), j[t] = column
+    int64_t idx = 0, mult = 1;
+    for (int d = 0; d < L.g; ++d) {
+        if (d != t) idx += mult * j[d];
+        mult *= (d == t) ? L.N[t] : L.cur[t][d];
+    }
+    return pb + L.P * idx;
+}
+
+// Stores the N outputs of one row, column c at dst + c * step, in chunks of
+// 16, 8 and 8 columns (chunks past N are skipped as a whole).
+template <typename To>
+__device__ __forceinline__ void store_outputs(To *dst, int64_t step, int N, const uint32_t (&r0)[32],
+                                              const uint32_t (&r1)[32]) {
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+        if (c < N) dst[c * step] = (To)(__uint_as_float(r1[c]) + __uint_as_float(r0[c]));
+    if (N > 16) {
+#pragma unroll
+        for (int c = 16; c < 24; ++c)
+            if (c < N) dst[c * step] = (To)(__uint_as_float(r1[c]) + __uint_as_float(r0[c]));
+    }
+    if (N > 24) {
+#pragma unroll
+        for (int c = 24; c < 32; ++c)
+            if (c < N) dst[c * step] = (To)(__uint_as_float(r1[c]) + __uint_as_float(r0[c]));
+    }
+}
+
 template <int F>
 __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant__ GLaunch L) {
     using T = FT<F>;
@@ -141,6 +201,16 @@ __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant
         uint4 *d = reinterpret_cast<uint4 *>(smem + L.simg[t]);
         for (uint32_t i = tid; i < L.img_bytes[t] / 16; i += kGThreads) d[i] = __ldg(s + i);
     }
+    // the epilogue's per-row offsets of every mode
+    for (int t = 0; t < L.g; ++t) {
+        if (t < L.g - 1) {
+            int *tab = reinterpret_cast<int *>(smem + L.etab_off[t]);
+            for (int row = tid; row < L.rows[t]; row += kGThreads) tab[row] = (int)epi_offset(L, t, row);
+        } else {
+            long long *tab = reinterpret_cast<long long *>(smem + L.etab_off[t]);
+            for (int row = tid; row < L.rows[t]; row += kGThreads) tab[row] = epi_offset(L, t, row);
+        }
+    }
     fence_proxy_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -168,15 +238,25 @@ __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant
                 const int kread = (K + T::MMA_K - 1) / T::MMA_K * T::MMA_K;
                 const int nch = (kread + CH - 1) / CH;  // chunks read by the MMAs
                 for (int tile = 0; tile < tiles; ++tile) {
+                    // rows past the last fibre are not converted: the MMA turns
+                    // whatever they hold into output rows that are never stored
+                    // (every output row depends on its own operand row only)
+                    const int rt = min(kBM, rows - tile * kBM);
                     const int items = kBM * nch;
                     for (int it = tid; it < items; it += kConvT) {
                         const int r = it % kBM, ch = it / kBM;
+                        if (r >= rt) continue;
                         const int row = tile * kBM + r;
                         const int k0 = ch * CH;
+                        const float *src = stage + row * kPitch + k0;
                         float v[CH];
+                        if (k0 + CH <= K) {
 #pragma unroll
-                        for (int e = 0; e < CH; ++e)
-                            v[e] = (row < rows && k0 + e < K) ? stage[row * kPitch + k0 + e] : 0.f;
+                            for (int e = 0; e < CH; ++e) v[e] = src[e];
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < CH; ++e) v[e] = k0 + e < K ? src[e] : 0.f;
+                        }
                         uint4 out[T::PIECES];
                         split_pack<F, float>(v, out);
                         uint8_t *base = op + ((size_t)(tile * L.kbmax + (ch >> 2)) * T::PIECES) * kTile;
@@ -240,8 +320,6 @@ __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant
             }
             phases ^= (1u << tiles) - 1u;
             const bool good = wg < tiles && gflag[wg] != 0;
-            int da, db;
-            others(L.g, t, da, db);
             const int qd = warp & 3;
             if (good) {
                 const int tile = wg;
@@ -252,53 +330,15 @@ __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant
                 tmem_ld32(ta + 32u, r1);
                 tmem_ld_wait();
                 const int row = tile * kBM + qd * 32 + lane;
-                // decode the row: pb, then the dims other than t
-                const int pb = row & (PB - 1);
-                int o = row >> L.lpb;
-                int j[3] = {0, 0, 0};
-                if (da >= 0) {
-                    const int sa = L.cur[t][da];
-                    j[da] = o % sa;
-                    o /= sa;
-                }
-                if (db >= 0) j[db] = o;
-                if (row >= rows || pb >= pvalid) {
-                } else if (!last) {
-                    // next mode t + 1: rows over the dims other than t + 1
-                    // (sizes cur[t + 1]), k = j[t + 1]; linear in j[t] = c
-                    int na, nb;
-                    others(L.g, t + 1, na, nb);
-                    const int sa = L.cur[t + 1][na >= 0 ? na : 0];
-                    // flatten: j[na] + sa * j[nb]
-                    const int ja = (na == t) ? 0 : (na >= 0 ? j[na] : 0);
-                    const int jb = (nb == t) ? 0 : (nb >= 0 ? j[nb] : 0);
-                    const int r0i = pb + PB * (ja + sa * jb);
-                    const int rc = PB * ((na == t) ? 1 : ((nb == t) ? sa : 0));
-                    float *dst = stage + r0i * kPitch + j[t + 1];
-                    const int step = rc * kPitch;
-#pragma unroll
-                    for (int c = 0; c < 32; ++c)
-                        if (c < N) dst[c * step] = __uint_as_float(r1[c]) + __uint_as_float(r0[c]);
-                } else {
-                    // C: p + P (j_0 + n_0 (j_1 + n_1 j_2) + Gout q), j[t] = c
-                    int64_t idx = 0, mult = 1, cs = 0;
-                    for (int d = 0; d < L.g; ++d) {
-                        if (d == t) cs = mult;
-                        else idx += mult * j[d];
-                        mult *= (d == t) ? N : L.cur[t][d];
-                    }
-                    const int64_t base = p0 + pb + L.P * (idx + L.Gout * q);
-                    const int64_t step = L.P * cs;
-                    if (L.dst64) {
-                        double *dst = static_cast<double *>(L.dst) + base;
-#pragma unroll
-                        for (int c = 0; c < 32; ++c)
-                            if (c < N) dst[c * step] = (double)(__uint_as_float(r1[c]) + __uint_as_float(r0[c]));
+                if (row < rows && (row & (PB - 1)) < pvalid) {
+                    if (!last) {
+                        const int off = reinterpret_cast<const int *>(smem + L.etab_off[t])[row];
+                        store_outputs<float>(stage + off, L.estep[t], N, r0, r1);
                     } else {
-                        float *dst = static_cast<float *>(L.dst) + base;
-#pragma unroll
-                        for (int c = 0; c < 32; ++c)
-                            if (c < N) dst[c * step] = __uint_as_float(r1[c]) + __uint_as_float(r0[c]);
+                        const int64_t base = p0 + reinterpret_cast<const long long *>(smem + L.etab_off[t])[row] +
+                                             L.P * L.Gout * q;
+                        if (L.dst64) store_outputs<double>(static_cast<double *>(L.dst) + base, L.estep[t], N, r0, r1);
+                        else store_outputs<float>(static_cast<float *>(L.dst) + base, L.estep[t], N, r0, r1);
                     }
                 }
             }
@@ -403,6 +443,29 @@ static bool tcg_plan_pb(int form, const GroupSpec &gs, int pb_cap, GLaunch &L, s
         L.simg[t] = (uint32_t)off;
         L.img_bytes[t] = (uint32_t)(L.KB[t] * g_pieces(form) * L.BN[t] * kRowBytes);
         off += (L.img_bytes[t] + 1023) / 1024 * 1024;
+    }
+    // the epilogue's per-row tables (int offsets before the last mode, 64-bit after)
+    for (int t = 0; t < gs.g; ++t) {
+        L.etab_off[t] = (uint32_t)off;
+        off += ((size_t)L.rows[t] * (t < gs.g - 1 ? 4 : 8) + 127) / 128 * 128;
+    }
+    // and their steps per output column: before the last mode, PB times the
+    // stride of dim t among the next mode's row dims (in increasing order),
+    // in staging words; after it, P times the product of the sizes before t
+    for (int t = 0; t < gs.g; ++t) {
+        if (t < gs.g - 1) {
+            int64_t stride = 1, rc = 0;
+            for (int d = 0; d < gs.g; ++d) {
+                if (d == t + 1) continue;
+                if (d == t) rc = stride;
+                stride *= L.cur[t + 1][d];
+            }
+            L.estep[t] = (int64_t)PB * rc * kPitch;
+        } else {
+            int64_t cs = 1;
+            for (int d = 0; d < t; ++d) cs *= L.cur[t][d];
+            L.estep[t] = gs.P * cs;
+        }
     }
     L.bar_off = (uint32_t)off;
     off += 128;  // two barriers per tile, tensor-memory slot, flags
