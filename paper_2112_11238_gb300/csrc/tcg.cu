@@ -63,6 +63,8 @@ struct GLaunch {
     int64_t estep[3];        // per mode: the offset's step per output column
     int kbmax;
     int vec4;                // groups of four input elements are 16-byte aligned
+    int bulk0;               // P = 1 and the slab copies as one bulk copy (16-byte multiple and aligned):
+                             // mode 0's rows are then staged with pitch m_0 (the slab as it is)
 };
 
 __device__ __forceinline__ void named_bar(int id, int n) {
@@ -86,7 +88,18 @@ __device__ __forceinline__ void others(int g, int t, int &da, int &db) {
 // goes to row pb + PB (j_1 + cur1 j_2), column j_0); threads t0, t0 + nt, ..
 // take part.  Padding p (past P) is not copied: its rows only feed outputs
 // that are never stored.
-__device__ __forceinline__ void load_unit(const GLaunch &L, int64_t u, float *stage, int t0, int nt) {
+__device__ __forceinline__ void load_unit(const GLaunch &L, int64_t u, float *stage, int t0, int nt, uint64_t *bar_in) {
+    if (L.bulk0) {
+        // one slab, contiguous in memory and in the staging array (pitch m_0):
+        // one bulk copy by the TMA unit, completing on bar_in
+        if (t0 == 0) {
+            const uint32_t bytes = (uint32_t)(L.Gin * 4);
+            fence_proxy_async_smem();  // the stage's previous readers came first
+            mbar_arrive_expect_tx(smem_u32(bar_in), bytes);
+            bulk_g2s(smem_u32(stage), L.src + L.Gin * u, bytes, smem_u32(bar_in));
+        }
+        return;
+    }
     const int64_t pblk = u % L.pblocks, q = u / L.pblocks;
     const int64_t p0 = pblk * L.PB;
     const int PB = L.PB;
@@ -176,7 +189,8 @@ __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant
     float *stage = reinterpret_cast<float *>(smem + L.stage_off);
     uint64_t *bar_mma = reinterpret_cast<uint64_t *>(smem + L.bar_off);  // per tile: its MMAs completed
     uint64_t *bar_conv = bar_mma + kGMaxTiles;                            // per tile: its operand is written
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_conv + kGMaxTiles);
+    uint64_t *bar_in = bar_conv + kGMaxTiles;                             // the unit's input (bulk copy)
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_in + 1);
     int *flag = reinterpret_cast<int *>(tslot + 1);
     int *gflag = flag + 1;  // per tile: its waits ended in time
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -188,6 +202,7 @@ __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant
             mbar_init(smem_u32(&bar_conv[i]), kConvT / 32);
             gflag[i] = 1;
         }
+        mbar_init(smem_u32(bar_in), 1);
         fence_mbar_init();
         *flag = 1;
     }
@@ -217,7 +232,8 @@ __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant
     tc_fence_after();
     const uint32_t tmem = *tslot;
     uint32_t phases = 0;  // bit i: parity of tile i's two barriers
-    if (blockIdx.x < L.units) load_unit(L, blockIdx.x, stage, tid, kGThreads);
+    uint32_t in_phase = 0;
+    if (blockIdx.x < L.units) load_unit(L, blockIdx.x, stage, tid, kGThreads, bar_in);
 
     for (int64_t u = blockIdx.x; u < L.units; u += gridDim.x) {
         const int64_t pblk = u % L.pblocks, q = u / L.pblocks;
@@ -225,8 +241,14 @@ __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant
         const int PB = L.PB;
         const int64_t pvalid = min((int64_t)PB, L.P - p0);
         // ---- 1. the unit's input (copies issued during the previous unit)
-        cp_async_wait<0>();
+        if (L.bulk0) {
+            if (tid == 0 && !mbar_wait(smem_u32(bar_in), in_phase)) *flag = 0;
+            in_phase ^= 1u;
+        } else {
+            cp_async_wait<0>();
+        }
         __syncthreads();
+        if (*flag == 0) break;
         for (int t = 0; t < L.g; ++t) {
             const int K = L.K[t], N = L.N[t], rows = L.rows[t], tiles = L.tiles[t];
             const int kb_n = L.KB[t];
@@ -235,6 +257,9 @@ __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant
             // K-major swizzled layout; each warp signals the tile's barrier.
             // Chunks past the last K-step of the MMAs are never read.
             if (!mma_warp) {
+                // mode 0 of a bulk-copied slab is staged with pitch m_0
+                const int pitch = (t == 0 && L.bulk0) ? L.K[0] : kPitch;
+                const bool vec_rows = t == 0 && L.bulk0;
                 const int kread = (K + T::MMA_K - 1) / T::MMA_K * T::MMA_K;
                 const int nch = (kread + CH - 1) / CH;  // chunks read by the MMAs
                 for (int tile = 0; tile < tiles; ++tile) {
@@ -248,9 +273,14 @@ __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant
                         if (r >= rt) continue;
                         const int row = tile * kBM + r;
                         const int k0 = ch * CH;
-                        const float *src = stage + row * kPitch + k0;
+                        const float *src = stage + row * pitch + k0;
                         float v[CH];
-                        if (k0 + CH <= K) {
+                        if (k0 + CH <= K && vec_rows) {
+                            // pitch m_0, a multiple of four: 16-byte rows of
+                            // eight lanes fall in distinct banks
+#pragma unroll
+                            for (int e = 0; e < CH; e += 4) *reinterpret_cast<float4 *>(&v[e]) = *reinterpret_cast<const float4 *>(src + e);
+                        } else if (k0 + CH <= K) {
 #pragma unroll
                             for (int e = 0; e < CH; ++e) v[e] = src[e];
                         } else {
@@ -272,7 +302,7 @@ __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant
                 // the next mode's rows there, or, after the last mode, the
                 // next unit's input may go there while this unit finishes
                 named_bar(5, kConvT);
-                if (last && u + gridDim.x < L.units) load_unit(L, u + gridDim.x, stage, tid, kConvT);
+                if (last && u + gridDim.x < L.units) load_unit(L, u + gridDim.x, stage, tid, kConvT, bar_in);
             } else if (lane == 0) {
                 // ---- 2b. the MMAs of each tile as soon as it is converted
                 const uint32_t idesc = make_idesc(T::FMT, kBM, (uint32_t)L.BN[t]);
@@ -522,6 +552,7 @@ cudaError_t tcg_run(int form, const GroupSpec &gs, const float *src, void *dst, 
     // slabs of a multiple of four, or p-blocks (PB >= 4) with P a multiple of four
     const bool base16 = (reinterpret_cast<uintptr_t>(src) & 15) == 0;
     L.vec4 = base16 && ((L.P == 1 && L.Gin % 4 == 0) || (L.P > 1 && L.PB >= 4 && L.P % 4 == 0)) ? 1 : 0;
+    L.bulk0 = (base16 && L.P == 1 && L.Gin % 4 == 0 && L.K[0] % 4 == 0) ? 1 : 0;
     switch (form) {
         case kTF32x3: return tcg_launch_f<kTF32x3>(L, smem, st);
         case kBF16x3: return tcg_launch_f<kBF16x3>(L, smem, st);
