@@ -235,7 +235,7 @@ kron_status run_chain(const kron_plan_s *pl, const void *T, const void *const *L
                 for (int k = 0; k < t; ++k) gc[mu + k] = pl->n[mu + k];
                 const ModeGeom gt = mode_geom(d, gc, nu, pl->n[nu]);
                 Contraction c = tc_mode_contraction(gt, nullptr, false, L[nu], io64, ldL[nu], trans, nullptr, false);
-                if (tc_build_bimage(form, c, ws + pl->img_off[nu], st) != cudaSuccess) return KRON_ERR_CUDA;
+                if (tc_build_bimage_bn(form, c, ws + pl->img_off[nu], kTcgBN, st) != cudaSuccess) return KRON_ERR_CUDA;
             }
             if (tcg_run(form, gs, static_cast<const float *>(src), dst, dst64, st) != cudaSuccess) return KRON_ERR_CUDA;
             for (int t = 0; t < gsz; ++t) cur[mu + t] = pl->n[mu + t];
@@ -282,6 +282,10 @@ void plan_layout(kron_plan_s *pl) {
     for (int k = 0; k < d; ++k) {
         pl->img_off[k] = off;
         pl->img_bytes[k] = form >= 0 ? tc_bimage_bytes(form, pl->n[k], pl->m[k]) : 0;
+        // small modes of the split forms may run in a fused group, whose image
+        // has N-tiles of kTcgBN columns
+        if (is_split(pl->prec) && pl->n[k] <= kTcgBN && pl->m[k] <= kTcgBN)
+            pl->img_bytes[k] = std::max(pl->img_bytes[k], tc_bimage_bytes_bn(form, pl->n[k], pl->m[k], kTcgBN));
         off += align_up(pl->img_bytes[k]);
     }
     // largest intermediate (outputs of steps 0..d-2)

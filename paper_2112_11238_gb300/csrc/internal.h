@@ -77,6 +77,8 @@ int tc_tile_n_cap(int form, int64_t N, int cap);
 // Writes the image of B (given as a Contraction's B side: colB/kB maps over
 // N x K) into `img` (device, tc_bimage_bytes long).
 cudaError_t tc_build_bimage(int form, const Contraction &c, void *img, cudaStream_t st);
+// the same image for N-tiles of width bn (tc_bimage_bytes_bn long)
+cudaError_t tc_build_bimage_bn(int form, const Contraction &c, void *img, int bn, cudaStream_t st);
 // C = A * B with the B operand from an image made by tc_build_bimage.
 cudaError_t tc_contract_bimage(int form, const Contraction &c, const void *img, cudaStream_t st);
 // Split-K contraction with both operands converted on load (the adjoint's
@@ -145,7 +147,9 @@ cudaError_t tcp_jobs_run(const TcpJobs &jobs, const void *table, int *done, cuda
 // ---- fused groups of small modes (tcg.cu) ----
 // Modes a .. a+g-1 (g <= 3) of a column-major tensor X[P, m_0, .., m_{g-1}, Q]
 // mapped to n_0 .. n_{g-1} in one launch, applied in that order; img[t]: the
-// image of op(L_t) made by tc_build_bimage.  Every m, n <= 32; the split forms.
+// image of op(L_t) made by tc_build_bimage_bn with N-tiles of kTcgBN columns.
+// Every m, n <= 32; the split forms.
+constexpr int kTcgBN = 32;
 struct GroupSpec {
     int g = 0;
     int64_t P = 1, Q = 1;

@@ -481,7 +481,10 @@ static cudaError_t dispatch_form(int form, const TcDev &d, bool akc, bool bimg, 
 }
 
 cudaError_t tc_build_bimage(int form, const Contraction &c, void *img, cudaStream_t st) {
-    const int bn = tc_tile_n(form, c.N);
+    return tc_build_bimage_bn(form, c, img, tc_tile_n(form, c.N), st);
+}
+
+cudaError_t tc_build_bimage_bn(int form, const Contraction &c, void *img, int bn, cudaStream_t st) {
     const int64_t nt = (c.N + bn - 1) / bn;
     const int64_t kb = (c.K + bk_of(form) - 1) / bk_of(form);
     const int64_t total = nt * kb * bn * kChunks;

@@ -18,8 +18,9 @@
 //      swizzled layout of the tcgen05 descriptors (up to four 128-row tiles);
 //      tile by tile, one thread issues the MMAs of the tile against the
 //      mode's op(L) image (kept in shared memory for the whole launch) into
-//      tensor memory (hi * hi apart from the cross products, as in the other
-//      kernels) while the next tile is converted; four groups of four warps,
+//      tensor memory (hi * hi apart from the smaller products, as in the other
+//      kernels; two B pieces per MMA where they sit side by side in the image)
+//      while the next tile is converted; four groups of four warps,
 //      one tile each, read the accumulators back and write the outputs into
 //      the staging array as the rows of the next mode, or, after the last
 //      mode, to global memory;
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant
         *flag = 1;
     }
     if (warp == 0) {
-        tmem_alloc(smem_u32(tslot), 256);
+        tmem_alloc(smem_u32(tslot), 512);
         tmem_relinquish();
     }
     // the images of op(L_t): small, loaded once (16-byte words)
@@ -305,9 +306,14 @@ __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant
                 if (last && u + gridDim.x < L.units) load_unit(L, u + gridDim.x, stage, tid, kConvT, bar_in);
             } else if (lane == 0) {
                 // ---- 2b. the MMAs of each tile as soon as it is converted
-                const uint32_t idesc = make_idesc(T::FMT, kBM, (uint32_t)L.BN[t]);
+                // op(L)'s pieces lie one after the other in its image (32 rows
+                // each), so one MMA of N = 64 multiplies an A piece by two B
+                // pieces at once; tensor memory per tile: Z = hi * hi, X = the
+                // products of piece-index sum 1, Y (BF16x6) sum 2, 32 columns each
+                const uint32_t idesc1 = make_idesc(T::FMT, kBM, (uint32_t)kTcgBN);
+                const uint32_t idesc2 = make_idesc(T::FMT, kBM, (uint32_t)(2 * kTcgBN));
                 const uint32_t img = smem_u32(smem + L.simg[t]);
-                const uint32_t PIECE_B = (uint32_t)L.BN[t] * kRowBytes;
+                constexpr uint32_t PIECE_B = (uint32_t)kTcgBN * kRowBytes;
                 const uint64_t adesc0 = smem_desc_kmajor(smem_u32(op), kRowBytes);
                 const uint64_t bdesc0 = smem_desc_kmajor(img, kRowBytes);
                 for (int tile = 0; tile < tiles; ++tile) {
@@ -316,7 +322,7 @@ __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant
                         continue;  // its MMA barrier never completes: the tile's group times out too
                     }
                     tc_fence_after();
-                    const uint32_t d = tmem + (uint32_t)(tile * 64);  // two regions of 32 columns
+                    const uint32_t d = tmem + (uint32_t)(tile * 128);
                     for (int kb = 0; kb < kb_n; ++kb) {
                         const int kval = min(BK, K - kb * BK);
                         const int ksteps = (kval + T::MMA_K - 1) / T::MMA_K;
@@ -324,14 +330,17 @@ __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant
                         const uint32_t a_off = (uint32_t)((tile * L.kbmax + kb) * T::PIECES) * kTile;
                         const uint32_t b_off = (uint32_t)(kb * T::PIECES) * PIECE_B;
                         for (int ks = 0; ks < ksteps; ++ks) {
-#pragma unroll
-                            for (int pr = 0; pr < T::NPROD; ++pr) {
-                                int pa, pb;
-                                prod_pieces<F>(pr, pa, pb);
-                                const uint64_t ad = adesc0 + ((a_off + pa * kTile + ks * 32) >> 4);
-                                const uint64_t bd = bdesc0 + ((b_off + pb * PIECE_B + ks * 32) >> 4);
-                                const bool first = kb == 0 && ks == 0 && first_in_region<F>(pr);
-                                tc_mma<T::KIND>(d + (uint32_t)region_of<F>(pr) * 32u, ad, bd, idesc, first ? 0u : 1u);
+                            const uint32_t acc = (kb == 0 && ks == 0) ? 0u : 1u;
+                            auto a = [&](int p) { return adesc0 + ((a_off + p * kTile + ks * 32) >> 4); };
+                            auto b = [&](int p) { return bdesc0 + ((b_off + p * PIECE_B + ks * 32) >> 4); };
+                            if constexpr (T::PIECES == 2) {
+                                tc_mma<T::KIND>(d, a(0), b(0), idesc2, acc);        // Z = a0 b0, X = a0 b1
+                                tc_mma<T::KIND>(d + 32u, a(1), b(0), idesc1, 1u);   // X += a1 b0
+                            } else {
+                                tc_mma<T::KIND>(d, a(0), b(0), idesc1, acc);        // Z = a0 b0
+                                tc_mma<T::KIND>(d + 32u, a(0), b(1), idesc2, acc);  // X = a0 b1, Y = a0 b2
+                                tc_mma<T::KIND>(d + 32u, a(1), b(0), idesc2, 1u);   // X += a1 b0, Y += a1 b1
+                                tc_mma<T::KIND>(d + 64u, a(2), b(0), idesc1, 1u);   // Y += a2 b0
                             }
                         }
                     }
@@ -354,10 +363,17 @@ __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant
             if (good) {
                 const int tile = wg;
                 tc_fence_after();
+                // r1 = X (+ Y), the smaller products, then r0 = Z = hi * hi
                 uint32_t r0[32], r1[32];
-                const uint32_t ta = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(tile * 64);
-                tmem_ld32(ta, r0);
+                const uint32_t ta = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(tile * 128);
                 tmem_ld32(ta + 32u, r1);
+                if constexpr (T::PIECES == 3) {
+                    tmem_ld32(ta + 64u, r0);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) r1[c] = __float_as_uint(__uint_as_float(r0[c]) + __uint_as_float(r1[c]));
+                }
+                tmem_ld32(ta, r0);
                 tmem_ld_wait();
                 const int row = tile * kBM + qd * 32 + lane;
                 if (row < rows && (row & (PB - 1)) < pvalid) {
@@ -388,7 +404,7 @@ __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, 256);
+        tmem_dealloc(tmem, 512);
     }
 }
 
@@ -422,8 +438,7 @@ static bool tcg_plan_pb(int form, const GroupSpec &gs, int pb_cap, GLaunch &L, s
         rows_max = std::max(rows_max, r);
         L.K[t] = (int)gs.m[t];
         L.N[t] = (int)gs.n[t];
-        L.BN[t] = tc_tile_n(form, gs.n[t]);
-        if (L.BN[t] > 32) return false;
+        L.BN[t] = kTcgBN;  // the image's N-tile (tc_build_bimage_bn with kTcgBN)
         L.KB[t] = (int)((gs.m[t] + bk - 1) / bk);
         sz[t] = (int)gs.n[t];
     }
@@ -530,11 +545,9 @@ static cudaError_t tcg_launch_f(const GLaunch &L, size_t smem, cudaStream_t st) 
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // resident CTAs per SM (registers: one of sixteen warps; tensor memory:
-    // 256 columns each, so at most two)
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tcg_kernel<F>, kGThreads, smem) != cudaSuccess)
-        per_sm = 1;
-    per_sm = std::max(1, std::min(per_sm, 2));
+    // one resident CTA per SM: each takes all 512 columns of tensor memory
+    (void)per_sm;
+    per_sm = 1;
     const int64_t grid = std::min<int64_t>(L.units, (int64_t)std::max(1, sms) * per_sm);
     tcg_kernel<F><<<(unsigned)grid, kGThreads, smem, st>>>(L);
     return cudaGetLastError();
