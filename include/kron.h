@@ -208,6 +208,14 @@ KRON_API kron_status kron_plan_destroy(kron_plan plan);
 KRON_API kron_status kron_plan_workspace_size(kron_plan plan, size_t *bytes);
 /* The 0-based mode order the plan applies (d entries). */
 KRON_API kron_status kron_plan_order(kron_plan plan, int *order);
+/*
+ * How kron_tucker runs the chain of this plan: *count launches of mode
+ * products, sizes[i] (up to d host entries) the number of mode products the
+ * i-th runs, in the plan's order: 1 for a product of its own, 2 or 3 for a
+ * fused group of small modes whose intermediates stay on chip.  The paper has
+ * no counterpart (its products each go through memory).  Host-only.
+ */
+KRON_API kron_status kron_plan_launches(kron_plan plan, int *sizes, int *count);
 /* Algorithmic FLOPs of one Tucker operator of this plan (see header comment). */
 KRON_API double kron_plan_flops(kron_plan plan);
 

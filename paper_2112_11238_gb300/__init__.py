@@ -68,6 +68,7 @@ _sig("kron_plan_create", [ctypes.POINTER(_vp), _ci, _i64p, _i64p, _ci, _ci, ctyp
 _sig("kron_plan_destroy", [_vp])
 _sig("kron_plan_workspace_size", [_vp, ctypes.POINTER(_sz)])
 _sig("kron_plan_order", [_vp, ctypes.POINTER(_ci)])
+_sig("kron_plan_launches", [_vp, ctypes.POINTER(_ci), ctypes.POINTER(_ci)])
 _sig("kron_plan_flops", [_vp], ctypes.c_double)
 _sig("kron_tucker", [_vp, _vp, ctypes.POINTER(_vp), _i64p, _vp, _vp, _sz, _vp])
 _sig("kron_ctucker_workspace_size", [_vp, ctypes.POINTER(_sz)])
@@ -108,7 +109,7 @@ EXPORTS = [
     "kron_status_string", "kron_version", "kron_get_device_error", "kron_debug_dependency_timeout",
     "kron_mump_workspace_size",
     "kron_mump", "kron_mump_noalloc", "kron_plan_create", "kron_plan_destroy", "kron_plan_workspace_size",
-    "kron_plan_order", "kron_plan_flops", "kron_tucker", "kron_ctucker_workspace_size", "kron_ctucker",
+    "kron_plan_order", "kron_plan_launches", "kron_plan_flops", "kron_tucker", "kron_ctucker_workspace_size", "kron_ctucker",
     "kron_gauss_hermite", "kron_gauss_laguerre", "kron_hermite_functions", "kron_laguerre_functions",
     "kron_fourier_resample", "kron_kronsumv_workspace_size", "kron_kronsumv", "kron_itucker_workspace_size", "kron_itucker", "kron_kronsum_pcg_workspace_size", "kron_kronsum_pcg", "kron_adjoint_workspace_size",
     "kron_tucker_adjoint", "kron_expm_workspace_size", "kron_expm",
@@ -316,6 +317,14 @@ class TuckerPlan:
         o = (ctypes.c_int * self.d)()
         _check(_lib.kron_plan_order(self._h, o), "kron_plan_order")
         return list(o)
+
+    def launches(self):
+        """Mode products per launch of kron_tucker, in the plan's order (2 or 3:
+        a fused group of small modes)."""
+        sz = (ctypes.c_int * self.d)()
+        cnt = ctypes.c_int(0)
+        _check(_lib.kron_plan_launches(self._h, sz, ctypes.byref(cnt)), "kron_plan_launches")
+        return list(sz)[:cnt.value]
 
     def flops(self) -> float:
         return float(_lib.kron_plan_flops(self._h))

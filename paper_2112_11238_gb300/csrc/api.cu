@@ -183,6 +183,34 @@ kron_status run_chain_fx(const kron_plan_s *pl, const void *T, const void *const
     return KRON_OK;
 }
 
+// Size of the fused group of small modes that starts at chain step s (the
+// modes order[s], order[s] + 1, .. applied one after the other), 0 if none:
+// split forms only, up to three modes, the largest group whose sizes fit the
+// fused kernel.  cur: the sizes before step s.  A group may not end with the
+// chain's last step when that step accumulates into S.
+int chain_group(const kron_plan_s *pl, int s, const int64_t *cur, bool acc_last, GroupSpec &gs) {
+    if (!is_split(pl->prec) || (pl->flags & KRON_PLAN_UNFUSED)) return 0;
+    const int d = pl->d, mu = pl->order[s];
+    for (int gg = std::min(3, d - s); gg >= 1; --gg) {
+        bool ok = !(acc_last && s + gg == d);
+        for (int t = 0; t < gg && ok; ++t) ok = pl->order[s + t] == mu + t;
+        if (!ok) continue;
+        GroupSpec c;
+        c.g = gg;
+        c.P = prod(cur, 0, mu);
+        c.Q = prod(cur, mu + gg, d);
+        for (int t = 0; t < gg; ++t) {
+            c.m[t] = cur[mu + t];
+            c.n[t] = pl->n[mu + t];
+        }
+        if (tcg_fits(form_of(pl->prec), c)) {
+            gs = c;
+            return gg;
+        }
+    }
+    return 0;
+}
+
 // acc_last: the last product adds into S instead of overwriting it.
 kron_status run_chain(const kron_plan_s *pl, const void *T, const void *const *L, const int64_t *ldL,
                       void *S, uint8_t *ws, cudaStream_t st, bool trans, bool acc_last = false) {
@@ -202,28 +230,9 @@ kron_status run_chain(const kron_plan_s *pl, const void *T, const void *const *L
         const ModeGeom g = mode_geom(d, cur, mu, pl->n[mu]);
         // split forms: consecutive small modes mu, mu + 1, .. applied in a row
         // run as one fused group with the intermediates on chip
-        int gsz = 0;
         GroupSpec gs;
-        if (split && !src64 && !(pl->flags & KRON_PLAN_UNFUSED)) {
-            for (int gg = std::min(3, d - s); gg >= 1 && gsz == 0; --gg) {
-                bool ok = !(acc_last && s + gg == d);
-                for (int t = 0; t < gg && ok; ++t) ok = pl->order[s + t] == mu + t;
-                if (!ok) continue;
-                GroupSpec c;
-                c.g = gg;
-                c.P = prod(cur, 0, mu);
-                c.Q = prod(cur, mu + gg, d);
-                for (int t = 0; t < gg; ++t) {
-                    c.m[t] = cur[mu + t];
-                    c.n[t] = pl->n[mu + t];
-                    c.img[t] = ws + pl->img_off[mu + t];
-                }
-                if (tcg_fits(form, c)) {
-                    gsz = gg;
-                    gs = c;
-                }
-            }
-        }
+        const int gsz = (split && !src64) ? chain_group(pl, s, cur, acc_last, gs) : 0;
+        for (int t = 0; t < gsz; ++t) gs.img[t] = ws + pl->img_off[mu + t];
         if (gsz > 0) {
             const bool last = (s + gsz == d);
             void *dst = last ? S : (void *)(ws + pl->buf_off[writes & 1]);
@@ -474,6 +483,27 @@ kron_status kron_plan_destroy(kron_plan plan) {
 kron_status kron_plan_workspace_size(kron_plan plan, size_t *bytes) {
     if (!plan || !bytes) return KRON_ERR_INVALID_ARG;
     *bytes = plan->ws_bytes;
+    return KRON_OK;
+}
+
+kron_status kron_plan_launches(kron_plan plan, int *sizes, int *count) {
+    if (!plan || !sizes || !count) return KRON_ERR_INVALID_ARG;
+    const int d = plan->d;
+    int64_t cur[KRON_MAX_D];
+    for (int k = 0; k < d; ++k) cur[k] = plan->m[k];
+    bool src64 = plan->dtype == KRON_F64;
+    int c = 0;
+    for (int s = 0; s < d;) {
+        GroupSpec gs;
+        int g = src64 ? 0 : chain_group(plan, s, cur, false, gs);
+        if (g == 0) g = 1;
+        for (int t = 0; t < g; ++t) cur[plan->order[s + t]] = plan->n[plan->order[s + t]];
+        sizes[c++] = g;
+        s += g;
+        src64 = false;  // the intermediates are FP32 (split forms) or of the plan's precision
+        if (plan->prec == KRON_PREC_FP64) src64 = true;
+    }
+    *count = c;
     return KRON_OK;
 }
 

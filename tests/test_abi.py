@@ -139,6 +139,33 @@ def test_tucker_batched_one_shot_validation(lib):
     assert lib.kron_tucker_batched(2, 3, m, n, None, None, None, 1, 2, None, ctypes.c_size_t(0), None) == 1
 
 
+def test_plan_launches_group_small_modes(lib):
+    """Which mode products run fused (host logic): the d=6 n=m=20 chain of a
+    split form with FP32 storage runs as groups {1,2,3}, {4,5}, {6}; FP64
+    storage cannot start a group (the fused kernel reads FP32), plain
+    precisions and the unfused flag run one product per launch, and modes
+    above 32 are never grouped."""
+    def launches(m, n, dtype, prec, flags=0):
+        h = ctypes.c_void_p()
+        assert lib.kron_plan_create(ctypes.byref(h), len(m), _i64(m), _i64(n), dtype, prec, flags) == 0
+        sz = (ctypes.c_int * len(m))()
+        cnt = ctypes.c_int(0)
+        assert lib.kron_plan_launches(h, sz, ctypes.byref(cnt)) == 0
+        lib.kron_plan_destroy(h)
+        return list(sz)[:cnt.value]
+    d6 = [20] * 6
+    for prec in (2, 3, 4):  # 3xTF32, BF16x3, BF16x6
+        assert launches(d6, d6, 1, prec) == [3, 2, 1]
+        assert launches(d6, d6, 1, prec, 0x4) == [1] * 6
+        g = launches(d6, d6, 0, prec)
+        assert g[0] == 1 and sum(g) == 6 and max(g) >= 2
+    for prec in (0, 1, 5, 6):  # FP64, FP32, FX32, FX32H
+        assert launches(d6, d6, 1, prec) == [1] * 6
+    assert launches([40, 40, 40], [40, 40, 40], 1, 2) == [1, 1, 1]
+    assert launches([40, 20, 20], [40, 20, 20], 1, 2, 0x2) == [1, 2]
+    assert sum(launches([7, 9, 5, 11], [13, 4, 8, 3], 1, 2, 0x2)) == 4
+
+
 def test_mump_workspace_query(lib):
     ws = ctypes.c_size_t(0)
     assert lib.kron_mump_workspace_size(3, _i64([5, 6, 7]), 1, 9, 1, 2, ctypes.byref(ws)) == 0
