@@ -155,23 +155,25 @@ __device__ __forceinline__ void split_pack(const Tin (&v)[16 / FT<F>::ELEM], uin
         out[0] = make_uint4(a0[0], a0[1], a0[2], a0[3]);
         out[1] = make_uint4(a1[0], a1[1], a1[2], a1[3]);
     } else {
-        uint32_t w[FT<F>::PIECES][8];
+        // two values at a time: one paired round-to-nearest conversion per
+        // piece gives the bf16x2 word directly (element e in the low half)
+        uint32_t w[FT<F>::PIECES][4];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const __nv_bfloat16 b0 = __float2bfloat16_rn(h[e]);
-            const float r = (h[e] - __bfloat162float(b0)) + l[e];
-            const __nv_bfloat16 b1 = __float2bfloat16_rn(r);
-            w[0][e] = __bfloat16_as_ushort(b0);
-            w[1][e] = __bfloat16_as_ushort(b1);
+        for (int e = 0; e < 8; e += 2) {
+            const __nv_bfloat162 b0 = __floats2bfloat162_rn(h[e], h[e + 1]);
+            const float2 f0 = __bfloat1622float2(b0);
+            const float r0 = (h[e] - f0.x) + l[e], r1 = (h[e + 1] - f0.y) + l[e + 1];
+            const __nv_bfloat162 b1 = __floats2bfloat162_rn(r0, r1);
+            w[0][e / 2] = *reinterpret_cast<const uint32_t *>(&b0);
+            w[1][e / 2] = *reinterpret_cast<const uint32_t *>(&b1);
             if constexpr (FT<F>::PIECES == 3) {
-                const __nv_bfloat16 b2 = __float2bfloat16_rn(r - __bfloat162float(b1));
-                w[2][e] = __bfloat16_as_ushort(b2);
+                const float2 f1 = __bfloat1622float2(b1);
+                const __nv_bfloat162 b2 = __floats2bfloat162_rn(r0 - f1.x, r1 - f1.y);
+                w[2][e / 2] = *reinterpret_cast<const uint32_t *>(&b2);
             }
         }
 #pragma unroll
-        for (int p = 0; p < FT<F>::PIECES; ++p)
-            out[p] = make_uint4(w[p][0] | (w[p][1] << 16), w[p][2] | (w[p][3] << 16),
-                                w[p][4] | (w[p][5] << 16), w[p][6] | (w[p][7] << 16));
+        for (int p = 0; p < FT<F>::PIECES; ++p) out[p] = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
     }
 }
 
