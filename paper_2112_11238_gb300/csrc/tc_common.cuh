@@ -141,6 +141,8 @@ __device__ __forceinline__ void load_chunk(const Tin *__restrict__ src, int64_t 
 template <int F, typename Tin>
 __device__ __forceinline__ void split_pack(const Tin (&v)[16 / FT<F>::ELEM], uint4 (&out)[FT<F>::PIECES]) {
     constexpr int CH = 16 / FT<F>::ELEM;
+    // FP32 input has no low part (l = 0): its residuals skip the addition
+    constexpr bool LO = sizeof(Tin) == 8;
     float h[CH], l[CH];
 #pragma unroll
     for (int e = 0; e < CH; ++e) to_hl(v[e], h[e], l[e]);
@@ -149,7 +151,8 @@ __device__ __forceinline__ void split_pack(const Tin (&v)[16 / FT<F>::ELEM], uin
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             a0[e] = to_tf32(h[e]);
-            const float r = (h[e] - __uint_as_float(a0[e])) + l[e];
+            float r = h[e] - __uint_as_float(a0[e]);
+            if constexpr (LO) r += l[e];
             a1[e] = to_tf32(r);
         }
         out[0] = make_uint4(a0[0], a0[1], a0[2], a0[3]);
@@ -162,7 +165,11 @@ __device__ __forceinline__ void split_pack(const Tin (&v)[16 / FT<F>::ELEM], uin
         for (int e = 0; e < 8; e += 2) {
             const __nv_bfloat162 b0 = __floats2bfloat162_rn(h[e], h[e + 1]);
             const float2 f0 = __bfloat1622float2(b0);
-            const float r0 = (h[e] - f0.x) + l[e], r1 = (h[e + 1] - f0.y) + l[e + 1];
+            float r0 = h[e] - f0.x, r1 = h[e + 1] - f0.y;
+            if constexpr (LO) {
+                r0 += l[e];
+                r1 += l[e + 1];
+            }
             const __nv_bfloat162 b1 = __floats2bfloat162_rn(r0, r1);
             w[0][e / 2] = *reinterpret_cast<const uint32_t *>(&b0);
             w[1][e / 2] = *reinterpret_cast<const uint32_t *>(&b1);
