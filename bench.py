@@ -778,7 +778,7 @@ def run_configs(args):
     return 0
 
 
-PROFILE_CASES = ("tcg_d6", "simt_small_d6", "expm_256", "adjoint_d4", "batched_512")
+PROFILE_CASES = ("tcg_d6", "tcf_d6", "simt_small_d6", "expm_256", "adjoint_d4", "batched_512")
 
 
 def run_profile_case(args):
@@ -788,12 +788,13 @@ def run_profile_case(args):
     import paper_2112_11238_gb300 as kron
     dev = torch.device("cuda", 0)
     name = args.profile_case
-    if name in ("tcg_d6", "simt_small_d6"):
+    if name in ("tcg_d6", "tcf_d6", "simt_small_d6"):
+        # the fused groups (tensor cores, CUDA cores) or the per-mode FP32 kernel
         c = W.tucker_d6()
         T = kron.colmajor(torch.from_numpy(c.T).float().to(dev))
         Ls = [kron.colmajor(torch.from_numpy(L).float().to(dev)) for L in c.L]
         prec = "3xtf32" if name == "tcg_d6" else "fp32"
-        plan = kron.TuckerPlan(T.shape, [20] * 6, torch.float32, prec)
+        plan = kron.TuckerPlan(T.shape, [20] * 6, torch.float32, prec, fused=name != "simt_small_d6")
         ws = plan.workspace(dev)
         S = kron.empty_colmajor([20] * 6, torch.float32, dev)
         fn = lambda: plan.tucker_into(T, Ls, S, ws=ws)  # noqa: E731

@@ -185,13 +185,15 @@ kron_status run_chain_fx(const kron_plan_s *pl, const void *T, const void *const
 
 // Size of the fused group of small modes that starts at chain step s (the
 // modes order[s], order[s] + 1, .. applied one after the other), 0 if none:
-// split forms only, up to three modes, the largest group whose sizes fit the
-// fused kernel.  cur: the sizes before step s.  A group may not end with the
+// split forms and FP32, up to three modes (FP32: at least two), the largest
+// group whose sizes fit the fused kernel.  cur: the sizes before step s.  A group may not end with the
 // chain's last step when that step accumulates into S.
 int chain_group(const kron_plan_s *pl, int s, const int64_t *cur, bool acc_last, GroupSpec &gs) {
-    if (!is_split(pl->prec) || (pl->flags & KRON_PLAN_UNFUSED)) return 0;
+    const bool fp32 = pl->prec == KRON_PREC_FP32;
+    if ((!is_split(pl->prec) && !fp32) || (pl->flags & KRON_PLAN_UNFUSED)) return 0;
     const int d = pl->d, mu = pl->order[s];
-    for (int gg = std::min(3, d - s); gg >= 1; --gg) {
+    // FP32: a single mode runs faster on the per-mode kernel
+    for (int gg = std::min(3, d - s); gg >= (fp32 ? 2 : 1); --gg) {
         bool ok = !(acc_last && s + gg == d);
         for (int t = 0; t < gg && ok; ++t) ok = pl->order[s + t] == mu + t;
         if (!ok) continue;
@@ -203,7 +205,7 @@ int chain_group(const kron_plan_s *pl, int s, const int64_t *cur, bool acc_last,
             c.m[t] = cur[mu + t];
             c.n[t] = pl->n[mu + t];
         }
-        if (tcg_fits(form_of(pl->prec), c)) {
+        if (fp32 ? tcf_fits(c) : tcg_fits(form_of(pl->prec), c)) {
             gs = c;
             return gg;
         }
@@ -230,8 +232,28 @@ kron_status run_chain(const kron_plan_s *pl, const void *T, const void *const *L
         const ModeGeom g = mode_geom(d, cur, mu, pl->n[mu]);
         // split forms: consecutive small modes mu, mu + 1, .. applied in a row
         // run as one fused group with the intermediates on chip
+        // (FP32: the same groups on the CUDA cores)
         GroupSpec gs;
-        const int gsz = (split && !src64) ? chain_group(pl, s, cur, acc_last, gs) : 0;
+        const bool fp32 = pl->prec == KRON_PREC_FP32;
+        const int gsz = ((split || fp32) && !src64) ? chain_group(pl, s, cur, acc_last, gs) : 0;
+        if (gsz > 0 && fp32) {
+            for (int t = 0; t < gsz; ++t) {
+                gs.L[t] = L[mu + t];
+                gs.ldL[t] = ldL[mu + t];
+            }
+            gs.trans = trans;
+            gs.l64 = io64;
+            const bool last = (s + gsz == d);
+            void *dst = last ? S : (void *)(ws + pl->buf_off[writes & 1]);
+            const bool dst64 = last ? io64 : false;
+            if (tcf_run(gs, static_cast<const float *>(src), dst, dst64, st) != cudaSuccess) return KRON_ERR_CUDA;
+            for (int t = 0; t < gsz; ++t) cur[mu + t] = pl->n[mu + t];
+            src = dst;
+            src64 = dst64;
+            ++writes;
+            s += gsz - 1;
+            continue;
+        }
         for (int t = 0; t < gsz; ++t) gs.img[t] = ws + pl->img_off[mu + t];
         if (gsz > 0) {
             const bool last = (s + gsz == d);

@@ -155,9 +155,18 @@ struct GroupSpec {
     int64_t P = 1, Q = 1;
     int64_t m[3] = {1, 1, 1}, n[3] = {1, 1, 1};
     const void *img[3] = {nullptr, nullptr, nullptr};
+    // the FP32 CUDA-core variant reads op(L_t) itself: L_t, its leading
+    // dimension, op = L^T (trans), FP64 storage (l64)
+    const void *L[3] = {nullptr, nullptr, nullptr};
+    int64_t ldL[3] = {0, 0, 0};
+    bool trans = false, l64 = false;
 };
 bool tcg_fits(int form, const GroupSpec &gs);
 cudaError_t tcg_run(int form, const GroupSpec &gs, const float *src, void *dst, bool dst64, cudaStream_t st);
+// The same fused group in FP32 on the CUDA cores (fused multiply-add, each
+// output one ascending sum over k).
+bool tcf_fits(const GroupSpec &gs);
+cudaError_t tcf_run(const GroupSpec &gs, const float *src, void *dst, bool dst64, cudaStream_t st);
 
 // ---- CUDA-core path (simt.cu) ----
 // FP64 (f64 = true) or FP32 fused multiply-add.

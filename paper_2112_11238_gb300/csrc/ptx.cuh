@@ -40,6 +40,14 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// The dynamic shared memory from its first 1024-byte boundary on, as a
+// pointer derived from the array by pointer arithmetic only, so that the
+// compiler still knows it (and everything derived from it) to be shared
+// memory and emits shared-memory accesses with 32-bit addresses.
+__device__ __forceinline__ uint8_t *smem_align1024(uint8_t *raw) {
+    return raw + ((1024u - (smem_u32(raw) & 1023u)) & 1023u);
+}
+
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

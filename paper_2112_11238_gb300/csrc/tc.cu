@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const TcDev p) {
     constexpr int BK = kRowBytes / T::ELEM;
     constexpr uint32_t PIECE_A = kBM * kRowBytes;
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *smem = smem_align1024(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int BN = p.BN, S = p.stages;
     const uint32_t A_ST = T::PIECES * PIECE_A;

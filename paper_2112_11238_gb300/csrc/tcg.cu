@@ -42,7 +42,6 @@ constexpr int kGThreads = 512;   // sixteen warps: four groups of one warp per t
 constexpr int kPitch = 33;       // staging row pitch in floats (odd)
 constexpr int kGMaxTiles = 4;    // rows per mode <= 512
 constexpr uint32_t kTile = kBM * kRowBytes;  // one piece of one K-block of a 128-row tile
-constexpr int kLoadDepth = 4;    // 16-byte input loads in flight per thread
 
 struct GLaunch {
     const float *src;
@@ -58,8 +57,12 @@ struct GLaunch {
     int PB, lpb;
     int64_t pblocks, units;
     int64_t Gin, Gout;       // elements of one (p, q) slab before / after the group
-    uint32_t magic0;         // ceil(2^32 / cur[0][0])
+    uint32_t magic0;         // ceil(2^32 / cur[0][0]); unused when cur[0][0] = 1 (2^32 has no 32-bit form)
     uint32_t op_off, stage_off, bar_off;
+    uint32_t stage2_off;     // FP32 variant: the second staging array
+    const void *Lsrc[3];     // FP32 variant: L_t in global memory, ld, op = L^T, FP64 storage
+    int64_t ldL[3];
+    int ltrans, l64;
     uint32_t etab_off[3];    // per mode: table of the epilogue's per-row offsets (shared memory)
     int64_t estep[3];        // per mode: the offset's step per output column
     int kbmax;
@@ -113,7 +116,7 @@ __device__ __forceinline__ void load_unit(const GLaunch &L, int64_t u, float *st
         const int pb = (int)(e & (uint32_t)(PB - 1));
         const uint32_t rest = e >> L.lpb;
         if (pb >= pvalid) continue;
-        const uint32_t o = __umulhi(rest, L.magic0);  // rest / cur0
+        const uint32_t o = c0 == 1u ? rest : __umulhi(rest, L.magic0);  // rest / cur0
         const uint32_t srow = (uint32_t)pb + (uint32_t)PB * o;
         cp_async4(s0 + (srow * kPitch + (rest - o * c0)) * 4u, src + pb + L.P * (int64_t)rest, 4u);
     }
@@ -185,7 +188,7 @@ __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant
     constexpr int BK = kRowBytes / T::ELEM;
     constexpr int kConvT = kGThreads - 32;  // converter threads (all warps but the last)
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *smem = smem_align1024(smem_raw);
     uint8_t *op = smem + L.op_off;
     float *stage = reinterpret_cast<float *>(smem + L.stage_off);
     uint64_t *bar_mma = reinterpret_cast<uint64_t *>(smem + L.bar_off);  // per tile: its MMAs completed
@@ -408,6 +411,177 @@ __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant
     }
 }
 
+// The FP32 CUDA-core variant of the fused group (same units, staging, rows
+// and offsets): mode t reads the staged rows of one array and writes the next
+// mode's rows into the other.  A weight that every lane of a warp needs costs
+// a full register write-back per lane when it is loaded, so each thread
+// takes a block of kFR rows x 4 output columns: per k it loads kFR row
+// values and one 16-byte word of op(L_t)^T ([k][c], 32 columns) for
+// 4 kFR fused multiply-adds.  Every output is one chain over k = 0 .. K-1
+// in ascending order from zero.  The rows of a thread are rg, rg + RG, ..
+// (RG = ceil(rows / kFR)), so that lanes with consecutive rg read rows of
+// distinct banks and store consecutive outputs; the loops over k are
+// unrolled to 32 (K <= 32), so that every shared-memory address is a
+// register plus a constant.
+constexpr int kFR = 8;
+constexpr int kFWP4 = 8;  // op(L_t)^T rows: 32 floats (eight 16-byte words)
+
+__global__ void __launch_bounds__(kGThreads, 1) tcf_kernel(const __grid_constant__ GLaunch L) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = smem_align1024(smem_raw);
+    float *const stg0 = reinterpret_cast<float *>(smem + L.stage_off);
+    float *const stg1 = reinterpret_cast<float *>(smem + L.stage2_off);
+    auto stg = [&](int i) { return (i & 1) ? stg1 : stg0; };
+    uint64_t *bar_in = reinterpret_cast<uint64_t *>(smem + L.bar_off);
+    int *flag = reinterpret_cast<int *>(bar_in + 1);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(smem_u32(bar_in), 1);
+        fence_mbar_init();
+        *flag = 1;
+    }
+    // op(L_t)^T in FP32: [k][c] with 32 columns, zero past N
+    for (int t = 0; t < L.g; ++t) {
+        float *d = reinterpret_cast<float *>(smem + L.simg[t]);
+        const int K = L.K[t], N = L.N[t], wp = 4 * kFWP4;
+        for (int i = tid; i < K * wp; i += kGThreads) {
+            const int k = i / wp, c = i % wp;
+            float v = 0.f;
+            if (c < N) {
+                const int64_t o = L.ltrans ? (int64_t)k + L.ldL[t] * c : (int64_t)c + L.ldL[t] * k;
+                v = L.l64 ? (float)static_cast<const double *>(L.Lsrc[t])[o] : static_cast<const float *>(L.Lsrc[t])[o];
+            }
+            d[i] = v;
+        }
+    }
+    for (int t = 0; t < L.g; ++t) {
+        if (t < L.g - 1) {
+            int *tab = reinterpret_cast<int *>(smem + L.etab_off[t]);
+            for (int row = tid; row < L.rows[t]; row += kGThreads) tab[row] = (int)epi_offset(L, t, row);
+        } else {
+            long long *tab = reinterpret_cast<long long *>(smem + L.etab_off[t]);
+            for (int row = tid; row < L.rows[t]; row += kGThreads) tab[row] = epi_offset(L, t, row);
+        }
+    }
+    __syncthreads();
+    uint32_t in_phase = 0;
+    int b = 0;  // the staging array holding the unit's input
+    if (blockIdx.x < L.units) load_unit(L, blockIdx.x, stg0, tid, kGThreads, bar_in);
+
+    for (int64_t u = blockIdx.x; u < L.units; u += gridDim.x) {
+        const int64_t pblk = u % L.pblocks, q = u / L.pblocks;
+        const int64_t p0 = pblk * L.PB;
+        const int PB = L.PB;
+        const int64_t pvalid = min((int64_t)PB, L.P - p0);
+        if (L.bulk0) {
+            if (tid == 0 && !mbar_wait(smem_u32(bar_in), in_phase)) *flag = 0;
+            in_phase ^= 1u;
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        if (*flag == 0) break;
+        for (int t = 0; t < L.g; ++t) {
+            const int K = L.K[t], N = L.N[t], rows = L.rows[t];
+            const bool last = (t == L.g - 1);
+            const float *in = stg(b + t);
+            // mode 0 of a bulk-copied slab is staged with pitch m_0 (a multiple of four)
+            const bool vec = t == 0 && L.bulk0;
+            const int pitch = vec ? L.K[0] : kPitch;
+            // the array the last mode does not read takes the next unit's input
+            if (last && u + gridDim.x < L.units) load_unit(L, u + gridDim.x, stg(b + t + 1), tid, kGThreads, bar_in);
+            const int RG = (rows + kFR - 1) / kFR;
+            const int CG = (N + 3) / 4;
+            const float4 *W4 = reinterpret_cast<const float4 *>(smem + L.simg[t]);
+            for (int task = tid; task < RG * CG; task += kGThreads) {
+                const int cg = task / RG, rg = task - cg * RG;
+                // rows past the last are read as row rg (in bounds) and never stored
+                int ro[kFR];  // the rows' word offsets in the staging array
+#pragma unroll
+                for (int j = 0; j < kFR; ++j) {
+                    const int row = rg + j * RG;
+                    ro[j] = (row < rows ? row : rg) * pitch;
+                }
+                float acc[kFR][4];
+#pragma unroll
+                for (int j = 0; j < kFR; ++j)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) acc[j][i] = 0.f;
+                const float4 *wc = W4 + cg;  // op(L_t)^T row k at wc[k * kFWP4]
+                if (vec) {
+#pragma unroll
+                    for (int k = 0; k < 32; k += 4) {
+                        if (k >= K) break;
+                        float4 w[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) w[e] = wc[(k + e) * kFWP4];
+#pragma unroll
+                        for (int h = 0; h < kFR; h += 4) {
+                            float4 xv[4];
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) xv[j] = *reinterpret_cast<const float4 *>(in + ro[h + j] + k);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) {
+                                    const float x = e == 0 ? xv[j].x : e == 1 ? xv[j].y : e == 2 ? xv[j].z : xv[j].w;
+                                    acc[h + j][0] = fmaf(x, w[e].x, acc[h + j][0]);
+                                    acc[h + j][1] = fmaf(x, w[e].y, acc[h + j][1]);
+                                    acc[h + j][2] = fmaf(x, w[e].z, acc[h + j][2]);
+                                    acc[h + j][3] = fmaf(x, w[e].w, acc[h + j][3]);
+                                }
+                            }
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        if (k >= K) break;
+                        const float4 w = wc[k * kFWP4];
+#pragma unroll
+                        for (int j = 0; j < kFR; ++j) {
+                            const float x = in[ro[j] + k];
+                            acc[j][0] = fmaf(x, w.x, acc[j][0]);
+                            acc[j][1] = fmaf(x, w.y, acc[j][1]);
+                            acc[j][2] = fmaf(x, w.z, acc[j][2]);
+                            acc[j][3] = fmaf(x, w.w, acc[j][3]);
+                        }
+                    }
+                }
+                const int c0 = 4 * cg;
+                const int64_t step = L.estep[t];
+#pragma unroll
+                for (int j = 0; j < kFR; ++j) {
+                    const int row = rg + j * RG;
+                    if (row >= rows || (row & (PB - 1)) >= pvalid) continue;
+                    if (!last) {
+                        float *dst = stg(b + t + 1) + reinterpret_cast<const int *>(smem + L.etab_off[t])[row] + c0 * step;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            if (c0 + i < N) dst[i * step] = acc[j][i];
+                    } else {
+                        const int64_t base = p0 + reinterpret_cast<const long long *>(smem + L.etab_off[t])[row] +
+                                             L.P * L.Gout * q + c0 * step;
+                        if (L.dst64) {
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                if (c0 + i < N) static_cast<double *>(L.dst)[base + i * step] = (double)acc[j][i];
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                if (c0 + i < N) static_cast<float *>(L.dst)[base + i * step] = acc[j][i];
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        b = (b + L.g) & 1;
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+}
+
 constexpr size_t kGSmemMax = 227 * 1024;
 
 }  // namespace
@@ -417,8 +591,14 @@ static int g_bk(int form) { return form == kTF32x3 ? kRowBytes / 4 : kRowBytes /
 
 // Fills the launch for a group with p-blocks of at most pb_cap; false if it
 // does not fit (sizes, shared memory).
+// form kFusedFP32: the CUDA-core variant (no operand tiles, no images: op(L)
+// in FP32 in shared memory; two staging arrays, mode t reading one and
+// writing the other).
+constexpr int kFusedFP32 = -2;
+
 static bool tcg_plan_pb(int form, const GroupSpec &gs, int pb_cap, GLaunch &L, size_t &smem) {
-    if (form != kTF32x3 && form != kBF16x3 && form != kBF16x6) return false;
+    const bool fp32 = form == kFusedFP32;
+    if (!fp32 && form != kTF32x3 && form != kBF16x3 && form != kBF16x6) return false;
     if (gs.g < 1 || gs.g > 3 || gs.P < 1 || gs.Q < 1) return false;
     L = GLaunch{};
     L.g = gs.g;
@@ -427,7 +607,7 @@ static bool tcg_plan_pb(int form, const GroupSpec &gs, int pb_cap, GLaunch &L, s
         if (gs.m[t] < 1 || gs.m[t] > 32 || gs.n[t] < 1 || gs.n[t] > 32) return false;
         sz[t] = (int)gs.m[t];
     }
-    const int bk = g_bk(form);
+    const int bk = fp32 ? 32 : g_bk(form);
     int64_t rows_max = 1;
     for (int t = 0; t < gs.g; ++t) {
         for (int d = 0; d < 3; ++d) L.cur[t][d] = d < gs.g ? sz[d] : 1;
@@ -474,20 +654,35 @@ static bool tcg_plan_pb(int form, const GroupSpec &gs, int pb_cap, GLaunch &L, s
         L.Gin *= gs.m[t];
         L.Gout *= gs.n[t];
     }
-    L.magic0 = (uint32_t)(((1ull << 32) + (uint64_t)gs.m[0] - 1) / (uint64_t)gs.m[0]);
+    L.magic0 = gs.m[0] == 1 ? 0u : (uint32_t)(((1ull << 32) + (uint64_t)gs.m[0] - 1) / (uint64_t)gs.m[0]);
     // shared memory: operand tiles, staging, images, barrier + slots
     size_t off = 0;
     L.op_off = 0;
-    off += (size_t)tiles_max * kbmax * g_pieces(form) * kTile;
+    if (!fp32) off += (size_t)tiles_max * kbmax * g_pieces(form) * kTile;
     int64_t stage_rows = 0;
     for (int t = 0; t < gs.g; ++t) stage_rows = std::max<int64_t>(stage_rows, L.rows[t]);
+    const size_t stage_bytes = ((size_t)stage_rows * kPitch * 4 + 1023) / 1024 * 1024;
     L.stage_off = (uint32_t)off;
-    off += ((size_t)stage_rows * kPitch * 4 + 1023) / 1024 * 1024;
-    for (int t = 0; t < gs.g; ++t) {
-        L.img[t] = static_cast<const uint8_t *>(gs.img[t]);
-        L.simg[t] = (uint32_t)off;
-        L.img_bytes[t] = (uint32_t)(L.KB[t] * g_pieces(form) * L.BN[t] * kRowBytes);
-        off += (L.img_bytes[t] + 1023) / 1024 * 1024;
+    off += stage_bytes;
+    if (fp32) {
+        L.stage2_off = (uint32_t)off;
+        off += stage_bytes;
+        for (int t = 0; t < gs.g; ++t) {
+            L.Lsrc[t] = gs.L[t];
+            L.ldL[t] = gs.ldL[t];
+            L.simg[t] = (uint32_t)off;  // op(L_t)^T in FP32, [k][c] with 32 columns
+            L.img_bytes[t] = (uint32_t)(L.K[t] * 32 * 4);
+            off += (L.img_bytes[t] + 127) / 128 * 128;
+        }
+        L.ltrans = gs.trans ? 1 : 0;
+        L.l64 = gs.l64 ? 1 : 0;
+    } else {
+        for (int t = 0; t < gs.g; ++t) {
+            L.img[t] = static_cast<const uint8_t *>(gs.img[t]);
+            L.simg[t] = (uint32_t)off;
+            L.img_bytes[t] = (uint32_t)(L.KB[t] * g_pieces(form) * L.BN[t] * kRowBytes);
+            off += (L.img_bytes[t] + 1023) / 1024 * 1024;
+        }
     }
     // the epilogue's per-row tables (int offsets before the last mode, 64-bit after)
     for (int t = 0; t < gs.g; ++t) {
@@ -526,6 +721,41 @@ static bool tcg_plan(int form, const GroupSpec &gs, GLaunch &L, size_t &smem) {
         if (gs.P == 1) break;  // one slab per unit: nothing to shrink
     }
     return false;
+}
+
+bool tcf_fits(const GroupSpec &gs) {
+    GLaunch L;
+    size_t smem = 0;
+    return tcg_plan(kFusedFP32, gs, L, smem);
+}
+
+static cudaError_t tcf_launch(const GLaunch &L, size_t smem, cudaStream_t st) {
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [&] {
+        attr = cudaFuncSetAttribute(tcf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGSmemMax);
+    });
+    if (attr != cudaSuccess) return attr;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t grid = std::min<int64_t>(L.units, (int64_t)std::max(1, sms));
+    tcf_kernel<<<(unsigned)grid, kGThreads, smem, st>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t tcf_run(const GroupSpec &gs, const float *src, void *dst, bool dst64, cudaStream_t st) {
+    GLaunch L;
+    size_t smem = 0;
+    if (!tcg_plan(kFusedFP32, gs, L, smem)) return cudaErrorInvalidValue;
+    if (L.units == 0) return cudaSuccess;
+    L.src = src;
+    L.dst = dst;
+    L.dst64 = dst64 ? 1 : 0;
+    const bool base16 = (reinterpret_cast<uintptr_t>(src) & 15) == 0;
+    L.vec4 = base16 && ((L.P == 1 && L.Gin % 4 == 0) || (L.P > 1 && L.PB >= 4 && L.P % 4 == 0)) ? 1 : 0;
+    L.bulk0 = (base16 && L.P == 1 && L.Gin % 4 == 0 && L.K[0] % 4 == 0) ? 1 : 0;
+    return tcf_launch(L, smem, st);
 }
 
 bool tcg_fits(int form, const GroupSpec &gs) {

@@ -703,7 +703,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
     constexpr uint32_t PIECE_A = kBM * kRowBytes;
     constexpr uint32_t A_ST = T::PIECES * PIECE_A;
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *smem = smem_align1024(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = L.stages, NACC = L.nacc, NBUF = L.nbuf;
     const uint32_t ACOLS = (uint32_t)L.acc_cols;

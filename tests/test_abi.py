@@ -142,9 +142,10 @@ def test_tucker_batched_one_shot_validation(lib):
 def test_plan_launches_group_small_modes(lib):
     """Which mode products run fused (host logic): the d=6 n=m=20 chain of a
     split form with FP32 storage runs as groups {1,2,3}, {4,5}, {6}; FP64
-    storage cannot start a group (the fused kernel reads FP32), plain
-    precisions and the unfused flag run one product per launch, and modes
-    above 32 are never grouped."""
+    storage cannot start a group (the fused kernel reads FP32), FP32 groups
+    the same way on the CUDA cores (two modes or more), FP64, the fixed-point forms and the
+    unfused flag run one product per launch, and modes above 32 are never
+    grouped."""
     def launches(m, n, dtype, prec, flags=0):
         h = ctypes.c_void_p()
         assert lib.kron_plan_create(ctypes.byref(h), len(m), _i64(m), _i64(n), dtype, prec, flags) == 0
@@ -159,8 +160,12 @@ def test_plan_launches_group_small_modes(lib):
         assert launches(d6, d6, 1, prec, 0x4) == [1] * 6
         g = launches(d6, d6, 0, prec)
         assert g[0] == 1 and sum(g) == 6 and max(g) >= 2
-    for prec in (0, 1, 5, 6):  # FP64, FP32, FX32, FX32H
+    for prec in (0, 5, 6):  # FP64, FX32, FX32H
         assert launches(d6, d6, 1, prec) == [1] * 6
+    # FP32 (CUDA cores): groups of two or three only
+    assert launches(d6, d6, 1, 1) == [3, 2, 1]
+    assert launches([40, 20, 20], [40, 20, 20], 1, 1) == [1, 2]
+    assert launches([20, 40, 20], [20, 40, 20], 1, 1) == [1, 1, 1]
     assert launches([40, 40, 40], [40, 40, 40], 1, 2) == [1, 1, 1]
     assert launches([40, 20, 20], [40, 20, 20], 1, 2, 0x2) == [1, 2]
     assert sum(launches([7, 9, 5, 11], [13, 4, 8, 3], 1, 2, 0x2)) == 4

@@ -95,6 +95,7 @@ FUSED_CASES = [
     ((20, 20, 20), (20, 20, 20)), ((7, 9, 5, 11), (13, 4, 8, 3)), ((32, 1, 17), (5, 32, 2)),
     ((40, 12, 13, 14), (40, 9, 30, 7)), ((3, 50, 6, 7, 8), (4, 50, 9, 2, 31)), ((5,) * 6, (6, 4, 7, 3, 5, 2)),
     ((33, 31, 3), (29, 30, 31)), ((1, 1, 1), (32, 1, 16)), ((16, 16, 16, 16, 16), (16,) * 5),
+    ((1, 6, 7), (9, 5, 4)), ((3, 1, 9, 2), (5, 7, 1, 6)),
 ]
 
 
@@ -113,6 +114,27 @@ def test_fused_groups_match_oracle_and_unfused(kron, m, n, prec):
     assert rel_err(to_host(S), ref32) <= TOL[prec], (prec, m, n, rel_err(to_host(S), ref32))
     assert rel_err(to_host(U), ref32) <= TOL[prec]
     assert rel_err(to_host(S), ref) <= max(TOL[prec], 1e-6)
+    assert kron.device_error() == 0
+
+
+@pytest.mark.parametrize("io", ["f32", "f64"])
+@pytest.mark.parametrize("trans", [False, True])
+@pytest.mark.parametrize("m,n", FUSED_CASES)
+def test_fused_fp32_groups_match_oracle_and_unfused_bitwise(kron, m, n, trans, io):
+    """FP32 groups on the CUDA cores: every output is the same ascending chain
+    of fused multiply-adds as in the per-mode kernel, over the same FP32
+    intermediates, so the fused and unfused chains agree bit for bit."""
+    import torch
+    dt = torch.float32 if io == "f32" else torch.float64
+    T = rnd(*m)
+    Ls = [rnd(m[k], n[k]) if trans else rnd(n[k], m[k]) for k in range(len(m))]
+    Td = to_dev(T, dt)
+    Ld = [to_dev(L, dt) for L in Ls]
+    S = kron.tucker(Td, Ld, prec="fp32", trans=trans, natural_order=True)
+    U = kron.tucker(Td, Ld, prec="fp32", trans=trans, natural_order=True, fused=False)
+    assert torch.equal(S, U), (m, n, trans, io)
+    ref = oracle.tucker(to_host(Td), [(to_host(L).T.copy(order="F") if trans else to_host(L)) for L in Ld])
+    assert rel_err(to_host(S), ref) <= tol("fp32", sum(m)), (m, n, rel_err(to_host(S), ref))
     assert kron.device_error() == 0
 
 
