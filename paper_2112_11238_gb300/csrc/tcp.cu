@@ -302,6 +302,9 @@ __device__ __forceinline__ bool conv_tile_loop_raw(const TcJob &J, const CUtenso
     const bool tma = J.tma != 0;
     // per-unit source offsets (rows fixed over the tile)
     const int64_t row0 = (int64_t)mt * kBM;
+    // TMA coordinates of the tile's rows (slab layout: row in slab, slab)
+    const int trow = J.tma == 3 ? (int)(row0 % J.tmaP) : (int)row0;
+    const int tslab = J.tma == 3 ? (int)(row0 / J.tmaP) : 0;
     int64_t base[R::UNITS];
     int nrow[R::UNITS];
 #pragma unroll
@@ -322,9 +325,9 @@ __device__ __forceinline__ bool conv_tile_loop_raw(const TcJob &J, const CUtenso
         mbar_arrive_expect_tx(bar, R::BYTES);
         const int k0 = (J.kb0 + kbi) * BK;
         if (J.tma == 2) {
-            tma_load_2d(raw0 + slot * R::BYTES, tm, k0, (int)row0, bar);
+            tma_load_2d(raw0 + slot * R::BYTES, tm, k0, trow, bar);
         } else {
-            tma_load_3d(raw0 + slot * R::BYTES, tm, (int)(row0 % J.tmaP), k0, (int)(row0 / J.tmaP), bar);
+            tma_load_3d(raw0 + slot * R::BYTES, tm, trow, k0, tslab, bar);
         }
     };
     if (tma) {
@@ -487,11 +490,12 @@ __device__ __forceinline__ void fx_consts(const TcJob &J, int j, FxConsts &k) {
 // colw: one word per column of the tile in shared memory (the scale 2^s as
 // a float for fixed-point output, the row exponent f_c otherwise); every
 // warp fills the words of its own chunks (warps of other lane quarters
-// with the same chunks write the same values).
+// with the same chunks write the same values), unless they already hold the
+// words of the same job and column tile (fill_colw false).
 template <int F>
 __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, uint32_t lane_base, uint32_t ACOLS,
                                             int64_t ro, int64_t n0, int lane, int part, int nparts, uint8_t *stg,
-                                            const CUtensorMap *tmC, int64_t rw0, uint32_t *colw) {
+                                            const CUtensorMap *tmC, int64_t rw0, uint32_t *colw, bool fill_colw) {
     const int eA = k.eA, eC = k.eC;
     const int lim = (int)min(J.N - n0, (int64_t)J.BN);
     const bool unit = (J.colC.R0 == 0 && J.colC.s0 == 1);
@@ -500,12 +504,15 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, u
     using X = FxForm<F>;
     const int base = eA + X::UNIT + X::BITS - eC;
     // column words of this warp's chunks: lanes 0-15 one chunk, 16-31 the next
-    for (int c = 16 * part + (lane >> 4) * step + (lane & 15); c - (lane & 15) < J.BN; c += 2 * step) {
+    for (int c = 16 * part + (lane >> 4) * step + (lane & 15); fill_colw && c - (lane & 15) < J.BN; c += 2 * step) {
         const int f = c < lim ? __ldg(J.fxF + n0 + c) : 0;
         // 2^s (s below -126 leaves only values that round to 0)
         colw[c] = J.cfix ? (uint32_t)((127 + min(100, max(-126, base + f))) << 23) : (uint32_t)f;
     }
     __syncwarp();
+    // TMA coordinates of the warp's rows (slab layout: row in slab, slab)
+    const int trow = (stg && J.tmc == 3) ? (int)(rw0 % J.tmcP) : (int)rw0;
+    const int tslab = (stg && J.tmc == 3) ? (int)(rw0 / J.tmcP) : 0;
     unsigned mx = 0;
     float mxf = 0.f;
     int cnt = 0;       // boxes staged by this warp
@@ -529,8 +536,8 @@ __device__ __forceinline__ void fx_epilogue(const TcJob &J, const FxConsts &k, u
                     const uint32_t src = smem_u32(stg + i * bbytes);
                     // boxes of a group are `step` columns apart
                     const int cb = (int)(pcol + (int64_t)i * step);
-                    if (J.tmc == 3) tma_store_3d(tmC, src, (int)(rw0 % J.tmcP), cb, (int)(rw0 / J.tmcP));
-                    else tma_store_2d(tmC, src, cb, (int)rw0);
+                    if (J.tmc == 3) tma_store_3d(tmC, src, trow, cb, tslab);
+                    else tma_store_2d(tmC, src, cb, trow);
                 }
                 bulk_commit();
             }
@@ -678,11 +685,14 @@ __device__ __forceinline__ bool fx_epi_tile(const TcLaunch &L, int t, int it, ui
     const int64_t rg = (int64_t)mt * kBM + q * 32 + lane;
     const int64_t ro = rg < J.M ? imap(J.rowC, rg) : -1;
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * Regions<F>::N) * ACOLS;
+    // one column tile per job and one table: the table still holds the
+    // words of the previous tile when that was of the same job
+    const bool fill = k.j != j || J.tiles_n > 1 || NBUF > 1;
     fx_consts<F>(J, j, k);
     if (J.cfix && lead && lane == 0) J.fxC->e = k.eC;
     const bool staged = stg != nullptr && J.tmc != 0;
     fx_epilogue<F>(J, k, lane_base, ACOLS, ro, (int64_t)nt * J.BN, lane, part, nparts, staged ? stg : nullptr,
-                &job_at(L, j).tmC, (int64_t)mt * kBM + q * 32, colt + buf * 256);
+                &job_at(L, j).tmC, (int64_t)mt * kBM + q * 32, colt + buf * 256, fill);
     tc_fence_before();
     __syncwarp();
     if (lane == 0) mbar_arrive(smem_u32(&acce[buf]));
