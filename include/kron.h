@@ -408,6 +408,26 @@ KRON_API kron_status kron_expkronsum_apply(kron_plan plan, const double *const *
                                   int nsteps, void *U, void *ws, size_t ws_bytes,
                                   kron_stream_t stream);
 
+/*
+ * kron_expkronsum_step for a state held in host memory (an addition for
+ * callers whose data lives on the host; the paper's operation is the one
+ * above).  U_in: host, sizes n, the plan's dtype, column-major; it is copied
+ * into the device buffer U_dev (same size, the caller's), the steps run on
+ * U_dev as in kron_expkronsum_step, and the result is copied to U_out (host;
+ * may be U_in).  The copy to the device runs on a stream of the library's
+ * own (one per device), forked from `stream` after its earlier work and
+ * joined back before the state is first read, so it overlaps the
+ * exponentials and the images of E when U_in is page-locked; from pageable
+ * memory the copy is not asynchronous.  The call only enqueues: U_out is
+ * complete, and U_in and U_dev may be reused, once `stream` has completed.
+ * Errors: KRON_ERR_INVALID_ARG for null pointers, KRON_ERR_ALIGNMENT for an
+ * unaligned U_dev, otherwise those of kron_expkronsum_step.
+ */
+KRON_API kron_status kron_expkronsum_step_host(kron_plan plan, const double *const *A,
+                                      const int64_t *ldA, double tau, int nsteps,
+                                      const void *U_in, void *U_out, void *U_dev, void *ws,
+                                      size_t ws_bytes, kron_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Batched Tucker operators (Section 3.2, Eq. (tensinterp); Section 4.3)     */
 /* ------------------------------------------------------------------------ */

@@ -93,6 +93,8 @@ _sig("kron_expm", [ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_double, _vp, _v
 _sig("kron_expkronsum_workspace_size", [_vp, ctypes.POINTER(_sz)])
 _sig("kron_expkronsum_step", [_vp, ctypes.POINTER(_vp), _i64p, ctypes.c_double, _ci, _vp, _vp, _sz, _vp])
 _sig("kron_expkronsum_apply", [_vp, ctypes.POINTER(_vp), _i64p, _ci, _vp, _vp, _sz, _vp])
+_sig("kron_expkronsum_step_host", [_vp, ctypes.POINTER(_vp), _i64p, ctypes.c_double, _ci, _vp, _vp, _vp, _vp, _sz,
+                                   _vp])
 _sig("kron_batched_plan_create", [ctypes.POINTER(_vp), _ci, _ci, _i64p, _i64p, _ci, _ci, ctypes.c_uint])
 _sig("kron_batched_plan_destroy", [_vp])
 _sig("kron_batched_workspace_size", [_vp, ctypes.POINTER(_sz)])
@@ -113,7 +115,7 @@ EXPORTS = [
     "kron_gauss_hermite", "kron_gauss_laguerre", "kron_hermite_functions", "kron_laguerre_functions",
     "kron_fourier_resample", "kron_kronsumv_workspace_size", "kron_kronsumv", "kron_itucker_workspace_size", "kron_itucker", "kron_kronsum_pcg_workspace_size", "kron_kronsum_pcg", "kron_adjoint_workspace_size",
     "kron_tucker_adjoint", "kron_expm_workspace_size", "kron_expm",
-    "kron_expkronsum_workspace_size", "kron_expkronsum_step", "kron_expkronsum_apply",
+    "kron_expkronsum_workspace_size", "kron_expkronsum_step", "kron_expkronsum_apply", "kron_expkronsum_step_host",
     "kron_batched_plan_create", "kron_batched_plan_destroy", "kron_batched_workspace_size",
     "kron_batched_flops", "kron_batched_bind", "kron_batched_run",
     "kron_tucker_batched_workspace_size", "kron_tucker_batched", "kron_batched_autotune", "kron_batched_tuning",
@@ -187,6 +189,11 @@ def colmajor_strides(shape):
 def is_colmajor(t: torch.Tensor) -> bool:
     return all(t.stride(k) == s or t.shape[k] == 1
                for k, s in enumerate(colmajor_strides(t.shape)))
+
+
+def pinned_colmajor(shape, dtype=torch.float64) -> torch.Tensor:
+    """Page-locked host tensor with column-major strides (for step_host)."""
+    return torch.empty_strided(tuple(int(s) for s in shape), colmajor_strides(shape), dtype=dtype, pin_memory=True)
 
 
 def colmajor(t: torch.Tensor) -> torch.Tensor:
@@ -637,6 +644,32 @@ class StepperPlan:
                                          _i64([ld for _, ld in mats]), float(tau), int(nsteps), U.data_ptr(),
                                          ws.data_ptr(), ws.numel(), _stream(stream)), "kron_expkronsum_step")
         return U
+
+    def step_host(self, U_in, As, tau: float, nsteps: int, U_out=None, U_dev=None, ws=None, stream=None):
+        """nsteps steps of a host state: U_in (CPU, column-major, best page-locked)
+        is copied to U_dev while the exponentials are computed, the steps run
+        there, and the result lands in U_out (CPU; default U_in).  Enqueued on
+        `stream`: U_out is complete once the stream is."""
+        _require_cuda(*As)
+        if U_in.is_cuda or (U_out is not None and U_out.is_cuda):
+            raise ValueError("step_host takes host tensors U_in / U_out")
+        U_out = U_in if U_out is None else U_out
+        if not (is_colmajor(U_in) and is_colmajor(U_out)):
+            raise ValueError("step_host takes column-major host tensors (see pinned_colmajor)")
+        if U_out.shape != U_in.shape or U_out.dtype != U_in.dtype:
+            raise ValueError("U_out must match U_in")
+        dev = As[0].device
+        if U_dev is None:
+            U_dev = empty_colmajor(U_in.shape, U_in.dtype, dev)
+        mats = [_mat(A) for A in As]
+        if ws is None:
+            ws = self.workspace(dev)
+        _check(_lib.kron_expkronsum_step_host(self.plan.handle, _ptrs([A for A, _ in mats]),
+                                              _i64([ld for _, ld in mats]), float(tau), int(nsteps),
+                                              ctypes.c_void_p(U_in.data_ptr()), ctypes.c_void_p(U_out.data_ptr()),
+                                              ctypes.c_void_p(U_dev.data_ptr()), ws.data_ptr(), ws.numel(),
+                                              _stream(stream)), "kron_expkronsum_step_host")
+        return U_out
 
     def apply(self, U, Es, nsteps: int, ws=None, stream=None):
         """nsteps steps with given FP64 E_mu = exp(tau A_mu)."""

@@ -4,6 +4,7 @@
 // Every step of the computation runs in the kernels of tc.cu / simt.cu /
 // expm.cu / batched.cu; this file only decides what to launch.
 #include <algorithm>
+#include <mutex>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -1364,8 +1365,10 @@ StepLayout step_layout(const kron_plan_s *pl) {
 // Fixed-point stepper: U (float) -> fixed point once, then every mode
 // product fixed point -> fixed point (state ping-pong), the last one back to
 // the storage type.
+// state_ready: when not null, an event the stream waits for before U is first
+// read (the exponentials' images do not need U and go ahead of it).
 kron_status run_steps_fx(const kron_plan_s *pl, const double *const *E, const int64_t *ldE, int nsteps, void *U,
-                         uint8_t *w, const StepLayout &lay, cudaStream_t cs) {
+                         uint8_t *w, const StepLayout &lay, cudaStream_t cs, cudaEvent_t state_ready) {
     const int d = pl->d;
     const bool io64 = pl->dtype == KRON_F64;
     const int total = nsteps * d;
@@ -1390,6 +1393,7 @@ kron_status run_steps_fx(const kron_plan_s *pl, const double *const *E, const in
             return KRON_ERR_CUDA;
     }
     const int64_t N = prod(pl->n, 0, d);
+    if (state_ready && cudaStreamWaitEvent(cs, state_ready, 0) != cudaSuccess) return KRON_ERR_CUDA;
     if (fx_from_float(form, U, io64, N, reinterpret_cast<int32_t *>(w + lay.st[0]), &sc[0], scratch, cs) !=
         cudaSuccess)
         return KRON_ERR_CUDA;
@@ -1425,8 +1429,8 @@ kron_status check_step_plan(const kron_plan_s *pl) {
 }
 
 kron_status run_steps(const kron_plan_s *pl, const double *const *E, const int64_t *ldE, int nsteps, void *U,
-                      uint8_t *w, const StepLayout &lay, cudaStream_t cs) {
-    if (is_fx(pl->prec)) return run_steps_fx(pl, E, ldE, nsteps, U, w, lay, cs);
+                      uint8_t *w, const StepLayout &lay, cudaStream_t cs, cudaEvent_t state_ready = nullptr) {
+    if (is_fx(pl->prec)) return run_steps_fx(pl, E, ldE, nsteps, U, w, lay, cs, state_ready);
     const int d = pl->d;
     const bool io64 = pl->dtype == KRON_F64;
     const bool split = is_split(pl->prec);
@@ -1442,6 +1446,7 @@ kron_status run_steps(const kron_plan_s *pl, const double *const *E, const int64
             if (tc_build_bimage(form, c, w + lay.img[k], cs) != cudaSuccess) return KRON_ERR_CUDA;
         }
     }
+    if (state_ready && cudaStreamWaitEvent(cs, state_ready, 0) != cudaSuccess) return KRON_ERR_CUDA;
     const void *src = U;
     bool src64 = io64;
     int sel = 0;
@@ -1503,8 +1508,27 @@ kron_status kron_expkronsum_apply(kron_plan plan, const double *const *E, const 
                      reinterpret_cast<cudaStream_t>(stream));
 }
 
-kron_status kron_expkronsum_step(kron_plan plan, const double *const *A, const int64_t *ldA, double tau,
-                                 int nsteps, void *U, void *ws, size_t ws_bytes, kron_stream_t stream) {
+}  // extern "C"
+
+namespace {
+
+// Copies of the host-state stepper: one stream per device, created on first
+// use, on which the state's host-to-device copy runs beside the exponentials.
+cudaStream_t copy_stream() {
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
+        streams[dev] = nullptr;
+    return streams[dev];
+}
+
+// kron_expkronsum_step with an optional event waited for before the state
+// is first read.
+kron_status expkronsum_step(kron_plan plan, const double *const *A, const int64_t *ldA, double tau, int nsteps,
+                            void *U, void *ws, size_t ws_bytes, cudaStream_t cs, cudaEvent_t state_ready) {
     if (!plan || !A || !ldA || !U || nsteps < 0) return KRON_ERR_INVALID_ARG;
     kron_status st = check_step_plan(plan);
     if (st != KRON_OK) return st;
@@ -1518,7 +1542,6 @@ kron_status kron_expkronsum_step(kron_plan plan, const double *const *A, const i
     st = check_ws(ws, ws_bytes, lay.total);
     if (st != KRON_OK) return st;
     auto *w = static_cast<uint8_t *>(ws);
-    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     const double *Ep[KRON_MAX_D];
     int64_t ldE[KRON_MAX_D];
     // the distinct A_mu, all exponentials in one launch
@@ -1546,7 +1569,51 @@ kron_status kron_expkronsum_step(kron_plan plan, const double *const *A, const i
         Ep[k] = Ek;
     }
     if (expm_pade13_batch(cnt, bn, bA, bld, tau, bE, bws, cs) != cudaSuccess) return KRON_ERR_CUDA;
-    return run_steps(plan, Ep, ldE, nsteps, U, w, lay, cs);
+    return run_steps(plan, Ep, ldE, nsteps, U, w, lay, cs, state_ready);
+}
+
+}  // namespace
+
+extern "C" {
+
+kron_status kron_expkronsum_step(kron_plan plan, const double *const *A, const int64_t *ldA, double tau,
+                                 int nsteps, void *U, void *ws, size_t ws_bytes, kron_stream_t stream) {
+    return expkronsum_step(plan, A, ldA, tau, nsteps, U, ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream),
+                           nullptr);
+}
+
+kron_status kron_expkronsum_step_host(kron_plan plan, const double *const *A, const int64_t *ldA, double tau,
+                                      int nsteps, const void *U_in, void *U_out, void *U_dev, void *ws,
+                                      size_t ws_bytes, kron_stream_t stream) {
+    if (!plan || !A || !ldA || !U_in || !U_out || !U_dev || nsteps < 0) return KRON_ERR_INVALID_ARG;
+    kron_status st = check_step_plan(plan);
+    if (st != KRON_OK) return st;
+    if (!aligned(U_dev, esize(plan->dtype))) return KRON_ERR_ALIGNMENT;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    cudaStream_t cp = copy_stream();
+    if (!cp) return KRON_ERR_CUDA;
+    const size_t bytes = (size_t)prod(plan->n, 0, plan->d) * esize(plan->dtype);
+    // fork: the copy into U_dev waits for the stream's earlier work (which
+    // may still use U_dev); join: the steps wait for the copy
+    cudaEvent_t fork = nullptr, join = nullptr;
+    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) return KRON_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventDestroy(fork);
+        return KRON_ERR_CUDA;
+    }
+    st = KRON_OK;
+    if (cudaEventRecord(fork, cs) != cudaSuccess || cudaStreamWaitEvent(cp, fork, 0) != cudaSuccess ||
+        cudaMemcpyAsync(U_dev, U_in, bytes, cudaMemcpyHostToDevice, cp) != cudaSuccess ||
+        cudaEventRecord(join, cp) != cudaSuccess)
+        st = KRON_ERR_CUDA;
+    if (st == KRON_OK) st = expkronsum_step(plan, A, ldA, tau, nsteps, U_dev, ws, ws_bytes, cs, join);
+    // a step that failed before waiting for the copy must still join it
+    if (st != KRON_OK) cudaStreamWaitEvent(cs, join, 0);
+    if (st == KRON_OK && cudaMemcpyAsync(U_out, U_dev, bytes, cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+        st = KRON_ERR_CUDA;
+    cudaEventDestroy(fork);
+    cudaEventDestroy(join);
+    return st;
 }
 
 }  // extern "C"

@@ -101,6 +101,18 @@ def test_call_validation_without_gpu(lib):
     assert lib.kron_plan_create(ctypes.byref(h), 2, _i64([3, 4]), _i64([3, 3]), 0, 0, 0) == 0
     assert lib.kron_expkronsum_workspace_size(h, ctypes.byref(ws)) == 1
     lib.kron_plan_destroy(h)
+    # host-state stepper: null host or device state, misaligned device state
+    # (checked before any copy is enqueued)
+    assert lib.kron_plan_create(ctypes.byref(h), 2, _i64([3, 3]), _i64([3, 3]), 0, 6, 0) == 0
+    A = (ctypes.c_void_p * 2)(8, 8)
+    p8 = ctypes.c_void_p(8)
+    args = (h, A, ld, ctypes.c_double(1e-3), 1)
+    tail = (ctypes.c_void_p(256), ctypes.c_size_t(1 << 20), None)
+    assert lib.kron_expkronsum_step_host(*args, None, p8, p8, *tail) == 1
+    assert lib.kron_expkronsum_step_host(*args, p8, None, p8, *tail) == 1
+    assert lib.kron_expkronsum_step_host(*args, p8, p8, None, *tail) == 1
+    assert lib.kron_expkronsum_step_host(*args, p8, p8, ctypes.c_void_p(12), *tail) == 3
+    lib.kron_plan_destroy(h)
     # the Kronecker-sum action needs a square plan, and V and S apart
     assert lib.kron_plan_create(ctypes.byref(h), 2, _i64([3, 4]), _i64([3, 3]), 0, 0, 0) == 0
     assert lib.kron_kronsumv_workspace_size(h, ctypes.byref(ws)) == 1

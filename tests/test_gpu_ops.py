@@ -277,3 +277,33 @@ def test_expm_random_matrix(kron):
     ref = oracle.expm_taylor(A, 0.37)
     E = kron.expm(to_dev(A), 0.37)
     assert rel_err(to_host(E), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fx32h", "3xtf32", "fp64"])
+def test_stepper_host_state_matches_device_state(kron, prec):
+    """kron_expkronsum_step_host (state copied in beside the exponentials,
+    copied back after the steps) gives the device-state stepper's bits, in
+    place and into a separate host buffer, and the oracle's values."""
+    import torch
+    import workloads as W
+    c = W.stepper(n=24, tau=1e-4, nsteps=3)
+    dev = torch.device("cuda")
+    A = [to_dev(a) for a in c.A]
+    plan = kron.StepperPlan([c.n] * 3, torch.float64, prec)
+    ws = plan.workspace(dev)
+    U_ref = plan.step(to_dev(c.U0), A, c.tau, c.nsteps, ws=ws)
+    torch.cuda.synchronize()
+    U_in = kron.pinned_colmajor(c.U0.shape)
+    U_in.copy_(torch.from_numpy(c.U0))
+    U_out = kron.pinned_colmajor(c.U0.shape)
+    plan.step_host(U_in, A, c.tau, c.nsteps, U_out=U_out, ws=ws)
+    torch.cuda.synchronize()
+    assert torch.equal(U_out, U_ref.cpu())
+    np.testing.assert_array_equal(U_in.numpy(), c.U0)  # the input is left as it was
+    plan.step_host(U_in, A, c.tau, c.nsteps, ws=ws)  # in place
+    torch.cuda.synchronize()
+    assert torch.equal(U_in, U_ref.cpu())
+    E = oracle.expm_tridiag_toeplitz(c.n, *c.tri, c.tau)
+    ref = oracle.expkronsum_steps(c.U0, [E] * 3, c.nsteps)
+    assert rel_err(U_out.numpy(), ref) <= tol(prec, 3 * c.n)
+    assert kron.device_error() == 0
