@@ -88,11 +88,6 @@ constexpr int kBM = 128;            // rows per tile (MMA M)
 
 __host__ __device__ __forceinline__ int64_t imap(const IdxMap &m, int64_t x) {
     if (m.R0 == 0) return x * m.s0;
-    if ((((uint64_t)x | (uint64_t)m.R0) >> 32) == 0) {
-        // both below 2^32: the 32-bit division (the 64-bit one is a long routine)
-        const uint32_t q = (uint32_t)x / (uint32_t)m.R0;
-        return (int64_t)((uint32_t)x - q * (uint32_t)m.R0) * m.s0 + (int64_t)q * m.s1;
-    }
     return (x % m.R0) * m.s0 + (x / m.R0) * m.s1;
 }
 

@@ -706,7 +706,10 @@ __device__ __forceinline__ bool fx_epi_tile(const TcLaunch &L, int t, int it, ui
     return true;
 }
 
-template <int F>
+// A64: some job reads an FP64 tensor (converted from registers); without it
+// the kernel holds only the staged FP32 path (a smaller kernel: launches of
+// many short jobs are bound by instruction fetch).
+template <int F, bool A64>
 __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant__ TcLaunch L) {
     using T = FT<F>;
     constexpr int BK = kRowBytes / T::ELEM;
@@ -989,9 +992,11 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
                 }
             } else {
                 auto none = []() { return true; };
-                ok = J.a64 ? conv_tile_loop<F, double>(J, mt, sA, A_ST, full, empty, S, g, lane, ct)
-                           : conv_tile_loop_raw<F>(J, tm, rfull, rc, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct, 1,
-                                                   none);
+                if (A64 && J.a64)
+                    ok = conv_tile_loop<F, double>(J, mt, sA, A_ST, full, empty, S, g, lane, ct);
+                else
+                    ok = conv_tile_loop_raw<F>(J, tm, rfull, rc, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct, 1,
+                                               none);
             }
         }
         if (ok) epi_prev();
@@ -1208,12 +1213,12 @@ static void pick_config(int form, int bn_max, int nkb_max, int &stages, int &nac
     smem = (size_t)stages * (a_st + b_st) + raw + extra;
 }
 
-template <int F>
+template <int F, bool A64>
 static cudaError_t launch_f(const TcLaunch &L, int grid, size_t smem, cudaStream_t st) {
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [&] {
-        attr = cudaFuncSetAttribute(tcp_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+        attr = cudaFuncSetAttribute(tcp_kernel<F, A64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
     });
     if (attr != cudaSuccess) return attr;
     cudaLaunchConfig_t cfg{};
@@ -1226,7 +1231,7 @@ static cudaError_t launch_f(const TcLaunch &L, int grid, size_t smem, cudaStream
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, tcp_kernel<F>, L);
+    return cudaLaunchKernelEx(&cfg, tcp_kernel<F, A64>, L);
 }
 
 static int num_sms() {
@@ -1269,12 +1274,14 @@ static cudaError_t tcp_launch(int form, const TcJob *jobs, int njobs, int total_
         if (e != cudaSuccess) return e;
     }
     const int grid = std::min(total_tiles, num_sms());
+    bool a64 = false;
+    for (int j = 0; j < njobs; ++j) a64 = a64 || jobs[j].a64 != 0;
     switch (form) {
-        case kTF32x3: return launch_f<kTF32x3>(L, grid, smem, st);
-        case kBF16x3: return launch_f<kBF16x3>(L, grid, smem, st);
-        case kBF16x6: return launch_f<kBF16x6>(L, grid, smem, st);
-        case kFX32: return launch_f<kFX32>(L, grid, smem, st);
-        case kFX32H: return launch_f<kFX32H>(L, grid, smem, st);
+        case kTF32x3: return a64 ? launch_f<kTF32x3, true>(L, grid, smem, st) : launch_f<kTF32x3, false>(L, grid, smem, st);
+        case kBF16x3: return a64 ? launch_f<kBF16x3, true>(L, grid, smem, st) : launch_f<kBF16x3, false>(L, grid, smem, st);
+        case kBF16x6: return a64 ? launch_f<kBF16x6, true>(L, grid, smem, st) : launch_f<kBF16x6, false>(L, grid, smem, st);
+        case kFX32: return launch_f<kFX32, false>(L, grid, smem, st);    // 32-bit integer sources only
+        case kFX32H: return launch_f<kFX32H, false>(L, grid, smem, st);
         default: return cudaErrorInvalidValue;
     }
 }
