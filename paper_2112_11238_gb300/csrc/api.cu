@@ -186,8 +186,8 @@ kron_status run_chain_fx(const kron_plan_s *pl, const void *T, const void *const
 
 // Size of the fused group of small modes that starts at chain step s (the
 // modes order[s], order[s] + 1, .. applied one after the other), 0 if none:
-// split forms and FP32, up to three modes (FP32: at least two), the largest
-// group whose sizes fit the fused kernel.  cur: the sizes before step s.  A group may not end with the
+// split forms and FP32, up to three modes (FP32: at least two, from a whole
+// slab), the largest group whose sizes fit the fused kernel.  cur: the sizes before step s.  A group may not end with the
 // chain's last step when that step accumulates into S.
 int chain_group(const kron_plan_s *pl, int s, const int64_t *cur, bool acc_last, GroupSpec &gs) {
     const bool fp32 = pl->prec == KRON_PREC_FP32;
@@ -206,7 +206,9 @@ int chain_group(const kron_plan_s *pl, int s, const int64_t *cur, bool acc_last,
             c.m[t] = cur[mu + t];
             c.n[t] = pl->n[mu + t];
         }
-        if (fp32 ? tcf_fits(c) : tcg_fits(form_of(pl->prec), c)) {
+        // FP32: only whole slabs (P = 1; the strided groups stream slower
+        // than the per-mode kernel)
+        if (fp32 ? (c.P == 1 && tcf_fits(c)) : tcg_fits(form_of(pl->prec), c)) {
             gs = c;
             return gg;
         }

@@ -155,7 +155,7 @@ def test_plan_launches_group_small_modes(lib):
     """Which mode products run fused (host logic): the d=6 n=m=20 chain of a
     split form with FP32 storage runs as groups {1,2,3}, {4,5}, {6}; FP64
     storage cannot start a group (the fused kernel reads FP32), FP32 groups
-    the same way on the CUDA cores (two modes or more), FP64, the fixed-point forms and the
+    on the CUDA cores (two modes or more, from a whole slab), FP64, the fixed-point forms and the
     unfused flag run one product per launch, and modes above 32 are never
     grouped."""
     def launches(m, n, dtype, prec, flags=0):
@@ -174,9 +174,10 @@ def test_plan_launches_group_small_modes(lib):
         assert g[0] == 1 and sum(g) == 6 and max(g) >= 2
     for prec in (0, 5, 6):  # FP64, FX32, FX32H
         assert launches(d6, d6, 1, prec) == [1] * 6
-    # FP32 (CUDA cores): groups of two or three only
-    assert launches(d6, d6, 1, 1) == [3, 2, 1]
-    assert launches([40, 20, 20], [40, 20, 20], 1, 1) == [1, 2]
+    # FP32 (CUDA cores): groups of two or three modes from a whole slab only
+    assert launches(d6, d6, 1, 1) == [3, 1, 1, 1]
+    assert launches([20, 20, 40], [20, 20, 40], 1, 1) == [2, 1]
+    assert launches([40, 20, 20], [40, 20, 20], 1, 1) == [1, 1, 1]
     assert launches([20, 40, 20], [20, 40, 20], 1, 1) == [1, 1, 1]
     assert launches([40, 40, 40], [40, 40, 40], 1, 2) == [1, 1, 1]
     assert launches([40, 20, 20], [40, 20, 20], 1, 2, 0x2) == [1, 2]
