@@ -361,22 +361,41 @@ __global__ void bimage_kernel(const Tin *__restrict__ B, IdxMap colB, IdxMap kB,
 }
 
 // Fixed-order sum of split-K partials: C[r, c] (+)= sum_z P[z][r + M c].
-__global__ void splitk_reduce_kernel(const float *__restrict__ P, int64_t splits, int64_t M, int64_t N,
-                                     void *C, IdxMap rowC, IdxMap colC, int c64, int acc) {
+// Sum of the split-K partials, in FP64 and in a fixed order (deterministic):
+// a block takes 32 consecutive outputs; its thread (o, g) sums the splits
+// z = g, g + 32, .. of output o in ascending z (loads of a warp: 32
+// consecutive outputs of one split), then the 32 sums of an output are
+// added in ascending g.
+constexpr int kRedOut = 32, kRedGroups = 32;
+
+__global__ void __launch_bounds__(kRedOut * kRedGroups) splitk_reduce_kernel(const float *__restrict__ P,
+                                                                             int64_t splits, int64_t M, int64_t N,
+                                                                             void *C, IdxMap rowC, IdxMap colC,
+                                                                             int c64, int acc) {
+    __shared__ double part[kRedGroups][kRedOut + 1];
     const int64_t total = M * N;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
+    const int o = threadIdx.x % kRedOut, g = threadIdx.x / kRedOut;
+    for (int64_t base = (int64_t)blockIdx.x * kRedOut; base < total; base += (int64_t)gridDim.x * kRedOut) {
+        const int64_t idx = base + o;
         double s = 0.0;
-        for (int64_t z = 0; z < splits; ++z) s += (double)P[z * total + idx];
-        const int64_t r = idx % M, c = idx / M;
-        const int64_t off = imap(rowC, r) + imap(colC, c);
-        if (c64) {
-            double *d = static_cast<double *>(C) + off;
-            *d = acc ? *d + s : s;
-        } else {
-            float *d = static_cast<float *>(C) + off;
-            *d = acc ? (float)((double)*d + s) : (float)s;
+        if (idx < total)
+            for (int64_t z = g; z < splits; z += kRedGroups) s += (double)P[z * total + idx];
+        part[g][o] = s;
+        __syncthreads();
+        if (g == 0 && idx < total) {
+            double t = 0.0;
+            for (int h = 0; h < kRedGroups; ++h) t += part[h][o];
+            const int64_t r = idx % M, c = idx / M;
+            const int64_t off = imap(rowC, r) + imap(colC, c);
+            if (c64) {
+                double *d = static_cast<double *>(C) + off;
+                *d = acc ? *d + t : t;
+            } else {
+                float *d = static_cast<float *>(C) + off;
+                *d = acc ? (float)((double)*d + t) : (float)t;
+            }
         }
+        __syncthreads();
     }
 }
 
@@ -588,10 +607,9 @@ cudaError_t tc_contract_splitk(int form, const Contraction &c, float *partial, c
     cudaError_t e = dispatch_form(form, d, kcontig(c.kA), false, kcontig(c.kB), grid, smem, st);
     if (e != cudaSuccess) return e;
     const int64_t total = c.M * c.N;
-    const int threads = 256;
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((total + threads - 1) / threads, 4096));
-    splitk_reduce_kernel<<<(unsigned)blocks, threads, 0, st>>>(partial, splits, c.M, c.N, c.C, c.rowC,
-                                                               c.colC, c.C_f64, c.accumulate);
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((total + kRedOut - 1) / kRedOut, 4096));
+    splitk_reduce_kernel<<<(unsigned)blocks, kRedOut * kRedGroups, 0, st>>>(partial, splits, c.M, c.N, c.C, c.rowC,
+                                                                            c.colC, c.C_f64, c.accumulate);
     return cudaGetLastError();
 }
 
