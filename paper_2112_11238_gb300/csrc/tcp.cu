@@ -706,9 +706,10 @@ __device__ __forceinline__ bool fx_epi_tile(const TcLaunch &L, int t, int it, ui
     return true;
 }
 
-// A64: some job reads an FP64 tensor (converted from registers); without it
-// the kernel holds only the staged FP32 path (a smaller kernel: launches of
-// many short jobs are bound by instruction fetch).
+// A64 (wide): some job reads an FP64 tensor (converted from registers),
+// writes FP64 or accumulates into C; without it the kernel holds only the
+// staged FP32 path and plain FP32 stores (a smaller kernel: launches of many
+// short jobs are bound by instruction fetch).
 template <int F, bool A64>
 __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant__ TcLaunch L) {
     using T = FT<F>;
@@ -899,8 +900,10 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
                         float s16[16];
 #pragma unroll
                         for (int e = 0; e < 16; ++e) s16[e] = __uint_as_float(h[16 * hh + e]);
-                        if (J.c64) store_row16<double>(J.C, ro, J.colC, n0 + c0 + 16 * hh, cmax, s16, J.acc != 0);
-                        else store_row16<float>(J.C, ro, J.colC, n0 + c0 + 16 * hh, cmax, s16, J.acc != 0);
+                        if (A64 && J.c64)
+                            store_row16<double>(J.C, ro, J.colC, n0 + c0 + 16 * hh, cmax, s16, J.acc != 0);
+                        else
+                            store_row16<float>(J.C, ro, J.colC, n0 + c0 + 16 * hh, cmax, s16, A64 && J.acc != 0);
                     }
                 }
             }
@@ -1274,8 +1277,8 @@ static cudaError_t tcp_launch(int form, const TcJob *jobs, int njobs, int total_
         if (e != cudaSuccess) return e;
     }
     const int grid = std::min(total_tiles, num_sms());
-    bool a64 = false;
-    for (int j = 0; j < njobs; ++j) a64 = a64 || jobs[j].a64 != 0;
+    bool a64 = false;  // the wide build: FP64 sources, FP64 outputs or accumulation
+    for (int j = 0; j < njobs; ++j) a64 = a64 || jobs[j].a64 != 0 || jobs[j].c64 != 0 || jobs[j].acc != 0;
     switch (form) {
         case kTF32x3: return a64 ? launch_f<kTF32x3, true>(L, grid, smem, st) : launch_f<kTF32x3, false>(L, grid, smem, st);
         case kBF16x3: return a64 ? launch_f<kBF16x3, true>(L, grid, smem, st) : launch_f<kBF16x3, false>(L, grid, smem, st);
