@@ -290,7 +290,7 @@ __device__ __forceinline__ void raw_issue(const TcJob &J, const int64_t (&base)[
 // Float sources: raw tiles arrive through cp.async several K-blocks ahead;
 // the converters split them from shared memory.
 // fmul: 2^(left shift) of a fixed-point A (fx_shift of its scale word).
-template <int F, typename Join>
+template <int F, bool TMA_OK, typename Join>
 __device__ __forceinline__ bool conv_tile_loop_raw(const TcJob &J, const CUtensorMap *tm, uint64_t *rfull,
                                                    uint32_t &rc, int mt, uint8_t *sA, uint32_t A_ST, uint8_t *sRaw,
                                                    uint64_t *full, uint64_t *empty, int S, uint32_t &g, int lane,
@@ -299,7 +299,7 @@ __device__ __forceinline__ bool conv_tile_loop_raw(const TcJob &J, const CUtenso
     constexpr int BK = R::BK;
     constexpr int CH = 16 / FT<F>::ELEM;
     const bool kc = J.akc != 0;
-    const bool tma = J.tma != 0;
+    const bool tma = TMA_OK && J.tma != 0;
     // per-unit source offsets (rows fixed over the tile)
     const int64_t row0 = (int64_t)mt * kBM;
     // TMA coordinates of the tile's rows (slab layout: row in slab, slab)
@@ -706,12 +706,14 @@ __device__ __forceinline__ bool fx_epi_tile(const TcLaunch &L, int t, int it, ui
     return true;
 }
 
-// A64 (wide): some job reads an FP64 tensor (converted from registers),
-// writes FP64 or accumulates into C; without it the kernel holds only the
-// staged FP32 path and plain FP32 stores (a smaller kernel: launches of many
-// short jobs are bound by instruction fetch).
-template <int F, bool A64>
+// MODE (split forms; the fixed-point forms take 1): 2 = wide, some job reads
+// an FP64 tensor (converted from registers), writes FP64 or accumulates into
+// C; 1 = FP32 sources staged by TMA or cp.async, plain FP32 stores; 0 = as 1
+// with cp.async staging only.  The smaller builds serve launches of many short
+// jobs, which are bound by instruction fetch.
+template <int F, int MODE>
 __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant__ TcLaunch L) {
+    constexpr bool A64 = MODE == 2;
     using T = FT<F>;
     constexpr int BK = kRowBytes / T::ELEM;
     constexpr uint32_t PIECE_A = kBM * kRowBytes;
@@ -987,7 +989,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
                 named_bar(2, 32 * kConv);
             }
             if constexpr (is_fx_f<F>()) {  // always 32-bit integers
-                ok = conv_tile_loop_raw<F>(J, tm, rfull, rc, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct, fmul,
+                ok = conv_tile_loop_raw<F, true>(J, tm, rfull, rc, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct, fmul,
                                            epi_prev);
                 if (join) {
                     pend = t;
@@ -998,7 +1000,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tcp_kernel(const __grid_constant
                 if (A64 && J.a64)
                     ok = conv_tile_loop<F, double>(J, mt, sA, A_ST, full, empty, S, g, lane, ct);
                 else
-                    ok = conv_tile_loop_raw<F>(J, tm, rfull, rc, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct, 1,
+                    ok = conv_tile_loop_raw<F, MODE >= 1>(J, tm, rfull, rc, mt, sA, A_ST, sRaw, full, empty, S, g, lane, ct, 1,
                                                none);
             }
         }
@@ -1216,12 +1218,12 @@ static void pick_config(int form, int bn_max, int nkb_max, int &stages, int &nac
     smem = (size_t)stages * (a_st + b_st) + raw + extra;
 }
 
-template <int F, bool A64>
+template <int F, int MODE>
 static cudaError_t launch_f(const TcLaunch &L, int grid, size_t smem, cudaStream_t st) {
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [&] {
-        attr = cudaFuncSetAttribute(tcp_kernel<F, A64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+        attr = cudaFuncSetAttribute(tcp_kernel<F, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
     });
     if (attr != cudaSuccess) return attr;
     cudaLaunchConfig_t cfg{};
@@ -1234,7 +1236,7 @@ static cudaError_t launch_f(const TcLaunch &L, int grid, size_t smem, cudaStream
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, tcp_kernel<F, A64>, L);
+    return cudaLaunchKernelEx(&cfg, tcp_kernel<F, MODE>, L);
 }
 
 static int num_sms() {
@@ -1277,14 +1279,24 @@ static cudaError_t tcp_launch(int form, const TcJob *jobs, int njobs, int total_
         if (e != cudaSuccess) return e;
     }
     const int grid = std::min(total_tiles, num_sms());
-    bool a64 = false;  // the wide build: FP64 sources, FP64 outputs or accumulation
-    for (int j = 0; j < njobs; ++j) a64 = a64 || jobs[j].a64 != 0 || jobs[j].c64 != 0 || jobs[j].acc != 0;
+    bool wide = false, tma = false;  // the build: FP64 sources, FP64 outputs or accumulation; TMA staging
+    for (int j = 0; j < njobs; ++j) {
+        wide = wide || jobs[j].a64 != 0 || jobs[j].c64 != 0 || jobs[j].acc != 0;
+        tma = tma || jobs[j].tma != 0;
+    }
+    const int mode = wide ? 2 : (tma ? 1 : 0);
     switch (form) {
-        case kTF32x3: return a64 ? launch_f<kTF32x3, true>(L, grid, smem, st) : launch_f<kTF32x3, false>(L, grid, smem, st);
-        case kBF16x3: return a64 ? launch_f<kBF16x3, true>(L, grid, smem, st) : launch_f<kBF16x3, false>(L, grid, smem, st);
-        case kBF16x6: return a64 ? launch_f<kBF16x6, true>(L, grid, smem, st) : launch_f<kBF16x6, false>(L, grid, smem, st);
-        case kFX32: return launch_f<kFX32, false>(L, grid, smem, st);    // 32-bit integer sources only
-        case kFX32H: return launch_f<kFX32H, false>(L, grid, smem, st);
+#define KRON_TCP_SPLIT(FORM)                                                       \
+    case FORM:                                                                     \
+        return mode == 2 ? launch_f<FORM, 2>(L, grid, smem, st)                   \
+                         : (mode == 1 ? launch_f<FORM, 1>(L, grid, smem, st)      \
+                                      : launch_f<FORM, 0>(L, grid, smem, st));
+        KRON_TCP_SPLIT(kTF32x3)
+        KRON_TCP_SPLIT(kBF16x3)
+        KRON_TCP_SPLIT(kBF16x6)
+#undef KRON_TCP_SPLIT
+        case kFX32: return launch_f<kFX32, 1>(L, grid, smem, st);    // 32-bit integer sources only
+        case kFX32H: return launch_f<kFX32H, 1>(L, grid, smem, st);
         default: return cudaErrorInvalidValue;
     }
 }
