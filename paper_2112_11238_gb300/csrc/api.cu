@@ -227,6 +227,34 @@ kron_status run_chain(const kron_plan_s *pl, const void *T, const void *const *L
     const bool i64 = pl->prec == KRON_PREC_FP64;
     int64_t cur[KRON_MAX_D];
     for (int k = 0; k < d; ++k) cur[k] = pl->m[k];
+    if (split) {
+        // the images of every op(L_mu) the chain uses, in one launch: the
+        // chain's steps are walked once ahead (fused group: 32-column tiles)
+        Contraction ic[KRON_MAX_D];
+        void *iimg[KRON_MAX_D];
+        int ibn[KRON_MAX_D];
+        int cnt = 0;
+        int64_t pc[KRON_MAX_D];
+        for (int k = 0; k < d; ++k) pc[k] = pl->m[k];
+        bool p64 = io64;
+        for (int s = 0; s < d;) {
+            GroupSpec gs;
+            const int gsz = !p64 ? chain_group(pl, s, pc, acc_last, gs) : 0;
+            const int steps = gsz > 0 ? gsz : 1;
+            for (int t = 0; t < steps; ++t) {
+                const int nu = pl->order[s + t];
+                ic[cnt] = tc_mode_contraction(mode_geom(d, pc, nu, pl->n[nu]), nullptr, false, L[nu], io64, ldL[nu],
+                                              trans, nullptr, false);
+                iimg[cnt] = ws + pl->img_off[nu];
+                ibn[cnt] = gsz > 0 ? kTcgBN : tc_tile_n(form, pl->n[nu]);
+                ++cnt;
+                pc[nu] = pl->n[nu];
+            }
+            s += steps;
+            p64 = (s == d) ? io64 : false;
+        }
+        if (tc_build_bimages(form, cnt, ic, iimg, ibn, st) != cudaSuccess) return KRON_ERR_CUDA;
+    }
     const void *src = T;
     bool src64 = io64;
     int writes = 0;  // intermediates written so far (ping-pong buffers)
@@ -262,15 +290,6 @@ kron_status run_chain(const kron_plan_s *pl, const void *T, const void *const *L
             const bool last = (s + gsz == d);
             void *dst = last ? S : (void *)(ws + pl->buf_off[writes & 1]);
             const bool dst64 = last ? io64 : false;
-            for (int t = 0; t < gsz; ++t) {
-                const int nu = mu + t;
-                int64_t gc[KRON_MAX_D];
-                for (int k = 0; k < d; ++k) gc[k] = cur[k];
-                for (int k = 0; k < t; ++k) gc[mu + k] = pl->n[mu + k];
-                const ModeGeom gt = mode_geom(d, gc, nu, pl->n[nu]);
-                Contraction c = tc_mode_contraction(gt, nullptr, false, L[nu], io64, ldL[nu], trans, nullptr, false);
-                if (tc_build_bimage_bn(form, c, ws + pl->img_off[nu], kTcgBN, st) != cudaSuccess) return KRON_ERR_CUDA;
-            }
             if (tcg_run(form, gs, static_cast<const float *>(src), dst, dst64, st) != cudaSuccess) return KRON_ERR_CUDA;
             for (int t = 0; t < gsz; ++t) cur[mu + t] = pl->n[mu + t];
             src = dst;
@@ -286,9 +305,7 @@ kron_status run_chain(const kron_plan_s *pl, const void *T, const void *const *L
         if (split) {
             Contraction c = tc_mode_contraction(g, src, src64, L[mu], io64, ldL[mu], trans, dst, dst64);
             c.accumulate = last && acc_last;
-            void *img = ws + pl->img_off[mu];
-            e = tc_build_bimage(form, c, img, st);
-            if (e == cudaSuccess) e = tcp_contract(form, c, img, st);
+            e = tcp_contract(form, c, ws + pl->img_off[mu], st);  // image built above
         } else if (simt_small_fits(i64, g.m, g.n)) {
             // small factor: one thread per fibre, op(L) in shared memory
             Contraction c = tc_mode_contraction(g, src, src64, L[mu], io64, ldL[mu], trans, dst, dst64);

@@ -79,6 +79,11 @@ int tc_tile_n_cap(int form, int64_t N, int cap);
 cudaError_t tc_build_bimage(int form, const Contraction &c, void *img, cudaStream_t st);
 // the same image for N-tiles of width bn (tc_bimage_bytes_bn long)
 cudaError_t tc_build_bimage_bn(int form, const Contraction &c, void *img, int bn, cudaStream_t st);
+// The images of count (<= KRON_MAX_D) contractions' B operands in one launch,
+// image j with N-tile bns[j] into imgs[j]; the same bytes as
+// tc_build_bimage_bn builds for each.
+cudaError_t tc_build_bimages(int form, int count, const Contraction *cs, void *const *imgs, const int *bns,
+                             cudaStream_t st);
 // C = A * B with the B operand from an image made by tc_build_bimage.
 cudaError_t tc_contract_bimage(int form, const Contraction &c, const void *img, cudaStream_t st);
 // Split-K contraction with both operands converted on load (the adjoint's

@@ -360,6 +360,49 @@ __global__ void bimage_kernel(const Tin *__restrict__ B, IdxMap colB, IdxMap kB,
     }
 }
 
+// Several images in one launch (up to KRON_MAX_D), the same bytes as
+// bimage_kernel builds for each: the items of image j follow those of j - 1.
+struct BimageSet {
+    const void *B[KRON_MAX_D];
+    IdxMap colB[KRON_MAX_D], kB[KRON_MAX_D];
+    int64_t N[KRON_MAX_D], K[KRON_MAX_D], KB[KRON_MAX_D], begin[KRON_MAX_D + 1];
+    uint8_t *img[KRON_MAX_D];
+    int BN[KRON_MAX_D], b64[KRON_MAX_D];
+    int count;
+};
+
+template <int F>
+__global__ void bimage_set_kernel(const __grid_constant__ BimageSet S) {
+    using T = FT<F>;
+    constexpr int BK = kRowBytes / T::ELEM;
+    constexpr int CH = 16 / T::ELEM;
+    const int64_t total = S.begin[S.count];
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int j = 0;
+        while (j + 1 < S.count && S.begin[j + 1] <= idx) ++j;
+        const int BN = S.BN[j];
+        const int64_t KB = S.KB[j];
+        int64_t rest = idx - S.begin[j];
+        const int ch = (int)(rest % kChunks);
+        rest /= kChunks;
+        const int row = (int)(rest % BN);
+        rest /= BN;
+        const int64_t kb = rest % KB;
+        const int64_t nt = rest / KB;
+        const int64_t cg = nt * BN + row;
+        const int64_t ro = cg < S.N[j] ? imap(S.colB[j], cg) : -1;
+        uint4 out[T::PIECES];
+        if (S.b64[j]) load_split<F, double>(static_cast<const double *>(S.B[j]), ro, S.kB[j], kb * BK + ch * CH, S.K[j], out);
+        else load_split<F, float>(static_cast<const float *>(S.B[j]), ro, S.kB[j], kb * BK + ch * CH, S.K[j], out);
+        uint8_t *base = S.img[j] + (size_t)((nt * KB + kb) * T::PIECES) * BN * kRowBytes;
+        const uint32_t off = swz(row, ch);
+#pragma unroll
+        for (int q = 0; q < T::PIECES; ++q)
+            *reinterpret_cast<uint4 *>(base + (size_t)q * BN * kRowBytes + off) = out[q];
+    }
+}
+
 // Fixed-order sum of split-K partials: C[r, c] (+)= sum_z P[z][r + M c].
 // Sum of the split-K partials, in FP64 and in a fixed order (deterministic):
 // a block takes 32 consecutive outputs; its thread (o, g) sums the splits
@@ -524,6 +567,39 @@ cudaError_t tc_build_bimage_bn(int form, const Contraction &c, void *img, int bn
         default: return cudaErrorInvalidValue;
     }
 #undef KRON_BIMG
+    return cudaGetLastError();
+}
+
+cudaError_t tc_build_bimages(int form, int count, const Contraction *cs, void *const *imgs, const int *bns,
+                             cudaStream_t st) {
+    if (count < 1) return cudaSuccess;
+    if (count > KRON_MAX_D) return cudaErrorInvalidValue;
+    BimageSet S{};
+    S.count = count;
+    S.begin[0] = 0;
+    for (int j = 0; j < count; ++j) {
+        const Contraction &c = cs[j];
+        const int bn = bns[j];
+        S.B[j] = c.B;
+        S.b64[j] = c.B_f64 ? 1 : 0;
+        S.colB[j] = c.colB;
+        S.kB[j] = c.kB;
+        S.N[j] = c.N;
+        S.K[j] = c.K;
+        S.KB[j] = (c.K + bk_of(form) - 1) / bk_of(form);
+        S.BN[j] = bn;
+        S.img[j] = static_cast<uint8_t *>(imgs[j]);
+        const int64_t nt = (c.N + bn - 1) / bn;
+        S.begin[j + 1] = S.begin[j] + nt * S.KB[j] * bn * kChunks;
+    }
+    const int threads = 256;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((S.begin[count] + threads - 1) / threads, 152 * 16));
+    switch (form) {
+        case kTF32x3: bimage_set_kernel<kTF32x3><<<(unsigned)blocks, threads, 0, st>>>(S); break;
+        case kBF16x3: bimage_set_kernel<kBF16x3><<<(unsigned)blocks, threads, 0, st>>>(S); break;
+        case kBF16x6: bimage_set_kernel<kBF16x6><<<(unsigned)blocks, threads, 0, st>>>(S); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
