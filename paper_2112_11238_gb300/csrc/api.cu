@@ -1109,7 +1109,7 @@ cudaError_t itucker_prepare(const kron_plan_s *plan, const void *const *P, const
                             const ItLayout &lay, const void **Li, int64_t *ldi, cudaStream_t cs) {
     const int d = plan->d;
     const bool io64 = plan->dtype == KRON_F64;
-    void *iws[KRON_MAX_D];
+    void *iws[KRON_MAX_D] = {};
     for (int k = 0; k < d; ++k) iws[k] = w + lay.inv[k];
     cudaError_t e = inv_gj_batch(d, plan->n, P, ldP, io64, iws, cs);
     for (int k = 0; k < d && e == cudaSuccess; ++k) {

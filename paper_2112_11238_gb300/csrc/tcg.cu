@@ -66,7 +66,6 @@ struct GLaunch {
     uint32_t etab_off[3];    // per mode: table of the epilogue's per-row offsets (shared memory)
     int64_t estep[3];        // per mode: the offset's step per output column
     int kbmax;
-    int vec4;                // groups of four input elements are 16-byte aligned
     int bulk0;               // P = 1 and the slab copies as one bulk copy (16-byte multiple and aligned):
                              // mode 0's rows are then staged with pitch m_0 (the slab as it is)
 };
@@ -753,7 +752,6 @@ cudaError_t tcf_run(const GroupSpec &gs, const float *src, void *dst, bool dst64
     L.dst = dst;
     L.dst64 = dst64 ? 1 : 0;
     const bool base16 = (reinterpret_cast<uintptr_t>(src) & 15) == 0;
-    L.vec4 = base16 && ((L.P == 1 && L.Gin % 4 == 0) || (L.P > 1 && L.PB >= 4 && L.P % 4 == 0)) ? 1 : 0;
     L.bulk0 = (base16 && L.P == 1 && L.Gin % 4 == 0 && L.K[0] % 4 == 0) ? 1 : 0;
     return tcf_launch(L, smem, st);
 }
@@ -794,7 +792,6 @@ cudaError_t tcg_run(int form, const GroupSpec &gs, const float *src, void *dst, 
     // four consecutive elements of a group start 16-byte aligned: P = 1 with
     // slabs of a multiple of four, or p-blocks (PB >= 4) with P a multiple of four
     const bool base16 = (reinterpret_cast<uintptr_t>(src) & 15) == 0;
-    L.vec4 = base16 && ((L.P == 1 && L.Gin % 4 == 0) || (L.P > 1 && L.PB >= 4 && L.P % 4 == 0)) ? 1 : 0;
     L.bulk0 = (base16 && L.P == 1 && L.Gin % 4 == 0 && L.K[0] % 4 == 0) ? 1 : 0;
     switch (form) {
         case kTF32x3: return tcg_launch_f<kTF32x3>(L, smem, st);
