@@ -38,6 +38,12 @@ constexpr int kThreadsE = 256;  // = kT * kT
 constexpr int kNB = 16;         // Gauss-Jordan panel width
 constexpr int kWarpsE = kThreadsE / 32;
 
+// Tile maps: one byte per 16 x 16 tile of an n x n matrix, nonzero when the
+// tile may hold a nonzero (kFlagMats maps of kMaxTiles^2 bytes per problem).
+constexpr int kMaxTiles = 64;  // n <= 1024
+constexpr int kFlagMats = 8;
+constexpr size_t kFlagBytes = (size_t)kFlagMats * kMaxTiles * kMaxTiles;
+
 struct ExpmProb {
     int n;
     const double *A;
@@ -46,6 +52,7 @@ struct ExpmProb {
     double *w;           // workspace base (doubles)
     unsigned *bar;       // [0] count, [1] generation
     unsigned long long *norm_bits;
+    unsigned char *flags;  // kFlagMats tile maps
 };
 
 struct ExpmDev {
@@ -88,15 +95,24 @@ __device__ bool grid_sync(unsigned *bar, int gs) {
 
 // C = alpha * A * B + beta * C0 (+ gamma * I), all n x n with ld n.  C0 may
 // alias C; A and B must not.  Tiles are spread over the group (block lb of gs).
+// fa / fb: tile maps of A and B (null: dense); a K-step whose A or B tile is
+// all zero is skipped (it adds exact zeros: the polynomial of the banded
+// stepper matrices is banded).  fc: the map of C to write (null: none).
 __device__ void gemm(int n, double alpha, const double *A, const double *B, double beta,
-                     const double *C0, double gamma, double *C, int lb, int gs) {
+                     const double *C0, double gamma, double *C, int lb, int gs,
+                     const unsigned char *fa = nullptr, const unsigned char *fb = nullptr,
+                     unsigned char *fc = nullptr) {
     __shared__ double As[kT][kT + 1], Bs[kT][kT + 1];
     const int tiles = (n + kT - 1) / kT;
     const int tr = threadIdx.x % kT, tc = threadIdx.x / kT;
     for (int t = lb; t < tiles * tiles; t += gs) {
         const int i0 = (t % tiles) * kT, j0 = (t / tiles) * kT;
+        const int ti = t % tiles, tj = t / tiles;
         double acc = 0.0;
         for (int k0 = 0; k0 < n; k0 += kT) {
+            const int tk = k0 / kT;
+            // the same decision in every thread of the block (same bytes)
+            if (fa && (__ldcg(fa + ti + kMaxTiles * tk) == 0 || __ldcg(fb + tk + kMaxTiles * tj) == 0)) continue;
             const int ia = i0 + tr, ka = k0 + tc;
             As[tc][tr] = (ia < n && ka < n) ? A[ia + (int64_t)n * ka] : 0.0;
             const int kb = k0 + tr, jb = j0 + tc;
@@ -107,13 +123,29 @@ __device__ void gemm(int n, double alpha, const double *A, const double *B, doub
             __syncthreads();
         }
         const int i = i0 + tr, j = j0 + tc;
+        double v = 0.0;
         if (i < n && j < n) {
             const int64_t o = i + (int64_t)n * j;
-            double v = alpha * acc;
+            v = alpha * acc;
             if (beta != 0.0) v += beta * C0[o];
             if (i == j) v += gamma;
             C[o] = v;
         }
+        if (fc) {
+            const int nz = __syncthreads_or(v != 0.0);
+            if (threadIdx.x == 0) fc[ti + kMaxTiles * tj] = nz ? 1 : 0;
+        }
+    }
+}
+
+// Tile map of a combination of matrices: a tile may be nonzero where any
+// of theirs may, and on the diagonal when an identity term is added.
+__device__ void flag_union(int n, unsigned char *f, const unsigned char *f1, const unsigned char *f2,
+                           const unsigned char *f3, bool diag, int lb, int gs) {
+    const int tiles = (n + kT - 1) / kT;
+    for (int t = lb * blockDim.x + threadIdx.x; t < tiles * tiles; t += gs * blockDim.x) {
+        const int ti = t % tiles, tj = t / tiles, o = ti + kMaxTiles * tj;
+        f[o] = (f1[o] | f2[o] | f3[o] | (diag && ti == tj)) ? 1 : 0;
     }
 }
 
@@ -245,6 +277,12 @@ __global__ void __launch_bounds__(kThreadsE) expm_kernel(const __grid_constant__
     double *U = T2 + nn, *V = U + nn, *Q0 = V + nn, *P0 = Q0 + nn, *X = P0 + nn, *R = X + nn;
     double *G = R + nn;  // augmented [Q | P | I]: n x 3n, ld n
     __shared__ double red_v[kThreadsE];
+    const int tiles = (n + kT - 1) / kT;
+    unsigned char *fB = p.flags, *fB2 = fB + kMaxTiles * kMaxTiles, *fB4 = fB2 + kMaxTiles * kMaxTiles,
+                  *fB6 = fB4 + kMaxTiles * kMaxTiles, *fT = fB6 + kMaxTiles * kMaxTiles,
+                  *fR = fT + kMaxTiles * kMaxTiles;
+    for (int t = lb * blockDim.x + threadIdx.x; t < tiles * tiles; t += gs * blockDim.x)
+        fB[(t % tiles) + kMaxTiles * (t / tiles)] = 0;
 
     // ---- ||tau A||_1
     for (int j = lb; j < n; j += gs) {
@@ -268,14 +306,18 @@ __global__ void __launch_bounds__(kThreadsE) expm_kernel(const __grid_constant__
     int s = 0;
     if (nrm > d.theta) s = (int)ceil(log2(nrm / d.theta));
     const double scale = ldexp(d.tau, -s);
-    for (int64_t e = (int64_t)lb * blockDim.x + threadIdx.x; e < nn; e += (int64_t)gs * blockDim.x)
-        B[e] = scale * p.A[(e % n) + p.ldA * (e / n)];
+    for (int64_t e = (int64_t)lb * blockDim.x + threadIdx.x; e < nn; e += (int64_t)gs * blockDim.x) {
+        const double v = scale * p.A[(e % n) + p.ldA * (e / n)];
+        B[e] = v;
+        if (v != 0.0) fB[(int)((e % n) / kT) + kMaxTiles * (int)((e / n) / kT)] = 1;
+    }
     if (!grid_sync(p.bar, gs)) return;
-    gemm(n, 1.0, B, B, 0.0, nullptr, 0.0, B2, lb, gs);
+    // the polynomial's products skip the all-zero tiles of their operands
+    gemm(n, 1.0, B, B, 0.0, nullptr, 0.0, B2, lb, gs, fB, fB, fB2);
     if (!grid_sync(p.bar, gs)) return;
-    gemm(n, 1.0, B2, B2, 0.0, nullptr, 0.0, B4, lb, gs);
+    gemm(n, 1.0, B2, B2, 0.0, nullptr, 0.0, B4, lb, gs, fB2, fB2, fB4);
     if (!grid_sync(p.bar, gs)) return;
-    gemm(n, 1.0, B4, B2, 0.0, nullptr, 0.0, B6, lb, gs);
+    gemm(n, 1.0, B4, B2, 0.0, nullptr, 0.0, B6, lb, gs, fB4, fB2, fB6);
     if (!grid_sync(p.bar, gs)) return;
     const double *b = d.b;
     // T1 = b13 B6 + b11 B4 + b9 B2 ; T2 = b12 B6 + b10 B4 + b8 B2
@@ -284,11 +326,12 @@ __global__ void __launch_bounds__(kThreadsE) expm_kernel(const __grid_constant__
     // U' = B6 T1 + b7 B6 + b5 B4 + b3 B2 + b1 I  (into R as scratch first)
     lincomb(n, R, b[7], B6, b[5], B4, b[3], B2, b[1], lb, gs);
     lincomb(n, X, b[6], B6, b[4], B4, b[2], B2, b[0], lb, gs);
+    flag_union(n, fT, fB6, fB4, fB2, false, lb, gs);  // the map of T1 and of T2
     if (!grid_sync(p.bar, gs)) return;
-    gemm(n, 1.0, B6, T1, 1.0, R, 0.0, R, lb, gs);
-    gemm(n, 1.0, B6, T2, 1.0, X, 0.0, V, lb, gs);
+    gemm(n, 1.0, B6, T1, 1.0, R, 0.0, R, lb, gs, fB6, fT, fR);
+    gemm(n, 1.0, B6, T2, 1.0, X, 0.0, V, lb, gs, fB6, fT, nullptr);
     if (!grid_sync(p.bar, gs)) return;
-    gemm(n, 1.0, B, R, 0.0, nullptr, 0.0, U, lb, gs);
+    gemm(n, 1.0, B, R, 0.0, nullptr, 0.0, U, lb, gs, fB, fR, nullptr);
     if (!grid_sync(p.bar, gs)) return;
     // Q0 = V - U, P0 = V + U, augmented G = [Q0 | P0 | I]
     for (int64_t e = (int64_t)lb * blockDim.x + threadIdx.x; e < nn; e += (int64_t)gs * blockDim.x) {
@@ -369,8 +412,9 @@ void pade13(double *b) {
 cudaError_t expm_error_word(unsigned int *out, bool clear, cudaStream_t st) { return read_error_word(out, clear, st); }
 
 size_t expm_workspace_bytes(int64_t n) {
-    // 13 n x n matrices + the n x 3n augmented matrix + barrier/norm words
-    return (size_t)(16 * n * n) * sizeof(double) + 256;
+    // 13 n x n matrices + the n x 3n augmented matrix + barrier/norm words +
+    // the tile maps
+    return (size_t)(16 * n * n) * sizeof(double) + 256 + kFlagBytes;
 }
 
 cudaError_t expm_pade13_batch(int count, const int64_t *n, const double *const *A, const int64_t *ldA, double tau,
@@ -392,6 +436,7 @@ cudaError_t expm_pade13_batch(int count, const int64_t *n, const double *const *
         p.bar = reinterpret_cast<unsigned *>(base);
         p.norm_bits = reinterpret_cast<unsigned long long *>(base + 64);
         p.w = reinterpret_cast<double *>(base + 256);
+        p.flags = base + 256 + (size_t)(16 * n[i] * n[i]) * sizeof(double);
         nmax = std::max(nmax, n[i]);
         cudaError_t e = cudaMemsetAsync(base, 0, 256, st);
         if (e != cudaSuccess) return e;
