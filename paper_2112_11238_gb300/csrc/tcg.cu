@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(kGThreads, 1) tcg_kernel(const __grid_constant
 // distinct banks and store consecutive outputs; the loops over k are
 // unrolled to 32 (K <= 32), so that every shared-memory address is a
 // register plus a constant.
-constexpr int kFR = 8;
+constexpr int kFR = 4;
 constexpr int kFWP4 = 8;  // op(L_t)^T rows: 32 floats (eight 16-byte words)
 
 __global__ void __launch_bounds__(kGThreads, 1) tcf_kernel(const __grid_constant__ GLaunch L) {
